@@ -1,0 +1,22 @@
+"""Writes tests/golden/synth_digests.json: structure digests of the seeded
+workloads and their oracle plan flop totals.  Calls only dmrg_synth and
+oracle; run from the repository root:  python tests/golden/make_golden.py"""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import dmrg_synth as S  # noqa: E402
+from oracle import heff  # noqa: E402
+
+out = {}
+for name in ("tiny", "mid"):
+    p = S.generate(name, seed=0)
+    plan = heff.plan(p)
+    out[name] = dict(structure_sha256=p.structure_digest(), dim=p.dim, n_terms=p.n_terms,
+                     op_len=int(p.op_data.size), plan_items=int(len(plan)),
+                     plan_flops=int(plan[:, 4].sum()))
+json.dump(out, open(os.path.join(ROOT, "tests", "golden", "synth_digests.json"), "w"), indent=1)
+print(json.dumps(out, indent=1))
