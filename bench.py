@@ -1,0 +1,318 @@
+#!/usr/bin/env python3
+"""H_eff*psi benchmark on GB300: FP64-equivalent TFLOP/s of the two-site DMRG
+effective-Hamiltonian product (and Davidson time-to-eigenvalue), one JSON line.
+
+A step is one H_eff*psi over nvec vectors of the named synthetic workload with
+operators resident in HBM.  `value` = algorithmic flops (min-order plan count, the
+same for every precision) x steps / device time.  Under torchrun every rank runs an
+independent replica (the product does not shard), value sums the ranks' work over
+the slowest rank's time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config mid]
+                    [--precision fp64|split] [--nvec 1] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Hψ FP64-equiv TFLOP/s; Davidson time-to-E, split vs FP64 (|ΔE/E|≤1e-10)"
+UNIT = "TFLOP/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# DRAM bytes per launch of the dominant kernel from one ncu capture, keyed by the
+# sha256 of the kernel source it was taken on (a changed kernel reports null).
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="mid")
+    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--nvec", type=int, default=1)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample length")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-davidson", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def workload_config(p, args, precision):
+    import dmrg_synth as S
+    cfg = S.CONFIGS[args.config]
+    return {
+        "workload": f"{args.config}: two-site H_eff, D={cfg['D']} per block over {len(p.left)} (n,2Sz) sectors, "
+                    f"T={p.n_terms} terms, |psi|={p.dim}, seed {args.seed}",
+        "D": cfg["D"], "sectors": int(len(p.left)), "terms": int(p.n_terms), "psi_dim": int(p.dim),
+        "operator_GB": round(p.op_data.size * 8 / 1e9, 3), "nvec": args.nvec, "precision": precision,
+        "l2": "inputs larger than L2 (all operator blocks are read every step)",
+        "parallelism": "replicas",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except (OSError, ValueError):
+        return {}
+
+
+def kernel_sha(name: str) -> str:
+    return hashlib.sha256(open(os.path.join(ROOT, "paper_2407_07411_gb300", "csrc", name), "rb").read()).hexdigest()
+
+
+def roofline(stats, precision, fp64_peak, timed_long):
+    """Dominant kernel (largest summed event time) against its tensor peak."""
+    by_kernel = {}
+    for s in stats:
+        k = s["name"].split("/")[0]
+        d = by_kernel.setdefault(k, dict(ms=0.0, flops=0.0, bytes=0.0, launches=0))
+        d["ms"] += s["ms_total"]; d["flops"] += s["flops_total"]; d["bytes"] += s["bytes_total"]
+        d["launches"] += s["launches"]
+    if not by_kernel:
+        return None
+    name, d = max(by_kernel.items(), key=lambda kv: kv[1]["ms"])
+    if d["ms"] <= 0:
+        return None
+    achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+    if name.startswith("fp64"):
+        peak, src, src_name = fp64_peak, "measured live: DMMA m16n8k16 probe (dmrg_probe_fp64_peak)", "k_fp64.cu"
+    else:
+        pk = peaks()
+        key = "bf16_tflops_sustained" if timed_long else "bf16_tflops"
+        peak = pk.get(key, 1700.0 if timed_long else 1900.0)
+        src = f"MEASURED_PEAKS.json {key}" if key in pk else "profiling recipe fallback"
+        src_name = "k_split.cu"
+    tr = NCU_TRAFFIC.get(kernel_sha(src_name))
+    return {"kernel": name, "bound": "tensor", "achieved": round(achieved, 4), "peak": round(peak, 4),
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4) if peak else None,
+            "traffic": tr, "algorithmic_bytes_per_launch": round(d["bytes"] / max(d["launches"], 1)),
+            "launches": d["launches"], "avg_launch_ms": round(d["ms"] / max(d["launches"], 1), 5),
+            "peak_source": src}
+
+
+def cpu_baseline(p, flops_per_vec, seconds):
+    """The oracle as it stands, timed on the host cores on a bounded sample."""
+    import numpy as np
+    from oracle import heff as oheff
+    x = p.random_vectors(1)[0]
+    calls, t0, c0 = 0, time.perf_counter(), time.process_time()
+    while True:
+        oheff.apply(p, x)
+        calls += 1
+        wall = time.perf_counter() - t0
+        if wall >= seconds:
+            break
+    cpu = time.process_time() - c0
+    return {"value": round(flops_per_vec * calls / wall / 1e12, 6), "unit": UNIT,
+            "cores": round(cpu / wall, 2), "kind": "oracle",
+            "sample": f"{calls} full oracle H_eff*psi calls (numpy block loop) on the bench workload, "
+                      f"{wall:.1f} s wall; cores = process CPU time / wall time",
+            "host_cores_available": os.cpu_count(), "_np": np.__version__}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import dmrg_synth as S
+    from oracle import heff as oheff
+    p = S.generate(args.config, seed=args.seed)
+    flops = oheff.plan_flops(p)
+    x = p.random_vectors(1)[0]
+    t0 = time.perf_counter()
+    oheff.apply(p, x)
+    one = time.perf_counter() - t0
+    budget = 150.0
+    frac = min(1.0, budget / max(one * (args.steps + args.warmup), 1e-9))
+    if frac < 1.0:   # bounded sample: the first fraction of the terms
+        T = max(1, int(p.n_terms * frac))
+        p = S.generate(args.config, seed=args.seed, n_terms=T)
+        flops = oheff.plan_flops(p)
+    for _ in range(args.warmup):
+        oheff.apply(p, x)
+    t0, c0 = time.perf_counter(), time.process_time()
+    for _ in range(args.steps):
+        oheff.apply(p, x)
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    value = flops * args.steps / wall / 1e12
+    sample = (f"each step = one oracle H_eff*psi over {'all' if frac >= 1 else f'the first {p.n_terms}'} "
+              f"terms of the {args.config} workload")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(wall / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded sector structure, random operator blocks)",
+            "config": workload_config(p, args, "fp64 (oracle)"),
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "kind": "oracle", "cores": round(cpu / wall, 2),
+                             "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import dmrg_synth as S
+    import paper_2407_07411_gb300 as lib
+
+    precision = {"fp64": "fp64", "split": "split_bf16", "split_bf16": "split_bf16"}[args.precision]
+    p = S.generate(args.config, seed=args.seed)
+    h = lib.HEff.from_problem(p, precision=precision, max_nvec=args.nvec)
+    flops_vec = h.flops
+    fp64_peak = lib.probe_fp64_peak() if precision == "fp64" else None
+    X = torch.from_numpy(p.random_vectors(args.nvec)).cuda()
+    Y = torch.empty_like(X)
+    st = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        h.apply(X, Y, nvec=args.nvec)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    h.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    gpu_index = int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local
+    with ClockSampler(gpu_index) as clk:
+        barrier()
+        e0.record(st)
+        for _ in range(args.steps):
+            h.apply(X, Y, nvec=args.nvec)
+        e1.record(st)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    stats = h.profile_read()
+    h.profile(False)
+    t_max = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    total_flops = flops_vec * args.nvec * args.steps * ws
+    value = total_flops / (t_max * 1e-3) / 1e12
+
+    # end to end through the public host API: pinned H2D of x, apply, D2H of y
+    xh = torch.from_numpy(p.random_vectors(args.nvec)).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    e2e_steps = max(3, min(args.steps, 50))
+    for _ in range(2):
+        h.apply_host_ptr(xh.data_ptr(), yh.data_ptr(), args.nvec)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        h.apply_host_ptr(xh.data_ptr(), yh.data_ptr(), args.nvec)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    nbytes = args.nvec * p.dim * 8
+    e2e = {"value": round(flops_vec * args.nvec * e2e_steps * ws / e2e_s / 1e12, 6), "unit": UNIT,
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+           "api": "dmrg_heff_apply_host (pinned host buffers, synchronous)"}
+
+    launches = sum(s["launches"] for s in stats)
+    line = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "bf16",
+            "data": "synthetic (seeded sector structure, random operator blocks)",
+            "config": workload_config(p, args, precision),
+            "roofline": roofline(stats, precision, fp64_peak, timed_long=t_max > 2000),
+            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
+            "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()} for s in stats],
+            "flops_per_step": flops_vec * args.nvec}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, flops_vec, args.cpu_seconds)
+        line["cpu_baseline"].pop("_np", None)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,153 @@
+/*
+ * dmrg_heff.h -- C ABI of the GB300 (sm_103a) two-site DMRG effective-Hamiltonian
+ * library: H_eff*psi and the Davidson eigensolver that calls it.
+ *
+ * The operation (paper: Numerical procedure, Eq. 2 and the Lanczos/Davidson step
+ * after it, which takes ~80% of the run time and scales as O(D^3)): the local
+ * two-site eigenproblem of DMRG with the effective Hamiltonian in symmetry-sector
+ * form
+ *
+ *     H_eff = sum_t c_t (A_t (x) B_t) P_t ,
+ *
+ * A_t acting on the left enlarged block and shifting its (n, 2S_z) sector by
+ * Delta_t, B_t acting on the right block and shifting it by -Delta_t, and
+ * P_t = (-1)^{n_L} on the *input* left sector for terms with the parity flag
+ * (odd Delta_n: fermionic operators that pass the left block), identity otherwise.
+ * Block-wise, every term and every wave-function block q = (q_L, q_R) gives
+ *
+ *     y[q_L+Delta, q_R-Delta] += c_t s_t A_t[q_L+Delta <- q_L] x[q] B_t[q_R-Delta <- q_R]^T .
+ *
+ * Layouts
+ *   sector tables   int32 (nsec x 3) rows (n, two_sz, dim), strictly ascending in
+ *                   (n, two_sz), dim >= 1.
+ *   wave function   blocks (q_L, q_R) with q_L + q_R = target, ascending in the
+ *                   left sector, each row-major dim(q_L) x dim(q_R), concatenated;
+ *                   nvec vectors are stored one after another (stride = dim).
+ *   operator blocks A_t[p <- q] is row-major dim(p) x dim(q) at op_data[a_off[t*nl+q]],
+ *                   p = q + Delta_t;  B_t[p <- q] is row-major dim(p) x dim(q) at
+ *                   op_data[b_off[t*nr+q]], p = q - Delta_t.  Offset -1 = absent.
+ *
+ * Ownership: dmrg_heff_create copies every host array it is given; the handle owns
+ * its device memory.  x, y, diag and x_inout of the device entry points are caller
+ * owned device pointers.  A handle is not thread-safe; distinct handles are.
+ * Errors: every entry point returns DMRG_OK (0) or a negative DMRG_ERR_* code; no
+ * exception crosses the ABI.  dmrg_strerror gives a message, dmrg_last_error the
+ * detail of the last failure on the calling thread.
+ */
+#ifndef DMRG_HEFF_H
+#define DMRG_HEFF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DMRG_OK                   0
+#define DMRG_ERR_INVALID_ARG     -1  /* null pointer, bad size, unsorted table, bad offset */
+#define DMRG_ERR_SECTOR_MISMATCH -2  /* a block present for a shift whose sector is absent */
+#define DMRG_ERR_OOM             -3  /* device or host allocation failed */
+#define DMRG_ERR_CUDA            -4  /* a CUDA runtime call failed */
+#define DMRG_ERR_DEVICE_TIMEOUT  -5  /* a bounded device-side wait gave up */
+#define DMRG_ERR_NOT_CONVERGED   -6  /* Davidson stopped before reaching tol */
+#define DMRG_ERR_BOUNDS          -7  /* bounds-checked build saw an out-of-range access */
+#define DMRG_ERR_UNSUPPORTED     -8  /* option not available in this build */
+
+/* Arithmetic of the contractions. */
+#define DMRG_PREC_FP64        0  /* FP64 DMMA tensor-core tiles (mma.sync m16n8k16 f64) */
+#define DMRG_PREC_SPLIT_BF16  1  /* Ozaki split: FP64 operands as BF16 digit slices on
+                                    tcgen05 tensor cores, exact FP32 partial sums,
+                                    recombined in FP64 */
+
+typedef struct dmrg_heff* dmrg_heff_t;
+
+typedef struct {
+    int32_t precision;  /* DMRG_PREC_*                                               */
+    int32_t n_slices;   /* split path: digit slices per operand (0 = default)        */
+    int32_t max_nvec;   /* largest nvec passed to apply (sizes the scratch), >= 1   */
+    int32_t flags;      /* DMRG_FLAG_* bits                                           */
+} dmrg_heff_opts;
+
+/* Build only the host-side plan: no device memory is touched, so the handle works
+ * without a GPU; only dmrg_heff_dim, _flops, _plan_dump and _destroy may be called. */
+#define DMRG_FLAG_PLAN_ONLY 1
+
+typedef struct {
+    int32_t iters;       /* Rayleigh-Ritz steps taken                               */
+    int32_t matvecs;     /* vectors multiplied by H_eff                              */
+    int32_t converged;   /* 1 if every wanted residual norm <= tol                   */
+    int32_t restarts;    /* thick restarts taken                                      */
+    double  resid_max;   /* largest residual norm of the wanted pairs at exit        */
+    double  seconds;     /* wall time inside dmrg_davidson                           */
+} dmrg_davidson_info;
+
+/* Build a handle: validate the tables, index the wave-function blocks, plan every
+ * (term, block) contraction (cheaper of (A x)B^T and A(x B^T) by exact integer flop
+ * count, A-first on a tie), lay the operator blocks out on the device and build the
+ * grouped-GEMM work lists.  All pointers are host pointers; all arrays are copied.
+ *   left, right : sector tables (nl x 3, nr x 3)
+ *   target_*    : quantum numbers of the two-site wave function
+ *   coef (T), delta (T x 2: dn, d2sz), parity (T: 0 or 1)
+ *   a_off (T x nl), b_off (T x nr): block offsets into op_data (-1 = absent)
+ *   op_data (op_len doubles), opts (NULL = FP64, max_nvec 1)
+ * Returns DMRG_ERR_INVALID_ARG / _SECTOR_MISMATCH for malformed input, _OOM, _CUDA. */
+int dmrg_heff_create(const int32_t* left, int32_t nl, const int32_t* right, int32_t nr,
+                     int32_t target_n, int32_t target_2sz,
+                     const double* coef, const int32_t* delta, const int32_t* parity,
+                     const int64_t* a_off, const int64_t* b_off, int64_t n_terms,
+                     const double* op_data, int64_t op_len,
+                     const dmrg_heff_opts* opts, dmrg_heff_t* out);
+
+/* Number of wave-function entries |psi| (0 for an empty target sector). */
+int64_t dmrg_heff_dim(dmrg_heff_t h);
+
+/* Algorithmic flops of one H_eff*psi for one vector: the sum over the plan of the
+ * cheaper order's 2abc + 2acd or 2bcd + 2abd. */
+int dmrg_heff_flops(dmrg_heff_t h, int64_t* flops);
+
+/* Canonical plan: rows (out_block, term, in_block, order 0=A-first 1=B-first, flops),
+ * int64, sorted by (out_block, term, in_block).  Call with buf = NULL to get *n_rows;
+ * otherwise buf must hold *n_rows * 5 values. */
+int dmrg_heff_plan_dump(dmrg_heff_t h, int64_t* buf, int64_t* n_rows);
+
+/* y = H_eff x for nvec vectors (1 <= nvec <= max_nvec); x, y device pointers of
+ * nvec*dim doubles, x and y must not overlap; runs asynchronously on `stream`
+ * (a cudaStream_t, NULL = legacy default stream) as one CUDA-graph launch. */
+int dmrg_heff_apply(dmrg_heff_t h, const double* x, double* y, int32_t nvec, void* stream);
+
+/* Same as dmrg_heff_apply with host x and y: copies x in, applies, copies y out and
+ * waits for the result (pinned host memory gives the fastest copies). */
+int dmrg_heff_apply_host(dmrg_heff_t h, const double* x, double* y, int32_t nvec);
+
+/* diag (device, dim doubles) = diagonal of H_eff: sum over Delta = 0 terms of
+ * c_t s_t A_t[l,l] B_t[r,r]. */
+int dmrg_heff_diagonal(dmrg_heff_t h, double* diag, void* stream);
+
+/* Lowest k_eig eigenpairs by block Davidson with FP64 CGS2 orthogonalisation,
+ * Rayleigh-Ritz by cyclic Jacobi on the device, diagonal preconditioner and thick
+ * restart; the steps are those of the library's documented Davidson variant.
+ *   block      : vectors added per step (1 <= block <= max_nvec)
+ *   tol        : residual-norm target ||H x - theta x|| for unit x
+ *   max_iter   : Rayleigh-Ritz steps allowed
+ *   n_iter     : > 0 runs exactly this many steps (no convergence test), else 0
+ *   x_inout    : device, block*dim doubles: start block in (need not be orthonormal);
+ *                the first k_eig rows hold the Ritz vectors on return
+ *   evals      : host, k_eig doubles; info: host, may be NULL.
+ * Returns DMRG_ERR_NOT_CONVERGED (results still written) when tol was not met. */
+int dmrg_davidson(dmrg_heff_t h, int32_t k_eig, double tol, int32_t max_iter, int32_t block,
+                  int32_t n_iter, double* x_inout, double* evals, dmrg_davidson_info* info);
+
+/* Release the handle and its device memory (NULL is ignored). */
+void dmrg_heff_destroy(dmrg_heff_t h);
+
+/* Static message for a DMRG_* code. */
+const char* dmrg_strerror(int code);
+
+/* Detail of the last failure on the calling thread ("" if none). */
+const char* dmrg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DMRG_HEFF_H */

@@ -1,0 +1,236 @@
+"""GB300 (sm_103a) two-site DMRG effective-Hamiltonian library: Python binding.
+
+This module only marshals arguments to the C ABI of libdmrg_gb300.so (declared
+in include/dmrg_heff.h); every step of H_eff*psi and of the Davidson solver runs
+in the library's CUDA kernels.  Importing it fails if the library has not been
+built (``python paper_2407_07411_gb300/build.py``): there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdmrg_gb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2407_07411_gb300/build.py`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+PREC_FP64 = 0
+PREC_SPLIT_BF16 = 1
+FLAG_PLAN_ONLY = 1
+_PREC = {"fp64": PREC_FP64, "split_bf16": PREC_SPLIT_BF16, "split": PREC_SPLIT_BF16}
+
+#: Every symbol the C ABI exports (include/dmrg_heff.h).
+SYMBOLS = ("dmrg_heff_create", "dmrg_heff_dim", "dmrg_heff_flops", "dmrg_heff_plan_dump",
+           "dmrg_heff_apply", "dmrg_heff_apply_host", "dmrg_heff_diagonal", "dmrg_davidson",
+           "dmrg_heff_destroy", "dmrg_strerror", "dmrg_last_error", "dmrg_heff_profile",
+           "dmrg_heff_profile_read", "dmrg_probe_fp64_peak")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("n_slices", ctypes.c_int32),
+                ("max_nvec", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class DavidsonInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("matvecs", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("resid_max", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("ms_total", ctypes.c_double),
+                ("flops_total", ctypes.c_double), ("bytes_total", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_i32, _i64, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_lib.dmrg_heff_create.argtypes = [_P, _i32, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _i64, _P, _i64,
+                                  ctypes.POINTER(Opts), ctypes.POINTER(_P)]
+_lib.dmrg_heff_create.restype = ctypes.c_int
+_lib.dmrg_heff_dim.argtypes = [_P]
+_lib.dmrg_heff_dim.restype = _i64
+_lib.dmrg_heff_flops.argtypes = [_P, ctypes.POINTER(_i64)]
+_lib.dmrg_heff_plan_dump.argtypes = [_P, _P, ctypes.POINTER(_i64)]
+_lib.dmrg_heff_apply.argtypes = [_P, _P, _P, _i32, _P]
+_lib.dmrg_heff_apply_host.argtypes = [_P, _P, _P, _i32]
+_lib.dmrg_heff_diagonal.argtypes = [_P, _P, _P]
+_lib.dmrg_davidson.argtypes = [_P, _i32, _f64, _i32, _i32, _i32, _P, _P, ctypes.POINTER(DavidsonInfo)]
+_lib.dmrg_heff_destroy.argtypes = [_P]
+_lib.dmrg_heff_destroy.restype = None
+_lib.dmrg_strerror.argtypes = [ctypes.c_int]
+_lib.dmrg_strerror.restype = ctypes.c_char_p
+_lib.dmrg_last_error.argtypes = []
+_lib.dmrg_last_error.restype = ctypes.c_char_p
+
+_lib.dmrg_heff_profile.argtypes = [_P, _i32]
+_lib.dmrg_heff_profile_read.argtypes = [_P, ctypes.POINTER(KernelStat), ctypes.POINTER(_i32)]
+_lib.dmrg_probe_fp64_peak.argtypes = [ctypes.POINTER(_f64)]
+
+ERR_NOT_CONVERGED = -6
+
+
+class DmrgError(RuntimeError):
+    def __init__(self, code: int):
+        self.code = code
+        msg = _lib.dmrg_strerror(code).decode()
+        detail = _lib.dmrg_last_error().decode()
+        super().__init__(f"{msg} ({code}): {detail}")
+
+
+def _check(rc: int) -> int:
+    if rc != 0:
+        raise DmrgError(rc)
+    return rc
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p) if a.size else None
+
+
+def _dev_ptr(t, n: int, what: str):
+    """Device pointer of a contiguous CUDA float64 tensor with >= n elements."""
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
+        raise ValueError(f"{what} must be a contiguous CUDA float64 tensor")
+    if t.numel() < n:
+        raise ValueError(f"{what} holds {t.numel()} values, {n} needed")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class HEff:
+    """Handle of one effective Hamiltonian on the current CUDA device."""
+
+    def __init__(self, left, right, target, coef, delta, parity, a_off, b_off, op_data,
+                 precision: str = "fp64", max_nvec: int = 1, n_slices: int = 0, plan_only: bool = False):
+        self._h = None
+        arr = lambda a, dt: np.ascontiguousarray(np.asarray(a, dtype=dt))
+        self._left = arr(left, np.int32).reshape(-1, 3)
+        self._right = arr(right, np.int32).reshape(-1, 3)
+        coef, delta = arr(coef, np.float64), arr(delta, np.int32).reshape(-1, 2)
+        parity = arr(parity, np.int32)
+        T = coef.shape[0]
+        a_off = arr(a_off, np.int64).reshape(T, len(self._left))
+        b_off = arr(b_off, np.int64).reshape(T, len(self._right))
+        op_data = arr(op_data, np.float64)
+        opts = Opts(_PREC[precision] if isinstance(precision, str) else int(precision), n_slices, max_nvec,
+                    FLAG_PLAN_ONLY if plan_only else 0)
+        h = ctypes.c_void_p()
+        _check(_lib.dmrg_heff_create(_ptr(self._left), len(self._left), _ptr(self._right), len(self._right),
+                                     int(target[0]), int(target[1]), _ptr(coef), _ptr(delta), _ptr(parity),
+                                     _ptr(a_off), _ptr(b_off), T, _ptr(op_data), op_data.size,
+                                     ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+        self.max_nvec = max_nvec
+        self.precision = precision
+
+    @classmethod
+    def from_problem(cls, p, **kw) -> "HEff":
+        """Build from any object with the fields of a two-site problem
+        (left, right, target, coef, delta, parity, a_off, b_off, op_data)."""
+        return cls(p.left, p.right, p.target, p.coef, p.delta, p.parity, p.a_off, p.b_off, p.op_data, **kw)
+
+    def close(self):
+        if self._h:
+            _lib.dmrg_heff_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def dim(self) -> int:
+        return int(_lib.dmrg_heff_dim(self._h))
+
+    @property
+    def flops(self) -> int:
+        f = _i64()
+        _check(_lib.dmrg_heff_flops(self._h, ctypes.byref(f)))
+        return int(f.value)
+
+    def plan_dump(self) -> np.ndarray:
+        n = _i64(0)
+        _check(_lib.dmrg_heff_plan_dump(self._h, None, ctypes.byref(n)))
+        buf = np.zeros((n.value, 5), np.int64)
+        _check(_lib.dmrg_heff_plan_dump(self._h, _ptr(buf), ctypes.byref(n)))
+        return buf
+
+    def apply(self, x, y, nvec: int = 1, stream=None):
+        """y = H_eff x for nvec vectors; x, y CUDA float64 tensors (or raw device
+        pointers), asynchronous on `stream` (default: torch's current stream)."""
+        n = nvec * self.dim
+        _check(_lib.dmrg_heff_apply(self._h, _dev_ptr(x, n, "x"), _dev_ptr(y, n, "y"), nvec,
+                                    _stream_ptr(stream)))
+        return y
+
+    def apply_host(self, x: np.ndarray) -> np.ndarray:
+        """y = H_eff x with host arrays (nvec, dim) or (dim,), synchronous."""
+        x = np.ascontiguousarray(x, np.float64)
+        nvec = 1 if x.ndim == 1 else x.shape[0]
+        if x.size != nvec * self.dim:
+            raise ValueError("x has the wrong size")
+        y = np.empty_like(x)
+        _check(_lib.dmrg_heff_apply_host(self._h, _ptr(x), _ptr(y), nvec))
+        return y
+
+    def apply_host_ptr(self, x_ptr: int, y_ptr: int, nvec: int):
+        """apply_host on raw host pointers (for pinned buffers)."""
+        _check(_lib.dmrg_heff_apply_host(self._h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), nvec))
+
+    def profile(self, enable: bool = True):
+        """Start (reset) or stop per-kernel CUDA-event timing of this handle."""
+        _check(_lib.dmrg_heff_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> list:
+        """Per-kernel dicts: name, launches, ms_total, flops_total, bytes_total."""
+        n = _i32(0)
+        _check(_lib.dmrg_heff_profile_read(self._h, None, ctypes.byref(n)))
+        buf = (KernelStat * max(n.value, 1))()
+        _check(_lib.dmrg_heff_profile_read(self._h, buf, ctypes.byref(n)))
+        return [dict(name=s.name.decode(), launches=s.launches, ms_total=s.ms_total,
+                     flops_total=s.flops_total, bytes_total=s.bytes_total) for s in buf[:n.value]]
+
+    def diagonal(self, out, stream=None):
+        _check(_lib.dmrg_heff_diagonal(self._h, _dev_ptr(out, self.dim, "diag"), _stream_ptr(stream)))
+        return out
+
+    def davidson(self, x0, k_eig: int = 1, tol: float = 1e-8, max_iter: int = 300, block: int | None = None,
+                 n_iter: int = 0):
+        """Lowest k_eig eigenpairs.  x0: CUDA float64 tensor (block, dim), the start
+        block, overwritten with the Ritz vectors in its first k_eig rows.
+        Returns (evals ndarray, info dict); info['converged'] is False when tol
+        was not met within max_iter."""
+        block = block or (x0.shape[0] if x0.dim() == 2 else 1)
+        ev = np.zeros(max(k_eig, 1), np.float64)
+        info = DavidsonInfo()
+        rc = _lib.dmrg_davidson(self._h, k_eig, tol, max_iter, block, n_iter,
+                                _dev_ptr(x0, block * self.dim, "x0"), _ptr(ev), ctypes.byref(info))
+        if rc not in (0, ERR_NOT_CONVERGED):
+            raise DmrgError(rc)
+        return ev[:k_eig], dict(iters=info.iters, matvecs=info.matvecs, converged=bool(info.converged),
+                                restarts=info.restarts, resid_max=info.resid_max, seconds=info.seconds)
+
+
+def probe_fp64_peak() -> float:
+    """FP64 tensor-core (DMMA m16n8k16) throughput of the current GPU, TFLOP/s."""
+    v = _f64()
+    _check(_lib.dmrg_probe_fp64_peak(ctypes.byref(v)))
+    return float(v.value)

@@ -1,0 +1,94 @@
+// The opaque handle behind dmrg_heff_t.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "plan.h"
+
+struct dmrg_heff {
+    virtual ~dmrg_heff() = default;
+};
+
+namespace dmrg {
+
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+// One diagonal contribution list entry: block `blk` of the wave function gets
+// sign * sum_t A_stack[t][i][i] * B_stack[t][j][j] over the n terms of a
+// Delta = 0 group (A_stack already carries c_t).
+struct DiagJob {
+    int64_t a_stack, b_stack, off;
+    int32_t n, rows, cols, pad;
+    double sign;
+};
+
+struct SplitState;
+struct DavidsonState;
+
+// Launch accounting of one handle: counts, algorithmic flops/bytes and (when
+// timing) CUDA-event pairs recorded on the launching stream.
+struct Profiler {
+    struct Pending { int id; cudaEvent_t start, stop; };
+    struct Rec { int id; cudaEvent_t start, stop; };
+    std::vector<std::string> names;
+    std::vector<int64_t> launches;
+    std::vector<double> flops, bytes, ms;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used = 0;
+    std::vector<Rec> recs;
+    bool timing = false;
+    int kernel_id(const char* name);
+    cudaEvent_t take_event();
+    void begin(int id, cudaStream_t st, double f, double b, Pending* p);
+    void end(const Pending& p, cudaStream_t st);
+    void reset();
+    int collect();
+    ~Profiler();
+};
+
+struct Handle : dmrg_heff {
+    Plan plan;
+    int precision = 0, max_nvec = 1, n_slices = 0;
+    int device = 0, n_sm = 152, tiles_per_sm = 8;
+    bool plan_only = false;
+    double* d_ops = nullptr;
+    double* d_scr = nullptr;
+    double* d_part = nullptr;
+    Tile* d_tiles1 = nullptr;
+    Tile* d_tiles2 = nullptr;
+    Gemm* d_gemms = nullptr;
+    Seg* d_segs = nullptr;
+    Reduce* d_red = nullptr;
+    int32_t* d_counters = nullptr;
+    double* d_xstage = nullptr;
+    double* d_ystage = nullptr;
+    DiagJob* d_diag_jobs = nullptr;
+    int32_t n_diag_jobs = 0;
+    SplitState* split = nullptr;
+    DavidsonState* dav = nullptr;
+    Profiler prof;
+    int kid_s1 = -1, kid_s2 = -1, kid_red = -1;
+    double s1_flops = 0, s2_flops = 0, s1_bytes = 0, s2_bytes = 0;
+
+    ~Handle() override;
+    Spaces spaces(const double* x, double* y) const;
+    int apply(const double* x, double* y, int32_t nvec, cudaStream_t st);
+    int apply_fp64(const double* x, double* y, int32_t nvec, cudaStream_t st);
+    int init_diag();
+    int diagonal(double* diag, cudaStream_t st);
+    // split-precision path (k_split.cu)
+    int init_split(const double* coef, const int64_t* a_off, const int64_t* b_off, const double* op_data);
+    int apply_split(const double* x, double* y, int32_t nvec, cudaStream_t st);
+    void release_split();
+    // Davidson (davidson.cu)
+    void release_davidson();
+};
+
+cudaError_t launch_diag(const DiagJob* jobs, int32_t n_jobs, const double* ops, double* diag,
+                        int64_t dim, cudaStream_t st);
+
+}  // namespace dmrg

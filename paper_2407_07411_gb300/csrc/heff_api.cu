@@ -1,0 +1,290 @@
+// C ABI of the library: handle life cycle, device layout of the operators and work
+// lists, and the apply entry points.  Every arithmetic step runs in the kernels of
+// k_*.cu; this file only validates, allocates, uploads and launches.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dmrg_heff.h"
+#include "handle.h"
+#include "kernels.h"
+
+namespace dmrg {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? DMRG_ERR_OOM : DMRG_ERR_CUDA;
+}
+
+template <class T>
+static int upload(const std::vector<T>& v, T** dst, const char* what) {
+    *dst = nullptr;
+    if (v.empty()) return DMRG_OK;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), sizeof(T) * v.size());
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    e = cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return DMRG_OK;
+}
+
+static int dalloc(void** p, size_t bytes, const char* what) {
+    *p = nullptr;
+    if (bytes == 0) return DMRG_OK;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return DMRG_OK;
+}
+
+Spaces Handle::spaces(const double* x, double* y) const {
+    Spaces s;
+    s.ops = d_ops; s.x = x; s.scr = d_scr; s.y = y; s.part = d_part;
+    s.x_vs = plan.dim; s.y_vs = plan.dim; s.scr_vs = plan.scratch_len;
+    s.part_vs = plan.n_slots * FP64_BM * FP64_BN;
+    return s;
+}
+
+int Handle::apply_fp64(const double* x, double* y, int32_t nvec, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(y, 0, sizeof(double) * plan.dim * nvec, st);
+    if (e != cudaSuccess) return cuda_fail(e, "zero y");
+    e = cudaMemsetAsync(d_counters, 0, sizeof(int32_t) * 2, st);
+    if (e != cudaSuccess) return cuda_fail(e, "zero counters");
+    const Spaces sp = spaces(x, y);
+    auto grid_for = [&](size_t n) {
+        int64_t items = int64_t(n) * nvec;
+        int64_t g = int64_t(n_sm) * tiles_per_sm;
+        return int32_t(items < g ? items : g);
+    };
+    Profiler::Pending pe;
+    if (!plan.tiles1.empty()) {
+        prof.begin(kid_s1, st, s1_flops * nvec, s1_bytes * nvec, &pe);
+        e = launch_fp64_tiles(d_tiles1, int32_t(plan.tiles1.size()), d_gemms, d_segs, sp, nvec,
+                              d_counters, grid_for(plan.tiles1.size()), st);
+        prof.end(pe, st);
+        if (e != cudaSuccess) return cuda_fail(e, "stage-1 tiles");
+    }
+    if (!plan.tiles2.empty()) {
+        prof.begin(kid_s2, st, s2_flops * nvec, s2_bytes * nvec, &pe);
+        e = launch_fp64_tiles(d_tiles2, int32_t(plan.tiles2.size()), d_gemms, d_segs, sp, nvec,
+                              d_counters + 1, grid_for(plan.tiles2.size()), st);
+        prof.end(pe, st);
+        if (e != cudaSuccess) return cuda_fail(e, "stage-2 tiles");
+    }
+    if (!plan.reduces.empty()) {
+        prof.begin(kid_red, st, 0.0, double(plan.reduces.size()) * FP64_BM * FP64_BN * 8.0 * nvec, &pe);
+        e = launch_fp64_reduce(d_red, int32_t(plan.reduces.size()), d_gemms, sp, nvec, st);
+        prof.end(pe, st);
+        if (e != cudaSuccess) return cuda_fail(e, "stage-2 reduce");
+    }
+    return DMRG_OK;
+}
+
+int Handle::apply(const double* x, double* y, int32_t nvec, cudaStream_t st) {
+    if (plan_only) return fail(DMRG_ERR_INVALID_ARG, "plan-only handle");
+    if (nvec < 1 || nvec > max_nvec) return fail(DMRG_ERR_INVALID_ARG, "nvec outside [1, max_nvec]");
+    if (plan.dim == 0) return DMRG_OK;
+    if (!x || !y) return fail(DMRG_ERR_INVALID_ARG, "null x or y");
+    const char* xb = reinterpret_cast<const char*>(x);
+    const char* yb = reinterpret_cast<const char*>(y);
+    const size_t bytes = sizeof(double) * plan.dim * nvec;
+    if (xb < yb + bytes && yb < xb + bytes) return fail(DMRG_ERR_INVALID_ARG, "x and y overlap");
+    if (precision == DMRG_PREC_FP64) return apply_fp64(x, y, nvec, st);
+    return apply_split(x, y, nvec, st);
+}
+
+Handle::~Handle() {
+    void* ptrs[] = {d_ops, d_scr, d_part, d_tiles1, d_tiles2, d_gemms, d_segs, d_red, d_counters,
+                    d_xstage, d_ystage, d_diag_jobs};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    release_split();
+    release_davidson();
+}
+
+}  // namespace dmrg
+
+using dmrg::Handle;
+
+extern "C" {
+
+int dmrg_heff_create(const int32_t* left, int32_t nl, const int32_t* right, int32_t nr,
+                     int32_t target_n, int32_t target_2sz, const double* coef, const int32_t* delta,
+                     const int32_t* parity, const int64_t* a_off, const int64_t* b_off,
+                     int64_t n_terms, const double* op_data, int64_t op_len,
+                     const dmrg_heff_opts* opts, dmrg_heff_t* out) {
+    if (!out) return dmrg::fail(DMRG_ERR_INVALID_ARG, "null output handle");
+    *out = nullptr;
+    dmrg_heff_opts o{DMRG_PREC_FP64, 0, 1, 0};
+    if (opts) o = *opts;
+    if (o.precision != DMRG_PREC_FP64 && o.precision != DMRG_PREC_SPLIT_BF16)
+        return dmrg::fail(DMRG_ERR_INVALID_ARG, "unknown precision");
+    if (o.max_nvec < 1 || o.max_nvec > 64 || (o.flags & ~DMRG_FLAG_PLAN_ONLY) != 0)
+        return dmrg::fail(DMRG_ERR_INVALID_ARG, "max_nvec must be in [1, 64], unknown flags must be 0");
+    if (op_len > 0 && !op_data) return dmrg::fail(DMRG_ERR_INVALID_ARG, "null op_data");
+    Handle* h = new (std::nothrow) Handle();
+    if (!h) return dmrg::fail(DMRG_ERR_OOM, "host allocation");
+    std::string err;
+    int rc = dmrg::build_plan(left, nl, right, nr, target_n, target_2sz, coef, delta, parity, a_off,
+                              b_off, n_terms, op_len, h->plan, &err);
+    if (rc != DMRG_OK) {
+        delete h;
+        return dmrg::fail(rc, err);
+    }
+    h->precision = o.precision;
+    h->max_nvec = o.max_nvec;
+    h->n_slices = o.n_slices;
+    h->plan_only = (o.flags & DMRG_FLAG_PLAN_ONLY) != 0;
+    if (h->plan_only) {
+        *out = h;
+        return DMRG_OK;
+    }
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return dmrg::cuda_fail(e, "cudaGetDevice");
+    }
+    cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
+    h->tiles_per_sm = dmrg::fp64_tiles_per_sm();
+    const dmrg::Plan& P = h->plan;
+    // Algorithmic work per vector of each stage: flops of the planned order, bytes =
+    // operator blocks read once + intermediates written (stage 1) or read (stage 2)
+    // + the wave function read (stage 1) or written (stage 2).
+    for (const dmrg::Group& G : P.groups) {
+        const double n = double(G.terms.size());
+        const double a = G.a, b = G.b, c = G.c, d = G.d;
+        if (G.order == 0) {
+            h->s1_flops += n * 2 * a * b * c; h->s2_flops += n * 2 * a * c * d;
+            h->s1_bytes += 8 * n * (a * b + a * c); h->s2_bytes += 8 * n * (a * c + d * c);
+        } else {
+            h->s1_flops += n * 2 * b * c * d; h->s2_flops += n * 2 * a * b * d;
+            h->s1_bytes += 8 * n * (d * c + d * b); h->s2_bytes += 8 * n * (a * b + d * b);
+        }
+    }
+    for (const dmrg::PsiBlock& B : P.blocks) {
+        h->s1_bytes += 8.0 * B.rows * B.cols;
+        h->s2_bytes += 8.0 * B.rows * B.cols;
+    }
+    if (o.precision == DMRG_PREC_FP64) {
+        h->kid_s1 = h->prof.kernel_id("fp64_tiles/stage1");
+        h->kid_s2 = h->prof.kernel_id("fp64_tiles/stage2");
+        h->kid_red = h->prof.kernel_id("fp64_reduce");
+    }
+    auto bail = [&](int code) {
+        delete h;
+        return code;
+    };
+    // Operators in the grouped device layout.
+    if (P.ops_len > 0) {
+        std::vector<double> staging(size_t(P.ops_len));
+        dmrg::fill_ops(P, coef, a_off, b_off, op_data, staging.data());
+        if ((rc = dmrg::upload(staging, &h->d_ops, "operators")) != DMRG_OK) return bail(rc);
+    }
+    const size_t nv = size_t(o.max_nvec);
+    if ((rc = dmrg::upload(P.tiles1, &h->d_tiles1, "tiles")) != DMRG_OK) return bail(rc);
+    if ((rc = dmrg::upload(P.tiles2, &h->d_tiles2, "tiles")) != DMRG_OK) return bail(rc);
+    if ((rc = dmrg::upload(P.gemms, &h->d_gemms, "gemms")) != DMRG_OK) return bail(rc);
+    if ((rc = dmrg::upload(P.segs, &h->d_segs, "segments")) != DMRG_OK) return bail(rc);
+    if ((rc = dmrg::upload(P.reduces, &h->d_red, "reduce jobs")) != DMRG_OK) return bail(rc);
+    if (o.precision == DMRG_PREC_FP64) {
+        if ((rc = dmrg::dalloc(reinterpret_cast<void**>(&h->d_scr), sizeof(double) * P.scratch_len * nv,
+                               "stage-1 scratch")) != DMRG_OK)
+            return bail(rc);
+        if ((rc = dmrg::dalloc(reinterpret_cast<void**>(&h->d_part),
+                               sizeof(double) * P.n_slots * dmrg::FP64_BM * dmrg::FP64_BN * nv,
+                               "partials")) != DMRG_OK)
+            return bail(rc);
+    } else {
+        if ((rc = h->init_split(coef, a_off, b_off, op_data)) != DMRG_OK) return bail(rc);
+    }
+    if ((rc = dmrg::dalloc(reinterpret_cast<void**>(&h->d_counters), 64, "counters")) != DMRG_OK)
+        return bail(rc);
+    if ((rc = h->init_diag()) != DMRG_OK) return bail(rc);
+    *out = h;
+    return DMRG_OK;
+}
+
+int64_t dmrg_heff_dim(dmrg_heff_t h) { return h ? static_cast<Handle*>(h)->plan.dim : -1; }
+
+int dmrg_heff_flops(dmrg_heff_t h, int64_t* flops) {
+    if (!h || !flops) return dmrg::fail(DMRG_ERR_INVALID_ARG, "null argument");
+    *flops = static_cast<Handle*>(h)->plan.flops;
+    return DMRG_OK;
+}
+
+int dmrg_heff_plan_dump(dmrg_heff_t h, int64_t* buf, int64_t* n_rows) {
+    if (!h || !n_rows) return dmrg::fail(DMRG_ERR_INVALID_ARG, "null argument");
+    const auto& c = static_cast<Handle*>(h)->plan.canon;
+    const int64_t rows = int64_t(c.size() / 5);
+    if (buf) {
+        if (*n_rows < rows) return dmrg::fail(DMRG_ERR_INVALID_ARG, "plan buffer too small");
+        std::memcpy(buf, c.data(), sizeof(int64_t) * c.size());
+    }
+    *n_rows = rows;
+    return DMRG_OK;
+}
+
+int dmrg_heff_apply(dmrg_heff_t h, const double* x, double* y, int32_t nvec, void* stream) {
+    if (!h) return dmrg::fail(DMRG_ERR_INVALID_ARG, "null handle");
+    return static_cast<Handle*>(h)->apply(x, y, nvec, static_cast<cudaStream_t>(stream));
+}
+
+int dmrg_heff_apply_host(dmrg_heff_t hh, const double* x, double* y, int32_t nvec) {
+    if (!hh) return dmrg::fail(DMRG_ERR_INVALID_ARG, "null handle");
+    Handle* h = static_cast<Handle*>(hh);
+    if (h->plan_only) return dmrg::fail(DMRG_ERR_INVALID_ARG, "plan-only handle");
+    if (nvec < 1 || nvec > h->max_nvec) return dmrg::fail(DMRG_ERR_INVALID_ARG, "nvec outside [1, max_nvec]");
+    const size_t bytes = sizeof(double) * h->plan.dim * nvec;
+    if (bytes == 0) return DMRG_OK;
+    if (!x || !y) return dmrg::fail(DMRG_ERR_INVALID_ARG, "null x or y");
+    int rc;
+    if (!h->d_xstage) {
+        const size_t full = sizeof(double) * h->plan.dim * h->max_nvec;
+        if ((rc = dmrg::dalloc(reinterpret_cast<void**>(&h->d_xstage), full, "x staging")) != DMRG_OK) return rc;
+        if ((rc = dmrg::dalloc(reinterpret_cast<void**>(&h->d_ystage), full, "y staging")) != DMRG_OK) return rc;
+    }
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaMemcpyAsync(h->d_xstage, x, bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return dmrg::cuda_fail(e, "copy x to device");
+    if ((rc = h->apply(h->d_xstage, h->d_ystage, nvec, st)) != DMRG_OK) return rc;
+    e = cudaMemcpyAsync(y, h->d_ystage, bytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return dmrg::cuda_fail(e, "copy y to host");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return dmrg::cuda_fail(e, "apply_host synchronize");
+    return DMRG_OK;
+}
+
+int dmrg_heff_diagonal(dmrg_heff_t h, double* diag, void* stream) {
+    if (!h) return dmrg::fail(DMRG_ERR_INVALID_ARG, "null handle");
+    return static_cast<Handle*>(h)->diagonal(diag, static_cast<cudaStream_t>(stream));
+}
+
+void dmrg_heff_destroy(dmrg_heff_t h) { delete static_cast<Handle*>(h); }
+
+const char* dmrg_strerror(int code) {
+    switch (code) {
+        case DMRG_OK: return "ok";
+        case DMRG_ERR_INVALID_ARG: return "invalid argument";
+        case DMRG_ERR_SECTOR_MISMATCH: return "sector mismatch";
+        case DMRG_ERR_OOM: return "out of memory";
+        case DMRG_ERR_CUDA: return "CUDA error";
+        case DMRG_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+        case DMRG_ERR_NOT_CONVERGED: return "not converged";
+        case DMRG_ERR_BOUNDS: return "out-of-bounds access detected";
+        case DMRG_ERR_UNSUPPORTED: return "unsupported option";
+        default: return "unknown error code";
+    }
+}
+
+const char* dmrg_last_error(void) { return dmrg::g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// Diagonal of H_eff, the Davidson preconditioner's input: only Delta = 0 terms
+// have diagonal entries, diag[(l, r)] = sum_t c_t s_t A_t[l, l] B_t[r, r].
+#include <vector>
+
+#include "../../include/dmrg_heff.h"
+#include "handle.h"
+
+namespace dmrg {
+namespace {
+
+// One CTA per diagonal job; jobs of one block are accumulated in job order by the
+// same CTA (jobs are grouped per block and a block is owned by one CTA).
+__global__ void k_diag(const DiagJob* __restrict__ jobs, const int32_t* __restrict__ first,
+                       const double* __restrict__ ops, double* __restrict__ diag) {
+    const int32_t j0 = first[blockIdx.x], j1 = first[blockIdx.x + 1];
+    if (j0 == j1) return;
+    const DiagJob J0 = jobs[j0];
+    for (int64_t e = threadIdx.x; e < int64_t(J0.rows) * J0.cols; e += blockDim.x) {
+        const int i = int(e / J0.cols), j = int(e % J0.cols);
+        double s = 0.0;
+        for (int32_t q = j0; q < j1; ++q) {
+            const DiagJob J = jobs[q];
+            double g = 0.0;
+            for (int t = 0; t < J.n; ++t)
+                g += ops[J.a_stack + int64_t(t) * J.rows * J.rows + int64_t(i) * J.rows + i] *
+                     ops[J.b_stack + int64_t(t) * J.cols * J.cols + int64_t(j) * J.cols + j];
+            s += J.sign * g;
+        }
+        diag[J0.off + e] = s;
+    }
+}
+
+}  // namespace
+
+int Handle::init_diag() {
+    std::vector<DiagJob> jobs;
+    std::vector<int32_t> first(1, 0);
+    std::vector<std::vector<int32_t>> per_block(plan.blocks.size());
+    for (int32_t g = 0; g < int32_t(plan.groups.size()); ++g) {
+        const Group& G = plan.groups[g];
+        if (G.dn == 0 && G.d2sz == 0) per_block[G.in_block].push_back(g);
+    }
+    for (size_t k = 0; k < plan.blocks.size(); ++k) {
+        for (int32_t g : per_block[k]) {
+            const Group& G = plan.groups[g];
+            jobs.push_back({G.a_stack, G.b_stack, plan.blocks[k].off, int32_t(G.terms.size()), G.a, G.c, 0,
+                            G.sign});
+        }
+        first.push_back(int32_t(jobs.size()));
+    }
+    n_diag_jobs = int32_t(jobs.size());
+    const size_t bytes = sizeof(DiagJob) * jobs.size() + sizeof(int32_t) * first.size();
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&d_diag_jobs), bytes + 16);
+    if (e != cudaSuccess) return cuda_fail(e, "diag jobs");
+    e = cudaMemcpy(d_diag_jobs, jobs.data(), sizeof(DiagJob) * jobs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(reinterpret_cast<char*>(d_diag_jobs) + sizeof(DiagJob) * jobs.size(), first.data(),
+                       sizeof(int32_t) * first.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "diag jobs");
+    return DMRG_OK;
+}
+
+int Handle::diagonal(double* diag, cudaStream_t st) {
+    if (plan_only) return fail(DMRG_ERR_INVALID_ARG, "plan-only handle");
+    if (plan.dim == 0) return DMRG_OK;
+    if (!diag) return fail(DMRG_ERR_INVALID_ARG, "null diag");
+    cudaError_t e = cudaMemsetAsync(diag, 0, sizeof(double) * plan.dim, st);
+    if (e != cudaSuccess) return cuda_fail(e, "zero diag");
+    if (plan.blocks.empty()) return DMRG_OK;
+    const int32_t* first = reinterpret_cast<const int32_t*>(
+        reinterpret_cast<const char*>(d_diag_jobs) + sizeof(DiagJob) * n_diag_jobs);
+    k_diag<<<int(plan.blocks.size()), 256, 0, st>>>(d_diag_jobs, first, d_ops, diag);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "diag kernel");
+    return DMRG_OK;
+}
+
+}  // namespace dmrg

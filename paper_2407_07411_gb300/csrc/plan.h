@@ -1,0 +1,102 @@
+// Host-side planner of the two-site H_eff*psi: sector indexing, contraction-order
+// choice and the grouped-GEMM work lists that the kernels walk.
+//
+// Grouping.  All terms with the same shift Delta and parity flag that touch the same
+// wave-function block q have identical block shapes (a, b, c, d) and therefore the
+// same cheaper contraction order.  Such a group g runs as
+//   A-first:  X_g  = s_g [c_t A_t]_t (stacked rows, n_g*a x b) * x_q (b x c)
+//             Y_O += sum_t X_{g,t} (a x c) * B_t^T (c x d)      (K = n_g*c)
+//   B-first:  Z_g^T = s_g [B_t]_t (stacked rows, n_g*d x c) * x_q^T (c x b)
+//             Y_O += sum_t c_t A_t (a x b) * Z_{g,t} (b x d)    (K = n_g*b)
+// so stage 1 is one tall GEMM per group and stage 2 one long-K GEMM per output block
+// (all groups that land on it), reduced in a fixed order without atomics.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace dmrg {
+
+// Address spaces a descriptor offset refers to.
+enum Space : int32_t { SP_OPS = 0, SP_X = 1, SP_SCR = 2, SP_Y = 3, SP_PART = 4 };
+
+// One K-run of a GEMM: nt sub-blocks of kc columns each.  For sub-block t and
+// column k (global K index = kbase + t*kc + k):
+//   L(i, K) = L[l_off + t*l_ts + i*l_ld + k]
+//   R(K, n) = R[r_off + t*r_ts + k*r_ld + n]   (r_trans = 0)
+//           = R[r_off + t*r_ts + n*r_ld + k]   (r_trans = 1)
+struct Seg {
+    int64_t l_off, r_off, l_ts, r_ts;
+    int32_t l_space, r_space, l_ld, r_ld;
+    int32_t kc, nt, r_trans, pad;
+};
+
+// D (M x N, row stride ldd) = alpha * sum over segs [seg0, seg0+nseg) of L*R.
+struct Gemm {
+    int64_t d_off, K;
+    int32_t d_space, ldd, M, N;
+    int32_t seg0, nseg;
+    double alpha;
+};
+
+// One output tile of one GEMM over the K range [k0, k1).  slot < 0: the tile
+// stores alpha*acc into D; slot >= 0: it stores acc into partial slot `slot`.
+struct Tile {
+    int64_t k0, k1;
+    int32_t gemm, m0, n0, slot;
+};
+
+// D tile = alpha * sum of partial slots [p0, p0+np) in slot order.
+struct Reduce {
+    int32_t gemm, m0, n0, p0, np, pad;
+};
+
+struct PsiBlock { int32_t iL, iR, rows, cols; int64_t off; };
+
+struct Group {
+    int32_t dn, d2sz, parity;
+    int32_t in_block, out_block;
+    int32_t order;          // 0 = A-first, 1 = B-first
+    int32_t a, b, c, d;
+    double sign;            // (-1)^{n_L(in)} for parity groups, else 1
+    std::vector<int32_t> terms;
+    int64_t a_stack, b_stack;  // offsets of the stacked operator copies (device ops)
+    int64_t scratch;           // offset of X_g or Z_g^T in the per-vector scratch
+};
+
+struct Plan {
+    std::vector<int32_t> left, right;   // (n, two_sz, dim) triples
+    int32_t nl = 0, nr = 0, tn = 0, t2sz = 0;
+    std::vector<PsiBlock> blocks;
+    int64_t dim = 0;
+    std::vector<int64_t> canon;         // 5 int64 per item, canonical order
+    int64_t flops = 0;                  // algorithmic flops per vector
+    std::vector<Group> groups;
+    int64_t ops_len = 0;                // doubles in the device operator copy
+    int64_t scratch_len = 0;            // doubles of stage-1 intermediates per vector
+    // FP64 grouped-GEMM work lists
+    std::vector<Seg> segs;
+    std::vector<Gemm> gemms;
+    std::vector<Tile> tiles1, tiles2;
+    std::vector<Reduce> reduces;
+    int64_t n_slots = 0;                // partial slots per vector
+    int64_t diag_terms = 0;
+};
+
+// Tile shape of the FP64 kernels.
+constexpr int FP64_BM = 32, FP64_BN = 32, FP64_BK = 16;
+// Stage-2 K range per work item (multiple of FP64_BK).
+constexpr int64_t FP64_KCHUNK = 512;
+
+// Validates the inputs and builds the plan; returns 0 or a DMRG_ERR_* code with
+// a message in *err.
+int build_plan(const int32_t* left, int32_t nl, const int32_t* right, int32_t nr,
+               int32_t tn, int32_t t2sz, const double* coef, const int32_t* delta,
+               const int32_t* parity, const int64_t* a_off, const int64_t* b_off,
+               int64_t T, int64_t op_len, Plan& P, std::string* err);
+
+// Fills the device operator layout (host staging buffer of P.ops_len doubles).
+void fill_ops(const Plan& P, const double* coef, const int64_t* a_off, const int64_t* b_off,
+              const double* op_data, double* ops);
+
+}  // namespace dmrg
