@@ -30,7 +30,10 @@ UNIT = "TFLOP/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes per launch of the dominant kernel from one ncu capture, keyed by the
 # sha256 of the kernel source it was taken on (a changed kernel reports null).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # k_fp64_tiles, mid workload: (280.8 + 358.1) / 2 MB per launch (profiles/fp64_tiles_mid.md)
+    "7ea6b95187a63352e09b039a09918be5e89d2a14561ebf2f4d93d0eae118ec22": 319.5e6,
+}
 
 
 def parse():

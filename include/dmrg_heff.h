@@ -73,12 +73,18 @@ typedef struct {
 #define DMRG_FLAG_PLAN_ONLY 1
 
 typedef struct {
-    int32_t iters;       /* Rayleigh-Ritz steps taken                               */
+    /* outputs */
+    int32_t iters;       /* Rayleigh-Ritz steps taken                                */
     int32_t matvecs;     /* vectors multiplied by H_eff                              */
     int32_t converged;   /* 1 if every wanted residual norm <= tol                   */
-    int32_t restarts;    /* thick restarts taken                                      */
+    int32_t restarts;    /* thick restarts taken                                     */
     double  resid_max;   /* largest residual norm of the wanted pairs at exit        */
     double  seconds;     /* wall time inside dmrg_davidson                           */
+    /* optional inputs: per-step history (host arrays of hist_cap entries, or NULL)  */
+    double* hist_theta;  /* lowest Ritz value after step i                           */
+    double* hist_time;   /* seconds since the call started, at the end of step i     */
+    int32_t hist_cap;
+    int32_t pad;
 } dmrg_davidson_info;
 
 /* Build a handle: validate the tables, index the wave-function blocks, plan every
@@ -126,12 +132,14 @@ int dmrg_heff_diagonal(dmrg_heff_t h, double* diag, void* stream);
 /* Lowest k_eig eigenpairs by block Davidson with FP64 CGS2 orthogonalisation,
  * Rayleigh-Ritz by cyclic Jacobi on the device, diagonal preconditioner and thick
  * restart; the steps are those of the library's documented Davidson variant.
- *   block      : vectors added per step (1 <= block <= max_nvec)
+ *   block      : vectors added per step (1 <= block <= min(8, max_nvec)); the basis
+ *                holds max(8 block, 24) vectors and must fit k_eig + 2 block
  *   tol        : residual-norm target ||H x - theta x|| for unit x
  *   max_iter   : Rayleigh-Ritz steps allowed
  *   n_iter     : > 0 runs exactly this many steps (no convergence test), else 0
- *   x_inout    : device, block*dim doubles: start block in (need not be orthonormal);
- *                the first k_eig rows hold the Ritz vectors on return
+ *   x_inout    : device, max(block, k_eig)*dim doubles: the first `block` rows are the
+ *                start block (need not be orthonormal); on return the first k_eig rows
+ *                hold the Ritz vectors
  *   evals      : host, k_eig doubles; info: host, may be NULL.
  * Returns DMRG_ERR_NOT_CONVERGED (results still written) when tol was not met. */
 int dmrg_davidson(dmrg_heff_t h, int32_t k_eig, double tol, int32_t max_iter, int32_t block,

@@ -40,7 +40,9 @@ class Opts(ctypes.Structure):
 class DavidsonInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("matvecs", ctypes.c_int32),
                 ("converged", ctypes.c_int32), ("restarts", ctypes.c_int32),
-                ("resid_max", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("resid_max", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("hist_theta", ctypes.c_void_p), ("hist_time", ctypes.c_void_p),
+                ("hist_cap", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class KernelStat(ctypes.Structure):
@@ -214,19 +216,26 @@ class HEff:
 
     def davidson(self, x0, k_eig: int = 1, tol: float = 1e-8, max_iter: int = 300, block: int | None = None,
                  n_iter: int = 0):
-        """Lowest k_eig eigenpairs.  x0: CUDA float64 tensor (block, dim), the start
-        block, overwritten with the Ritz vectors in its first k_eig rows.
+        """Lowest k_eig eigenpairs.  x0: CUDA float64 tensor with max(block, k_eig)
+        rows of length dim; its first `block` rows are the start block, and its
+        first k_eig rows are overwritten with the Ritz vectors.
         Returns (evals ndarray, info dict); info['converged'] is False when tol
         was not met within max_iter."""
         block = block or (x0.shape[0] if x0.dim() == 2 else 1)
         ev = np.zeros(max(k_eig, 1), np.float64)
+        cap = max(max_iter, n_iter, 1)
+        th = np.full(cap, np.nan)
+        tm = np.full(cap, np.nan)
         info = DavidsonInfo()
+        info.hist_theta, info.hist_time, info.hist_cap = th.ctypes.data, tm.ctypes.data, cap
         rc = _lib.dmrg_davidson(self._h, k_eig, tol, max_iter, block, n_iter,
-                                _dev_ptr(x0, block * self.dim, "x0"), _ptr(ev), ctypes.byref(info))
+                                _dev_ptr(x0, max(block, k_eig) * self.dim, "x0"), _ptr(ev), ctypes.byref(info))
         if rc not in (0, ERR_NOT_CONVERGED):
             raise DmrgError(rc)
-        return ev[:k_eig], dict(iters=info.iters, matvecs=info.matvecs, converged=bool(info.converged),
-                                restarts=info.restarts, resid_max=info.resid_max, seconds=info.seconds)
+        n = info.iters
+        return ev[:k_eig], dict(iters=n, matvecs=info.matvecs, converged=bool(info.converged),
+                                restarts=info.restarts, resid_max=info.resid_max, seconds=info.seconds,
+                                theta=th[:n].copy(), time=tm[:n].copy())
 
 
 def probe_fp64_peak() -> float:
