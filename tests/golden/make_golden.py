@@ -1,5 +1,6 @@
 """Writes tests/golden/synth_digests.json: structure digests of the seeded
-workloads and their oracle plan flop totals.  Calls only dmrg_synth and
+workloads, their oracle plan flop totals and the oracle ground-state energy of
+the mid workload.  Calls only dmrg_synth and
 oracle; run from the repository root:  python tests/golden/make_golden.py"""
 import json
 import os
@@ -9,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 sys.path.insert(0, ROOT)
 
 import dmrg_synth as S  # noqa: E402
-from oracle import heff  # noqa: E402
+from oracle import davidson, heff  # noqa: E402
 
 out = {}
 for name in ("tiny", "mid"):
@@ -18,5 +19,13 @@ for name in ("tiny", "mid"):
     out[name] = dict(structure_sha256=p.structure_digest(), dim=p.dim, n_terms=p.n_terms,
                      op_len=int(p.op_data.size), plan_items=int(len(plan)),
                      plan_flops=int(plan[:, 4].sum()))
+    if name == "mid":
+        # converged lowest eigenvalue (residual <= 1e-10, so the eigenvalue error is
+        # ~||r||^2 / gap, far below 1e-12 relative)
+        r = davidson.davidson(lambda V: heff.apply(p, V), heff.diagonal(p), p.random_vectors(1),
+                              tol=1e-10, max_iter=600)
+        assert r["converged"]
+        out[name]["e0"] = float(r["evals"][0])
+        out[name]["e0_residual"] = float(r["resid"][0])
 json.dump(out, open(os.path.join(ROOT, "tests", "golden", "synth_digests.json"), "w"), indent=1)
 print(json.dumps(out, indent=1))
