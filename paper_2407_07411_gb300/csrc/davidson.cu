@@ -435,6 +435,7 @@ extern "C" int dmrg_davidson(dmrg_heff_t hh, int32_t k_eig, double tol, int32_t 
     const int k = k_eig < kb ? k_eig : kb;
     if ((rc = run.check(cudaMemcpy(x_inout, s->X, sizeof(double) * k * dim, cudaMemcpyDeviceToDevice), "x out"))) return rc;
     if ((rc = run.check(cudaDeviceSynchronize(), "davidson"))) return rc;
+    if ((rc = h->check_status())) return rc;
     double rmax = 0.0;
     for (int j = 0; j < k; ++j) {
         evals[j] = th[j];

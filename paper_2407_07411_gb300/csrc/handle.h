@@ -55,6 +55,7 @@ struct Handle : dmrg_heff {
     int precision = 0, max_nvec = 1, n_slices = 0;
     int device = 0, n_sm = 152, tiles_per_sm = 8;
     bool plan_only = false;
+    int64_t split_host_bytes = 0;   // plan-only split handles: device bytes the plan needs
     double* d_ops = nullptr;
     double* d_scr = nullptr;
     double* d_part = nullptr;
@@ -84,6 +85,8 @@ struct Handle : dmrg_heff {
     int init_split(const double* coef, const int64_t* a_off, const int64_t* b_off, const double* op_data);
     int apply_split(const double* x, double* y, int32_t nvec, cudaStream_t st);
     void release_split();
+    // reads and clears the device status word of the split kernels (synchronises)
+    int check_status();
     // Davidson (davidson.cu)
     void release_davidson();
 };

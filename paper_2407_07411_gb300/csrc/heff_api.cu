@@ -12,6 +12,7 @@
 #include "../../include/dmrg_heff.h"
 #include "handle.h"
 #include "kernels.h"
+#include "split.h"
 
 namespace dmrg {
 
@@ -145,6 +146,15 @@ int dmrg_heff_create(const int32_t* left, int32_t nl, const int32_t* right, int3
     h->n_slices = o.n_slices;
     h->plan_only = (o.flags & DMRG_FLAG_PLAN_ONLY) != 0;
     if (h->plan_only) {
+        if (o.precision == DMRG_PREC_SPLIT_BF16) {   // host-side split plan and its bounds proof
+            dmrg::SplitHost sh;
+            rc = dmrg::build_split_plan(h->plan, sh, &err);
+            if (rc != DMRG_OK) {
+                delete h;
+                return dmrg::fail(rc, err);
+            }
+            h->split_host_bytes = sh.op_sl * 2 + sh.ap_sl_vs * 2 + sh.s1_vs * 8 + sh.s2_vs * 8;
+        }
         *out = h;
         return DMRG_OK;
     }
@@ -260,7 +270,7 @@ int dmrg_heff_apply_host(dmrg_heff_t hh, const double* x, double* y, int32_t nve
     if (e != cudaSuccess) return dmrg::cuda_fail(e, "copy y to host");
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return dmrg::cuda_fail(e, "apply_host synchronize");
-    return DMRG_OK;
+    return h->check_status();
 }
 
 int dmrg_heff_diagonal(dmrg_heff_t h, double* diag, void* stream) {

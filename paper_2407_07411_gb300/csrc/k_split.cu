@@ -1,14 +1,861 @@
-// Split-precision (Ozaki) path: placeholder until the slice kernels land.
+// Split-precision (Ozaki) H_eff*psi on the tcgen05 tensor cores (the arithmetic is
+// described in split.h).  Kernels:
+//   k_slice   FP64 or int64 operand vectors -> 5 BF16 digit slices in the UMMA
+//             canonical K-major layout, plus the vector's exponent (integer ops only
+//             for int64 sources).
+//   k_umma    warp-specialised slice GEMM: one producer thread streams 72 KB stages
+//             with cp.async.bulk, one thread issues the 42 tcgen05.mma of each K tile
+//             into five TMEM accumulators, four epilogue warps drain the
+//             exact FP32 sums into int64 every 256 K and store / atomically add.
+//   k_finalize  stage-2 int64 sums -> FP64 wave-function blocks.
+// Every mbarrier wait is bounded; on timeout the CTA records DMRG_ERR_DEVICE_TIMEOUT in
+// the handle's status word, drains its own copies and MMAs and releases TMEM.
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+#include <vector>
+
 #include "../../include/dmrg_heff.h"
 #include "handle.h"
+#include "split.h"
 
 namespace dmrg {
-struct SplitState {};
+
+constexpr int UM_STAGES = 3;
+constexpr int UM_THREADS = 192;       // warp 0 producer, warp 1 MMA, warps 2-5 epilogue
+constexpr int UM_TMEM_COLS = 512;     // 5 accumulators x 64 columns (power-of-two allocation)
+constexpr int UM_TBUF = 1;            // TMEM accumulator sets (drain alternates when 2)
+constexpr uint32_t UM_L_BYTES = SPL_S * SPL_LT * 2;   // 48 KB
+constexpr uint32_t UM_R_BYTES = SPL_S * SPL_RT * 2;   // 24 KB
+constexpr long long UM_WAIT_CYCLES = 4000000000ll;     // ~2 s at 2 GHz
+
+struct UmmaSmem {
+    uint16_t L[UM_STAGES][SPL_S * SPL_LT];
+    uint16_t R[UM_STAGES][SPL_S * SPL_RT];
+    uint64_t full[UM_STAGES], empty[UM_STAGES], tfull[2], tempty[2], done;
+    uint32_t tmem_base;
+    volatile int abort;
+};
+
+struct SplitState {
+    uint16_t* op_sl = nullptr;
+    int32_t* op_ex = nullptr;
+    uint16_t* ap_sl = nullptr;
+    int32_t* ap_ex = nullptr;
+    int64_t* s1 = nullptr;
+    int64_t* s2 = nullptr;
+    SGemm* gemms = nullptr;
+    SWork* work1 = nullptr;
+    SWork* work2 = nullptr;
+    SSeg* segs = nullptr;
+    SJob* jobs = nullptr;
+    SVBlock* vb = nullptr;      // [operator blocks | x blocks | mid blocks]
+    SBlock* blocks = nullptr;
+    SPart* parts = nullptr;
+    int32_t* status = nullptr;
+    int64_t n_work1 = 0, n_work2 = 0, n_vb_op = 0, n_vb_x = 0, n_vb_mid = 0, n_blocks = 0;
+    int64_t ap_sl_vs = 0, ap_ex_vs = 0, s1_vs = 0, s2_vs = 0;
+    int kid_x = -1, kid_s1 = -1, kid_mid = -1, kid_s2 = -1, kid_fin = -1;
+    ~SplitState() {
+        void* p[] = {op_sl, op_ex, ap_sl, ap_ex, s1, s2, gemms, work1, work2, segs, jobs, vb, blocks, parts, status};
+        for (void* q : p)
+            if (q) cudaFree(q);
+    }
+};
+
+namespace {
+
+// ----------------------------------------------------------------------------------
+// slicing
+
+__device__ __forceinline__ int exp_f64(double a) {
+    const uint64_t b = static_cast<uint64_t>(__double_as_longlong(a));
+    const int ex = int((b >> 52) & 0x7FF);
+    return ex == 0 ? INT_MIN : ex - 1022;   // |a| < 2^(ex-1022); zero and subnormal -> none
+}
+
+__device__ __forceinline__ int exp_i64(long long F, int eF) {
+    if (F == 0) return INT_MIN;
+    const unsigned long long u = F < 0 ? static_cast<unsigned long long>(-F) : static_cast<unsigned long long>(F);
+    return (64 - __clzll(u)) + eF;          // |F 2^eF| < 2^(msb+1+eF)
+}
+
+// Balanced base-256 digits of the non-negative integer R <= 2^47, most significant
+// first, with the sign applied.
+__device__ __forceinline__ void balanced_digits(unsigned long long R, bool neg, int (&d)[SPL_S]) {
+#pragma unroll
+    for (int k = SPL_S - 1; k >= 0; --k) {
+        int t = int(R & 255ull);
+        R >>= 8;
+        if (t > 128) {
+            t -= 256;
+            R += 1;
+        }
+        d[k] = neg ? -t : t;
+    }
+}
+
+// R = round(|a| 2^(47 - E)) from the FP64 bit pattern (integer ops only).
+__device__ __forceinline__ void digits_f64(double a, int E, int (&d)[SPL_S]) {
+    const uint64_t b = static_cast<uint64_t>(__double_as_longlong(a));
+    const int ex = int((b >> 52) & 0x7FF);
+    unsigned long long R = 0;
+    if (ex != 0) {
+        const unsigned long long m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+        const int sh = 1028 + E - ex;       // >= 6 because |a| < 2^E
+        R = sh >= 64 ? 0ull : (m + (1ull << (sh - 1))) >> sh;
+    }
+    balanced_digits(R, (b >> 63) != 0, d);
+}
+
+// value = F 2^eF; R = round(|F| 2^(eF + 47 - E)).
+__device__ __forceinline__ void digits_i64(long long F, int eF, int E, int (&d)[SPL_S]) {
+    unsigned long long u = F < 0 ? static_cast<unsigned long long>(-F) : static_cast<unsigned long long>(F);
+    const int sh = E - eF - 47;
+    unsigned long long R;
+    if (sh > 0) R = sh >= 63 ? 0ull : (u + (1ull << (sh - 1))) >> sh;
+    else R = u << (-sh);
+    balanced_digits(R, F < 0, d);
+}
+
+__device__ __forceinline__ uint16_t digit_bf16(int d, int k) {
+    const float f = float(d) * __int_as_float((127 - 8 * k) << 23);   // d * 2^(-8k), exact
+    return uint16_t(__float_as_uint(f) >> 16);
+}
+
+// Position of (vector v, K index K) inside a job's tile array (bf16 elements), slice s.
+__device__ __forceinline__ int64_t tile_pos(const SJob& J, int v, int K, int s) {
+    const int vt = v / J.rows_tile, vr = v % J.rows_tile, kt = K / SPL_TK, kr = K % SPL_TK;
+    const int64_t tile = (int64_t(vt) * J.kt + kt) * SPL_S + s;
+    return J.out_tiles + tile * (int64_t(J.rows_tile) * SPL_TK) + ((vr >> 3) * 4 + (kr >> 3)) * 64 + (vr & 7) * 8 +
+           (kr & 7);
+}
+
+struct SliceArgs {
+    const SVBlock* vb;
+    int64_t n_vb;
+    const SJob* jobs;
+    const SSeg* segs;
+    const double* ops;
+    const double* x;
+    int64_t x_vs;
+    const int64_t* s1;
+    int64_t s1_vs;
+    uint16_t* op_sl;
+    uint16_t* ap_sl;
+    int64_t ap_sl_vs;
+    int32_t* op_ex;
+    int32_t* ap_ex;
+    int64_t ap_ex_vs;
+    int nvec;
+};
+
+__global__ void __launch_bounds__(256) k_slice(SliceArgs a) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t n_items = a.n_vb * a.nvec;
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const SVBlock B = a.vb[item / a.nvec];
+        const int v = int(item % a.nvec);
+        const SJob J = a.jobs[B.job];
+        const int vec = B.v0 + warp;
+        if (vec >= J.npad) continue;
+        const bool valid = vec < J.nvalid;
+        uint16_t* out = (J.out_buf ? a.ap_sl + int64_t(v) * a.ap_sl_vs : a.op_sl);
+        int32_t* oex = (J.out_buf ? a.ap_ex + int64_t(v) * a.ap_ex_vs : a.op_ex);
+        const double* x = a.x + int64_t(v) * a.x_vs;
+        const int64_t* s1 = a.s1 + int64_t(v) * a.s1_vs;
+        const int32_t* cex = a.ap_ex + int64_t(v) * a.ap_ex_vs;   // stage-1 R exponents
+        // pass 1: exponent of the vector
+        int E = INT_MIN;
+        if (valid) {
+            for (int s = J.seg0; s < J.seg0 + J.nseg; ++s) {
+                const SSeg g = a.segs[s];
+                for (int t = 0; t < g.nt; ++t) {
+                    const int64_t base = g.off + t * g.ts + int64_t(vec) * g.vs;
+                    for (int k = lane; k < g.kc; k += 32) {
+                        int e;
+                        if (g.is_i64) {
+                            const int eF = a.op_ex[g.er_off + int64_t(t) * g.er_ts + vec] + cex[g.ec_off + k] - g.e_off;
+                            e = exp_i64(s1[base + k * g.ks], eF);
+                        } else {
+                            e = exp_f64((g.space == SP_OPS ? a.ops : x)[base + k * g.ks]);
+                        }
+                        E = max(E, e);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+        const bool zero = E == INT_MIN;
+        if (lane == 0) oex[J.out_exp + vec] = zero ? 0 : E;
+        // pass 2: digits
+        int K0 = 0;
+        if (valid && !zero) {
+            for (int s = J.seg0; s < J.seg0 + J.nseg; ++s) {
+                const SSeg g = a.segs[s];
+                for (int t = 0; t < g.nt; ++t, K0 += g.kc) {
+                    const int64_t base = g.off + t * g.ts + int64_t(vec) * g.vs;
+                    for (int k = lane; k < g.kc; k += 32) {
+                        int d[SPL_S];
+                        if (g.is_i64) {
+                            const int eF = a.op_ex[g.er_off + int64_t(t) * g.er_ts + vec] + cex[g.ec_off + k] - g.e_off;
+                            digits_i64(s1[base + k * g.ks], eF, E, d);
+                        } else {
+                            digits_f64((g.space == SP_OPS ? a.ops : x)[base + k * g.ks], E, d);
+                        }
+#pragma unroll
+                        for (int q = 0; q < SPL_S; ++q) out[tile_pos(J, vec, K0 + k, q)] = digit_bf16(d[q], q);
+                    }
+                }
+            }
+        }
+        const int Kpad = J.kt * SPL_TK;
+        for (int K = (valid && !zero) ? K0 + lane : lane; K < Kpad; K += 32)
+#pragma unroll
+            for (int q = 0; q < SPL_S; ++q) out[tile_pos(J, vec, K, q)] = 0;
+    }
+}
+
+// ----------------------------------------------------------------------------------
+// tcgen05 slice GEMM
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+// Shared-memory matrix descriptor, K-major without swizzle: 8x8 core matrices of 128
+// contiguous bytes, LBO = 128 B between K-adjacent cores, SBO = 512 B between 8-row groups.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    return uint64_t((addr >> 4) & 0x3FFF) | (uint64_t(128 >> 4) << 16) | (uint64_t(512 >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: BF16 x BF16 -> FP32, both K-major, M=128, N=64.
+constexpr uint32_t UM_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(SPL_TN >> 3) << 17) |
+                              (uint32_t(SPL_TM >> 4) << 24);
+
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t ph) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(ph)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; false on timeout or when another role has aborted.
+__device__ __forceinline__ bool mbar_wait(UmmaSmem& sm, uint64_t* b, uint32_t ph, int* status) {
+    const long long t0 = clock64();
+    while (!mbar_try(b, ph)) {
+        if (sm.abort) return false;
+        if (clock64() - t0 > UM_WAIT_CYCLES) {
+            sm.abort = 1;
+            atomicExch(status, DMRG_ERR_DEVICE_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool mbar_wait_final(uint64_t* b, uint32_t ph) {
+    const long long t0 = clock64();
+    while (!mbar_try(b, ph))
+        if (clock64() - t0 > UM_WAIT_CYCLES) return false;
+    return true;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, int n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     su32(dst)),
+                 "l"(src), "r"(bytes), "r"(su32(b))
+                 : "memory");
+}
+__device__ __forceinline__ void umma(uint32_t d, uint64_t da, uint64_t db, uint32_t accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(da), "l"(db), "r"(UM_IDESC), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* b) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(addr));
+}
+
+struct UmmaArgs {
+    const SWork* work;
+    int64_t n_work;
+    const SGemm* gemms;
+    const uint16_t* op_sl;
+    const uint16_t* ap_sl;
+    int64_t ap_sl_vs;
+    int64_t* s1;
+    int64_t s1_vs;
+    int64_t* s2;
+    int64_t s2_vs;
+    int nvec;
+    int* status;
+};
+
+// Slice pairs (i, j) with i + j <= 5 in issue order, grouped by level i + j; pair 0
+// feeds acc0, pairs 1-2 acc1, 3-5 acc2, 6-9 acc3, 10-20 acc4.
+__constant__ int8_t c_pair_i[SPL_PAIRS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
+__constant__ int8_t c_pair_j[SPL_PAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
+
+__global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    UmmaSmem& sm = *reinterpret_cast<UmmaSmem*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&sm.tmem_base)),
+                     "r"(UM_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < UM_STAGES; ++s) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.empty[s], 1);
+        }
+        for (int b = 0; b < UM_TBUF; ++b) {
+            mbar_init(&sm.tfull[b], 1);
+            mbar_init(&sm.tempty[b], 128);
+        }
+        mbar_init(&sm.done, 1);
+        sm.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem_base;
+    const int64_t total = a.n_work * a.nvec;
+
+    if (warp == 0 && lane == 0) {
+        // ---- producer
+        int64_t kidx = 0;
+        bool ok = true;
+        for (int64_t it = blockIdx.x; it < total && ok; it += gridDim.x) {
+            const SWork W = a.work[it / a.nvec];
+            const int v = int(it % a.nvec);
+            const SGemm G = a.gemms[W.gemm];
+            const uint16_t* Lb = (G.l_buf ? a.ap_sl + int64_t(v) * a.ap_sl_vs : a.op_sl) + G.l_tiles;
+            const uint16_t* Rb = (G.r_buf ? a.ap_sl + int64_t(v) * a.ap_sl_vs : a.op_sl) + G.r_tiles;
+            for (int kt = W.k0; kt < W.k1; ++kt, ++kidx) {
+                const int s = int(kidx % UM_STAGES);
+                const int64_t n = kidx / UM_STAGES;
+                if (n > 0 && !(ok = mbar_wait(sm, &sm.empty[s], uint32_t((n - 1) & 1), a.status))) break;
+                mbar_expect_tx(&sm.full[s], UM_L_BYTES + UM_R_BYTES);
+                bulk_g2s(sm.L[s], Lb + (int64_t(W.mtile) * G.kt + kt) * (SPL_S * SPL_LT), UM_L_BYTES, &sm.full[s]);
+                bulk_g2s(sm.R[s], Rb + (int64_t(W.ntile) * G.kt + kt) * (SPL_S * SPL_RT), UM_R_BYTES, &sm.full[s]);
+            }
+        }
+        // every issued stage must land before the CTA may exit
+        for (int64_t q = kidx - UM_STAGES; q < kidx; ++q)
+            if (q >= 0) mbar_wait_final(&sm.full[q % UM_STAGES], uint32_t((q / UM_STAGES) & 1));
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        int64_t kidx = 0, dchunk = 0;
+        bool ok = true;
+        for (int64_t it = blockIdx.x; it < total && ok; it += gridDim.x) {
+            const SWork W = a.work[it / a.nvec];
+            for (int kc0 = W.k0; kc0 < W.k1 && ok; kc0 += SPL_DRAIN_KT, ++dchunk) {
+                const int b = int(dchunk % UM_TBUF);
+                const int64_t n = dchunk / UM_TBUF;
+                if (n > 0 && !(ok = mbar_wait(sm, &sm.tempty[b], uint32_t((n - 1) & 1), a.status))) break;
+                tc_fence_after();
+                const uint32_t acc = tmem + uint32_t(b) * (SPL_ACCS * SPL_TN);
+                const int kc1 = min(kc0 + SPL_DRAIN_KT, W.k1);
+                for (int kt = kc0; kt < kc1; ++kt, ++kidx) {
+                    const int s = int(kidx % UM_STAGES);
+                    if (!(ok = mbar_wait(sm, &sm.full[s], uint32_t((kidx / UM_STAGES) & 1), a.status))) break;
+                    tc_fence_after();
+                    const uint32_t la = su32(sm.L[s]), ra = su32(sm.R[s]);
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+#pragma unroll
+                        for (int p = 0; p < SPL_PAIRS; ++p) {
+                            const int i = c_pair_i[p], j = c_pair_j[p];
+                            const int which = p == 0 ? 0 : (p < 3 ? 1 : (p < 6 ? 2 : (p < 10 ? 3 : 4)));
+                            const bool first =
+                                kt == kc0 && ks == 0 && (p == 0 || p == 1 || p == 3 || p == 6 || p == 10);
+                            umma(acc + uint32_t(which) * SPL_TN, sdesc(la + i * (SPL_LT * 2) + ks * 256),
+                                 sdesc(ra + j * (SPL_RT * 2) + ks * 256), first ? 0u : 1u);
+                        }
+                    }
+                    umma_commit(&sm.empty[s]);
+                }
+                if (ok) umma_commit(&sm.tfull[b]);
+            }
+        }
+        umma_commit(&sm.done);   // completes when every MMA issued above has finished
+        mbar_wait_final(&sm.done, 0);
+    } else if (warp >= 2) {
+        // ---- epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (tile rows)
+        const int q = warp & 3;
+        const int row = 32 * q + lane;
+        const uint32_t lane_addr = uint32_t(32 * q) << 16;
+        int64_t dchunk = 0;
+        bool ok = true;
+        for (int64_t it = blockIdx.x; it < total && ok; it += gridDim.x) {
+            const SWork W = a.work[it / a.nvec];
+            const int v = int(it % a.nvec);
+            const int fs = a.gemms[W.gemm].fshift;
+            const float scale_f = __int_as_float((127 + fs) << 23);   // 2^fs
+            long long acc[SPL_TN];
+#pragma unroll
+            for (int j = 0; j < SPL_TN; ++j) acc[j] = 0;
+            for (int kc0 = W.k0; kc0 < W.k1; kc0 += SPL_DRAIN_KT, ++dchunk) {
+                const int b = int(dchunk % UM_TBUF);
+                if (!(ok = mbar_wait(sm, &sm.tfull[b], uint32_t((dchunk / UM_TBUF) & 1), a.status))) break;
+                tc_fence_after();
+                const uint32_t base = tmem + lane_addr + uint32_t(b) * (SPL_ACCS * SPL_TN);
+#pragma unroll
+                for (int c0 = 0; c0 < SPL_TN; c0 += 8) {
+                    uint32_t r0[8], r1[8], r2[8], r3[8], r4[8];
+                    tmem_ld8(base + c0, r0);
+                    tmem_ld8(base + SPL_TN + c0, r1);
+                    tmem_ld8(base + 2 * SPL_TN + c0, r2);
+                    tmem_ld8(base + 3 * SPL_TN + c0, r3);
+                    tmem_ld8(base + 4 * SPL_TN + c0, r4);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const long long i0 = __float2int_rn(__uint_as_float(r0[j]));                 // exact
+                        const long long i1 = __float2int_rn(__uint_as_float(r1[j]) * 256.0f);        // exact
+                        const long long i2 = __float2int_rn(__uint_as_float(r2[j]) * 65536.0f);      // exact
+                        const long long i3 = __float2int_rn(__uint_as_float(r3[j]) * 16777216.0f);   // exact
+                        const long long i4 = __float2ll_rn(__uint_as_float(r4[j]) * scale_f);
+                        acc[c0 + j] += (i0 << fs) + (i1 << (fs - 8)) + (i2 << (fs - 16)) + (i3 << (fs - 24)) + i4;
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&sm.tempty[b]);
+            }
+            if (!ok) break;
+            const SGemm G = a.gemms[W.gemm];
+            const int r = W.mtile * SPL_TM + row;
+            if (r < G.M) {
+                if (G.kind == 0) {
+                    int64_t* D = a.s1 + int64_t(v) * a.s1_vs + G.d_off + int64_t(r) * G.ldd;
+#pragma unroll
+                    for (int j = 0; j < SPL_TN; ++j) {
+                        const int c = W.ntile * SPL_TN + j;
+                        if (c < G.N) D[c] = G.sign > 0 ? acc[j] : -acc[j];
+                    }
+                } else {
+                    unsigned long long* D = reinterpret_cast<unsigned long long*>(a.s2 + int64_t(v) * a.s2_vs +
+                                                                                  G.d_off + int64_t(r) * G.ldd);
+#pragma unroll
+                    for (int j = 0; j < SPL_TN; ++j) {
+                        const int c = W.ntile * SPL_TN + j;
+                        if (c < G.N && acc[j] != 0) atomicAdd(D + c, static_cast<unsigned long long>(acc[j]));
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UM_TMEM_COLS));
+    }
+}
+
+// ----------------------------------------------------------------------------------
+// stage-2 sums -> FP64 wave function
+
+__global__ void k_finalize(const SBlock* __restrict__ blocks, const SPart* __restrict__ parts,
+                           const int64_t* __restrict__ s2, int64_t s2_vs, const int32_t* __restrict__ op_ex,
+                           const int32_t* __restrict__ ap_ex, int64_t ap_ex_vs, double* __restrict__ y, int64_t dim) {
+    const SBlock B = blocks[blockIdx.x];
+    const int v = blockIdx.y;
+    const int32_t* aex = ap_ex + int64_t(v) * ap_ex_vs;
+    const int64_t* S2 = s2 + int64_t(v) * s2_vs;
+    for (int e = threadIdx.x; e < B.rows * B.cols; e += blockDim.x) {
+        const int i = e / B.cols, j = e % B.cols;
+        double sum = 0.0;
+        for (int p = B.p0; p < B.p0 + B.np; ++p) {
+            const SPart P = parts[p];
+            const long long F = S2[P.acc_off + e];
+            if (F == 0) continue;
+            const int er = (P.er_buf ? aex : op_ex)[P.er_off + i];
+            const int ec = (P.ec_buf ? aex : op_ex)[P.ec_off + j];
+            sum += scalbn(static_cast<double>(F), er + ec - P.e_off);
+        }
+        y[int64_t(v) * dim + B.y_off + e] = sum;
+    }
+}
+
+}  // namespace
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// s = 47 - ceil(log2 K): |F| <= K 2^14 2^s (1 + 2^-6) < 2^62 for any contraction length
+// (s >= 24 because K <= 2^23, so the shifts s - 8, s - 16, s - 24 of the epilogue are valid).
+int32_t fshift_for(int64_t K) {
+    int c = 0;
+    while ((int64_t(1) << c) < K) ++c;
+    return 47 - c;
+}
+
+// ----------------------------------------------------------------------------------
+// host side
+
+// Host-side bounds proof of a split plan: every bulk-copy source range, slicer write,
+// exponent read/write, stage-1 store and stage-2 sum lies inside its buffer.
+int validate_split_plan(const Plan& P, const SplitHost& H, std::string* err) {
+    auto bad = [&](const char* what) {
+        *err = std::string("split plan out of bounds: ") + what;
+        return DMRG_ERR_BOUNDS;
+    };
+    for (const SJob& J : H.jobs) {
+        const int64_t tiles = int64_t(J.npad / J.rows_tile) * J.kt * SPL_S * J.rows_tile * SPL_TK;
+        const int64_t sl = J.out_buf ? H.ap_sl_vs : H.op_sl;
+        const int64_t ex = J.out_buf ? H.ap_ex_vs : H.op_ex;
+        if (J.npad % J.rows_tile || J.npad < J.nvalid || J.kt * SPL_TK < J.K) return bad("job shape");
+        if (J.out_tiles < 0 || J.out_tiles % 8 || J.out_tiles + tiles > sl) return bad("slice tiles");
+        if (J.out_exp < 0 || J.out_exp + J.npad > ex) return bad("exponents");
+        int64_t K = 0;
+        for (int s = J.seg0; s < J.seg0 + J.nseg; ++s) {
+            const SSeg& g = H.segs[s];
+            K += int64_t(g.kc) * g.nt;
+            if (J.nvalid == 0 || g.kc <= 0 || g.nt <= 0) continue;
+            const int64_t last = g.off + (g.nt - 1) * g.ts + int64_t(J.nvalid - 1) * g.vs + int64_t(g.kc - 1) * g.ks;
+            const int64_t lim = g.space == SP_OPS ? P.ops_len : (g.space == SP_X ? P.dim : P.scratch_len);
+            if (g.off < 0 || last >= lim) return bad("slice source");
+            if (g.is_i64) {
+                if (g.space != SP_SCR) return bad("int64 source space");
+                if (g.er_off < 0 || g.er_off + int64_t(g.nt - 1) * g.er_ts + J.nvalid > H.op_ex) return bad("row exps");
+                if (g.ec_off < 0 || g.ec_off + g.kc > H.ap_ex_vs) return bad("col exps");
+            }
+        }
+        if (K != J.K) return bad("job K");
+    }
+    auto check_work = [&](const std::vector<SWork>& w) {
+        for (const SWork& x : w) {
+            const SGemm& G = H.gemms[x.gemm];
+            if (x.k0 < 0 || x.k1 > G.kt || x.k0 >= x.k1) return false;
+            const int64_t lsz = G.l_buf ? H.ap_sl_vs : H.op_sl, rsz = G.r_buf ? H.ap_sl_vs : H.op_sl;
+            const int64_t lend = G.l_tiles + (int64_t(x.mtile) * G.kt + x.k1) * (SPL_S * SPL_LT);
+            const int64_t rend = G.r_tiles + (int64_t(x.ntile) * G.kt + x.k1) * (SPL_S * SPL_RT);
+            if (G.l_tiles % 8 || G.r_tiles % 8 || lend > lsz || rend > rsz) return false;
+            if (int64_t(x.mtile) * SPL_TM >= G.M || int64_t(x.ntile) * SPL_TN >= G.N) return false;
+            const int64_t dend = G.d_off + int64_t(G.M - 1) * G.ldd + G.N;
+            if (G.ldd < G.N || dend > (G.kind == 0 ? H.s1_vs : H.s2_vs)) return false;
+        }
+        return true;
+    };
+    if (!check_work(H.w1) || !check_work(H.w2)) return bad("gemm work");
+    for (const SBlock& B : H.blocks)
+        for (int p = B.p0; p < B.p0 + B.np; ++p) {
+            const SPart& Q = H.parts[p];
+            if (Q.acc_off + int64_t(B.rows) * B.cols > H.s2_vs) return bad("finalize sums");
+            if (Q.er_off + B.rows > (Q.er_buf ? H.ap_ex_vs : H.op_ex)) return bad("finalize row exps");
+            if (Q.ec_off + B.cols > (Q.ec_buf ? H.ap_ex_vs : H.op_ex)) return bad("finalize col exps");
+        }
+    return DMRG_OK;
+}
+
+int build_split_plan(const Plan& P, SplitHost& H, std::string* err) {
+    std::vector<SGemm>& gemms = H.gemms;
+    std::vector<SSeg>& segs = H.segs;
+    std::vector<SJob>& jobs = H.jobs;
+    std::vector<int32_t> op_jobs, x_jobs, mid_jobs;
+    std::vector<SWork>& w1 = H.w1;
+    std::vector<SWork>& w2 = H.w2;
+    std::vector<SBlock>& blocks = H.blocks;
+    blocks.assign(P.blocks.size(), SBlock{});
+    std::vector<SPart>& parts = H.parts;
+    int64_t op_sl = 0, op_ex = 0, ap_sl = 0, ap_ex = 0, s2 = 0;
+
+    auto add_job = [&](int out_buf, int rows_tile, int nvalid, int64_t K, const std::vector<SSeg>& js,
+                       int64_t* tiles_off, int64_t* exp_off) {
+        SJob J{};
+        J.out_buf = out_buf;
+        J.rows_tile = rows_tile;
+        J.nvalid = nvalid;
+        J.npad = int32_t(cdiv(nvalid, rows_tile) * rows_tile);
+        J.K = int32_t(K);
+        J.kt = int32_t(cdiv(K, SPL_TK));
+        J.seg0 = int32_t(segs.size());
+        J.nseg = int32_t(js.size());
+        segs.insert(segs.end(), js.begin(), js.end());
+        int64_t& sl = out_buf ? ap_sl : op_sl;
+        int64_t& ex = out_buf ? ap_ex : op_ex;
+        J.out_tiles = sl;
+        J.out_exp = ex;
+        sl += int64_t(J.npad) * J.kt * SPL_TK * SPL_S;
+        ex += J.npad;
+        *tiles_off = J.out_tiles;
+        *exp_off = J.out_exp;
+        jobs.push_back(J);
+        return int32_t(jobs.size() - 1);
+    };
+    auto seg = [](int space, int64_t off, int64_t ts, int64_t vs, int64_t ks, int kc, int nt) {
+        SSeg s{};
+        s.space = space; s.off = off; s.ts = ts; s.vs = vs; s.ks = ks; s.kc = kc; s.nt = nt;
+        return s;
+    };
+    if (int64_t(P.groups.size()) > (int64_t(1) << 30)) {
+        *err = "too many groups";
+        return DMRG_ERR_INVALID_ARG;
+    }
+
+    // stage 1: one GEMM per group; L = stacked operator (operator slices), R = x block
+    std::vector<int64_t> s1_lexp(P.groups.size()), s1_rexp(P.groups.size());
+    std::vector<int32_t> s1_eoff(P.groups.size());
+    for (size_t g = 0; g < P.groups.size(); ++g) {
+        const Group& G = P.groups[g];
+        const PsiBlock& B = P.blocks[G.in_block];
+        const int n = int(G.terms.size());
+        SGemm m{};
+        int64_t lt, le, rt, re;
+        if (G.order == 0) {   // X_g = A_stack (n a x b) * x_q (b x c)
+            m.M = n * G.a; m.N = G.c;
+            op_jobs.push_back(add_job(0, SPL_TM, m.M, G.b, {seg(SP_OPS, G.a_stack, 0, G.b, 1, G.b, 1)}, &lt, &le));
+            x_jobs.push_back(add_job(1, SPL_TN, m.N, G.b, {seg(SP_X, B.off, 0, 1, G.c, G.b, 1)}, &rt, &re));
+        } else {              // Z_g^T = B_stack (n d x c) * x_q^T (c x b)
+            m.M = n * G.d; m.N = G.b;
+            op_jobs.push_back(add_job(0, SPL_TM, m.M, G.c, {seg(SP_OPS, G.b_stack, 0, G.c, 1, G.c, 1)}, &lt, &le));
+            x_jobs.push_back(add_job(1, SPL_TN, m.N, G.c, {seg(SP_X, B.off, 0, G.c, 1, G.c, 1)}, &rt, &re));
+        }
+        m.l_tiles = lt; m.r_tiles = rt; m.l_buf = 0; m.r_buf = 1;
+        m.kt = int32_t(cdiv(G.order == 0 ? G.b : G.c, SPL_TK));
+        m.d_off = G.scratch; m.ldd = m.N; m.kind = 0; m.sign = G.sign < 0 ? -1 : 1;
+        m.fshift = fshift_for(G.order == 0 ? G.b : G.c);
+        s1_lexp[g] = le; s1_rexp[g] = re; s1_eoff[g] = 14 + m.fshift;
+        const int32_t gi = int32_t(gemms.size());
+        gemms.push_back(m);
+        for (int mt = 0; mt < cdiv(m.M, SPL_TM); ++mt)
+            for (int nt = 0; nt < cdiv(m.N, SPL_TN); ++nt) w1.push_back({gi, mt, nt, 0, m.kt, 0});
+    }
+    // stage 2: per output block, one GEMM over its A-first groups and one over its B-first groups
+    std::vector<std::vector<int32_t>> by_out(P.blocks.size());
+    for (int32_t g = 0; g < int32_t(P.groups.size()); ++g) by_out[P.groups[g].out_block].push_back(g);
+    for (size_t o = 0; o < P.blocks.size(); ++o) {
+        const PsiBlock& O = P.blocks[o];
+        blocks[o] = {O.off, O.rows, O.cols, int32_t(parts.size()), 0};
+        for (int order = 0; order < 2; ++order) {
+            std::vector<SSeg> lseg, rseg;
+            int64_t K = 0;
+            for (int32_t g : by_out[o]) {
+                const Group& G = P.groups[g];
+                if (G.order != order) continue;
+                const int n = int(G.terms.size());
+                if (order == 0) {  // L = X_g rows (int64), R = B_t rows (operator)
+                    SSeg s = seg(SP_SCR, G.scratch, int64_t(G.a) * G.c, G.c, 1, G.c, n);
+                    s.is_i64 = 1; s.er_off = s1_lexp[g]; s.er_ts = G.a; s.ec_off = s1_rexp[g]; s.e_off = s1_eoff[g];
+                    lseg.push_back(s);
+                    rseg.push_back(seg(SP_OPS, G.b_stack, int64_t(G.d) * G.c, G.c, 1, G.c, n));
+                    K += int64_t(G.c) * n;
+                } else {           // L = c_t A_t rows (operator), R = Z_g^T rows (int64)
+                    lseg.push_back(seg(SP_OPS, G.a_stack, int64_t(G.a) * G.b, G.b, 1, G.b, n));
+                    SSeg s = seg(SP_SCR, G.scratch, int64_t(G.d) * G.b, G.b, 1, G.b, n);
+                    s.is_i64 = 1; s.er_off = s1_lexp[g]; s.er_ts = G.d; s.ec_off = s1_rexp[g]; s.e_off = s1_eoff[g];
+                    rseg.push_back(s);
+                    K += int64_t(G.b) * n;
+                }
+            }
+            if (lseg.empty()) continue;
+            if (K > SPL_MAX_K) {
+                *err = "stage-2 contraction longer than 2^23";
+                return DMRG_ERR_INVALID_ARG;
+            }
+            SGemm m{};
+            m.M = O.rows; m.N = O.cols; m.kt = int32_t(cdiv(K, SPL_TK));
+            int64_t lt, le, rt, re;
+            const int lbuf = order == 0 ? 1 : 0, rbuf = order == 0 ? 0 : 1;
+            int32_t lj = add_job(lbuf, SPL_TM, m.M, K, lseg, &lt, &le);
+            int32_t rj = add_job(rbuf, SPL_TN, m.N, K, rseg, &rt, &re);
+            (lbuf ? mid_jobs : op_jobs).push_back(lj);
+            (rbuf ? mid_jobs : op_jobs).push_back(rj);
+            m.l_tiles = lt; m.r_tiles = rt; m.l_buf = lbuf; m.r_buf = rbuf;
+            m.d_off = s2; m.ldd = m.N; m.kind = 1; m.sign = 1;
+            m.fshift = fshift_for(K);
+            parts.push_back({s2, le, re, lbuf, rbuf, 14 + m.fshift, 0});
+            blocks[o].np += 1;
+            s2 += int64_t(m.M) * m.N;
+            const int32_t gi = int32_t(gemms.size());
+            gemms.push_back(m);
+            for (int mt = 0; mt < cdiv(m.M, SPL_TM); ++mt)
+                for (int nt = 0; nt < cdiv(m.N, SPL_TN); ++nt)
+                    for (int k0 = 0; k0 < m.kt; k0 += SPL_S2_KCHUNK)
+                        w2.push_back({gi, mt, nt, k0, std::min(m.kt, k0 + SPL_S2_KCHUNK), 0});
+        }
+    }
+    auto by_cost = [](const SWork& x, const SWork& y) { return (x.k1 - x.k0) > (y.k1 - y.k0); };
+    std::stable_sort(w1.begin(), w1.end(), by_cost);
+    std::stable_sort(w2.begin(), w2.end(), by_cost);
+    std::vector<SVBlock>& vb = H.vb;
+    auto add_vb = [&](const std::vector<int32_t>& js) {
+        for (int32_t j : js)
+            for (int v0 = 0; v0 < jobs[j].npad; v0 += 8) vb.push_back({j, v0});
+    };
+    add_vb(op_jobs);
+    H.n_vb_op = int64_t(vb.size());
+    add_vb(x_jobs);
+    H.n_vb_x = int64_t(vb.size()) - H.n_vb_op;
+    add_vb(mid_jobs);
+    H.n_vb_mid = int64_t(vb.size()) - H.n_vb_op - H.n_vb_x;
+    H.op_sl = op_sl;
+    H.op_ex = op_ex + 1;
+    H.ap_sl_vs = cdiv(ap_sl, 64) * 64;
+    H.ap_ex_vs = cdiv(ap_ex, 4) * 4 + 4;
+    H.s1_vs = P.scratch_len;
+    H.s2_vs = s2;
+    return validate_split_plan(P, H, err);
+}
+
 int Handle::init_split(const double*, const int64_t*, const int64_t*, const double*) {
-    return fail(DMRG_ERR_UNSUPPORTED, "split precision not built yet");
+    const Plan& P = plan;
+    SplitState* S = new SplitState();
+    split = S;
+    SplitHost H;
+    std::string err;
+    int rc0 = build_split_plan(P, H, &err);
+    if (rc0 != DMRG_OK) return fail(rc0, err);
+    const std::vector<SGemm>& gemms = H.gemms;
+    const std::vector<SSeg>& segs = H.segs;
+    const std::vector<SJob>& jobs = H.jobs;
+    const std::vector<SWork>& w1 = H.w1;
+    const std::vector<SWork>& w2 = H.w2;
+    const std::vector<SBlock>& blocks = H.blocks;
+    const std::vector<SPart>& parts = H.parts;
+    const std::vector<SVBlock>& vb = H.vb;
+    const int64_t op_sl = H.op_sl, op_ex = H.op_ex;
+    S->n_vb_op = H.n_vb_op;
+    S->n_vb_x = H.n_vb_x;
+    S->n_vb_mid = H.n_vb_mid;
+    S->n_work1 = int64_t(w1.size());
+    S->n_work2 = int64_t(w2.size());
+    S->n_blocks = int64_t(blocks.size());
+    S->ap_sl_vs = H.ap_sl_vs;
+    S->ap_ex_vs = H.ap_ex_vs;
+    S->s1_vs = H.s1_vs;
+    S->s2_vs = H.s2_vs;
+
+    // device buffers
+    const size_t nv = size_t(max_nvec);
+    auto al = [&](void** p, size_t bytes, const char* w) {
+        *p = nullptr;
+        if (bytes == 0) return DMRG_OK;
+        cudaError_t e = cudaMalloc(p, bytes);
+        return e == cudaSuccess ? DMRG_OK : cuda_fail(e, w);
+    };
+    auto up = [&](void** p, const void* src, size_t bytes, const char* w) {
+        int rc = al(p, bytes, w);
+        if (rc || bytes == 0) return rc;
+        cudaError_t e = cudaMemcpy(*p, src, bytes, cudaMemcpyHostToDevice);
+        return e == cudaSuccess ? DMRG_OK : cuda_fail(e, w);
+    };
+    int rc;
+    if ((rc = al((void**)&S->op_sl, sizeof(uint16_t) * op_sl, "operator slices")) ||
+        (rc = al((void**)&S->op_ex, sizeof(int32_t) * op_ex, "operator exponents")) ||
+        (rc = al((void**)&S->ap_sl, sizeof(uint16_t) * S->ap_sl_vs * nv, "apply slices")) ||
+        (rc = al((void**)&S->ap_ex, sizeof(int32_t) * S->ap_ex_vs * nv, "apply exponents")) ||
+        (rc = al((void**)&S->s1, sizeof(int64_t) * S->s1_vs * nv, "stage-1 int64 results")) ||
+        (rc = al((void**)&S->s2, sizeof(int64_t) * S->s2_vs * nv, "stage-2 int64 sums")) ||
+        (rc = up((void**)&S->gemms, gemms.data(), sizeof(SGemm) * gemms.size(), "split gemms")) ||
+        (rc = up((void**)&S->work1, w1.data(), sizeof(SWork) * w1.size(), "split work")) ||
+        (rc = up((void**)&S->work2, w2.data(), sizeof(SWork) * w2.size(), "split work")) ||
+        (rc = up((void**)&S->segs, segs.data(), sizeof(SSeg) * segs.size(), "slice segments")) ||
+        (rc = up((void**)&S->jobs, jobs.data(), sizeof(SJob) * jobs.size(), "slice jobs")) ||
+        (rc = up((void**)&S->vb, vb.data(), sizeof(SVBlock) * vb.size(), "slice blocks")) ||
+        (rc = up((void**)&S->blocks, blocks.data(), sizeof(SBlock) * blocks.size(), "output blocks")) ||
+        (rc = up((void**)&S->parts, parts.data(), sizeof(SPart) * parts.size(), "output parts")) ||
+        (rc = al((void**)&S->status, sizeof(int32_t), "status")))
+        return rc;
+    cudaError_t e = cudaMemset(S->status, 0, sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "status");
+    e = cudaFuncSetAttribute(k_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(UmmaSmem)));
+    if (e != cudaSuccess) return cuda_fail(e, "umma shared memory");
+    S->kid_x = prof.kernel_id("split_slice/x");
+    S->kid_s1 = prof.kernel_id("umma_slices/stage1");
+    S->kid_mid = prof.kernel_id("split_slice/intermediate");
+    S->kid_s2 = prof.kernel_id("umma_slices/stage2");
+    S->kid_fin = prof.kernel_id("split_finalize");
+    // operator slices, once
+    if (S->n_vb_op > 0) {
+        SliceArgs sa{S->vb, S->n_vb_op, S->jobs, S->segs, d_ops, nullptr, 0, nullptr, 0, S->op_sl, S->ap_sl, 0,
+                     S->op_ex, S->ap_ex, 0, 1};
+        const int64_t grid = std::min<int64_t>(S->n_vb_op, int64_t(n_sm) * 8);
+        k_slice<<<unsigned(grid), 256>>>(sa);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "operator slicing");
+    }
+    return DMRG_OK;
 }
-int Handle::apply_split(const double*, double*, int32_t, cudaStream_t) {
-    return fail(DMRG_ERR_UNSUPPORTED, "split precision not built yet");
+
+int Handle::apply_split(const double* x, double* y, int32_t nvec, cudaStream_t st) {
+    SplitState* S = split;
+    Profiler::Pending pe;
+    cudaError_t e;
+    const int64_t slice_grid_cap = int64_t(n_sm) * 8;
+    auto slice = [&](int64_t vb0, int64_t nvb, int kid) {
+        if (nvb == 0) return cudaSuccess;
+        SliceArgs sa{S->vb + vb0, nvb, S->jobs, S->segs, d_ops, x, plan.dim, S->s1, S->s1_vs, S->op_sl, S->ap_sl,
+                     S->ap_sl_vs, S->op_ex, S->ap_ex, S->ap_ex_vs, nvec};
+        prof.begin(kid, st, 0.0, 0.0, &pe);
+        k_slice<<<unsigned(std::min(nvb * nvec, slice_grid_cap)), 256, 0, st>>>(sa);
+        prof.end(pe, st);
+        return cudaGetLastError();
+    };
+    auto gemm = [&](const SWork* w, int64_t nw, int kid, double flops) {
+        if (nw == 0) return cudaSuccess;
+        UmmaArgs ua{w, nw, S->gemms, S->op_sl, S->ap_sl, S->ap_sl_vs, S->s1, S->s1_vs, S->s2, S->s2_vs, nvec, S->status};
+        prof.begin(kid, st, flops * nvec, 0.0, &pe);
+        k_umma<<<unsigned(std::min<int64_t>(nw * nvec, n_sm)), UM_THREADS, sizeof(UmmaSmem), st>>>(ua);
+        prof.end(pe, st);
+        return cudaGetLastError();
+    };
+    if ((e = slice(S->n_vb_op, S->n_vb_x, S->kid_x)) != cudaSuccess) return cuda_fail(e, "slice x");
+    if ((e = gemm(S->work1, S->n_work1, S->kid_s1, s1_flops)) != cudaSuccess) return cuda_fail(e, "stage-1 slice gemm");
+    if ((e = slice(S->n_vb_op + S->n_vb_x, S->n_vb_mid, S->kid_mid)) != cudaSuccess)
+        return cuda_fail(e, "slice intermediates");
+    if (S->s2_vs > 0 && (e = cudaMemsetAsync(S->s2, 0, sizeof(int64_t) * S->s2_vs * nvec, st)) != cudaSuccess)
+        return cuda_fail(e, "zero stage-2 sums");
+    if ((e = gemm(S->work2, S->n_work2, S->kid_s2, s2_flops)) != cudaSuccess) return cuda_fail(e, "stage-2 slice gemm");
+    if (S->n_blocks > 0) {
+        prof.begin(S->kid_fin, st, 0.0, 0.0, &pe);
+        k_finalize<<<dim3(unsigned(S->n_blocks), unsigned(nvec)), 256, 0, st>>>(
+            S->blocks, S->parts, S->s2, S->s2_vs, S->op_ex, S->ap_ex, S->ap_ex_vs, y, plan.dim);
+        prof.end(pe, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "finalize");
+    }
+    return DMRG_OK;
 }
-void Handle::release_split() { delete split; split = nullptr; }
+
+int Handle::check_status() {
+    if (!split) return DMRG_OK;
+    int32_t v = 0;
+    cudaError_t e = cudaMemcpy(&v, split->status, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read status");
+    if (v != 0) {
+        cudaMemset(split->status, 0, sizeof(int32_t));
+        return fail(v, "a bounded device wait in the slice GEMM timed out");
+    }
+    return DMRG_OK;
+}
+
+void Handle::release_split() {
+    delete split;
+    split = nullptr;
+}
+
 }  // namespace dmrg

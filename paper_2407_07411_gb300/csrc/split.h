@@ -1,0 +1,110 @@
+// Split-precision (Ozaki) path: descriptors shared by the host planner and the kernels.
+//
+// Arithmetic.  An FP64 operand is cut, per row of the left factor and per column of
+// the right factor (a "vector" along the contraction index K), into S = 6 balanced
+// base-256 digits relative to the vector's exponent E (|a| < 2^E for every entry):
+//     a = 2^(E-7) * sum_k d_k 2^(-8k),   d_0 in [-128, 128], d_k in [-127, 128],
+// rounded after the sixth digit (relative error <= 2^-48 of the vector's maximum).
+// Slice k stores the exact BF16 value d_k 2^(-8k).  A product L*R is the sum of the
+// slice-pair products with i + j <= 5 (21 pairs; the dropped pairs weigh <= 2^-48),
+// accumulated on the tensor cores in five FP32 accumulators, one per pair level
+// l = i + j up to 3 and one for the rest:
+//     acc0 = L_0 R_0                        (integers, exact while K <= 1024)
+//     acc1 = L_0 R_1 + L_1 R_0              (multiples of 2^-8, exact while K <= 512)
+//     acc2 = the 3 pairs with i + j = 2     (multiples of 2^-16, exact while K <= 341)
+//     acc3 = the 4 pairs with i + j = 3     (multiples of 2^-24, exact while K <= 256)
+//     acc4 = the 11 pairs with i + j = 4, 5 (magnitude ~2^-32 of acc0)
+// The tensor cores add with truncation, so an inexact accumulator drifts by ~2^-23 of
+// its own magnitude per addition; keeping every level up to 3 exact confines that drift
+// to acc4, ~2^-47 of the result.  The accumulators are drained every 256 K into the
+// integer F = round(2^s (acc0 + ... + acc4)), with a
+// per-GEMM shift s = 47 - ceil(log2 K) that keeps |F| < 2^62 for K <= 2^23 while short
+// contractions keep a resolution far below 2^-46 of the result; then
+//     L*R = 2^(E_row + E_col - 14 - s) * F.
+// Stage-1 results are kept as int64 F (their exponents implied by the operand vectors),
+// sliced again for stage 2 with integer shifts only, and stage-2 results are summed as
+// int64 with atomics (exact, hence independent of order) before one conversion to
+// FP64 per output entry.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "plan.h"
+
+namespace dmrg {
+
+constexpr int SPL_S = 6;          // digit slices per operand
+constexpr int SPL_PAIRS = 21;     // slice pairs (i, j) with i + j <= 5
+constexpr int SPL_TM = 128;       // MMA tile rows (M)
+constexpr int SPL_TN = 64;        // MMA tile columns (N)
+constexpr int SPL_TK = 32;        // K per tile (two K=16 MMAs)
+constexpr int SPL_LT = SPL_TM * SPL_TK;   // bf16 elements per L slice tile
+constexpr int SPL_RT = SPL_TN * SPL_TK;   // bf16 elements per R slice tile
+constexpr int SPL_DRAIN_KT = 8;           // K tiles per exact drain (256 K)
+constexpr int SPL_ACCS = 5;               // TMEM accumulators (pair levels 0-3 exact, rest)
+constexpr int64_t SPL_MAX_K = int64_t(1) << 23;   // longest contraction (s >= 24)
+constexpr int SPL_S2_KCHUNK = 256;        // K tiles per stage-2 work item (8192 K)
+
+// One split GEMM: D (M x N) = L (M x K) * R (K x N) over kt K tiles.  L and R are
+// sliced tile arrays (buffer 0 = operator slices, 1 = per-apply slices); tile (mt, kt)
+// of L holds the 5 slices of rows [128 mt, +128) x K [32 kt, +32) contiguously.
+struct SGemm {
+    int64_t l_tiles, r_tiles;   // bf16 element offsets of tile (0, 0)
+    int64_t d_off;              // int64 element offset of D (stage-1 scratch or stage-2 sums)
+    int32_t l_buf, r_buf;
+    int32_t M, N, ldd, kt;
+    int32_t kind;               // 0: store sign*F (stage 1), 1: atomic add (stage 2)
+    int32_t sign;
+    int32_t fshift;             // s: F = round(2^s * accumulated slice sums)
+    int32_t pad;
+};
+
+struct SWork { int32_t gemm, mtile, ntile, k0, k1, pad; };
+
+// A contraction run of a sliced operand: nt sub-blocks of kc entries; entry k of
+// sub-block t of vector v is at off + t*ts + v*vs + k*ks in its source space.  For int64
+// sources (stage-1 results F) the entry's value is F * 2^e with
+//     e = op_exp[er_off + t*er_ts + v] + ap_exp[ec_off + k] - e_off.
+struct SSeg {
+    int64_t off, ts, vs, ks;
+    int64_t er_off, ec_off;
+    int32_t space, kc, nt, er_ts;
+    int32_t is_i64, e_off;
+};
+
+// Slice one operand: vectors [0, npad) (valid below nvalid) along K [0, kt*32) (valid
+// below K), rows_tile vectors per tile (128 for L, 64 for R).
+struct SJob {
+    int64_t out_tiles;   // bf16 element offset in the output slice buffer
+    int64_t out_exp;     // int32 offset in the output exponent buffer
+    int32_t out_buf, rows_tile;
+    int32_t nvalid, npad, K, kt;
+    int32_t seg0, nseg;
+};
+
+struct SVBlock { int32_t job, v0; };   // 8 vectors of one job (one per warp)
+
+// Output block of the wave function and the stage-2 sums that land on it.
+struct SBlock { int64_t y_off; int32_t rows, cols, p0, np; };
+struct SPart { int64_t acc_off, er_off, ec_off; int32_t er_buf, ec_buf, e_off, pad; };
+
+// Host-side split plan.
+struct SplitHost {
+    std::vector<SGemm> gemms;
+    std::vector<SSeg> segs;
+    std::vector<SJob> jobs;
+    std::vector<SWork> w1, w2;
+    std::vector<SBlock> blocks;
+    std::vector<SPart> parts;
+    std::vector<SVBlock> vb;
+    int64_t n_vb_op = 0, n_vb_x = 0, n_vb_mid = 0;
+    int64_t op_sl = 0, op_ex = 0, ap_sl_vs = 0, ap_ex_vs = 0, s1_vs = 0, s2_vs = 0;
+};
+
+int64_t cdiv(int64_t a, int64_t b);
+int32_t fshift_for(int64_t K);
+int build_split_plan(const Plan& P, SplitHost& H, std::string* err);
+int validate_split_plan(const Plan& P, const SplitHost& H, std::string* err);
+
+}  // namespace dmrg

@@ -95,3 +95,12 @@ def test_plan_only_handle_refuses_compute():
     with pytest.raises(lib.DmrgError) as e:
         h.apply_host(np.zeros(p.dim))
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("name,n_terms", [("tiny", None), ("mid", None), ("heavy", 120), ("precision", 24)])
+def test_split_plan_bounds_proof(name, n_terms):
+    # the split planner proves on the host that every copy, slice write, exponent
+    # access and output store of its kernels stays inside its buffer
+    p = S.generate(name, n_terms=n_terms)
+    h = lib.HEff.from_problem(p, precision="split", plan_only=True)
+    assert h.dim == p.dim and h.plan_dump().tobytes() == heff.plan(p).tobytes()
