@@ -145,6 +145,35 @@ int dmrg_heff_diagonal(dmrg_heff_t h, double* diag, void* stream);
 int dmrg_davidson(dmrg_heff_t h, int32_t k_eig, double tol, int32_t max_iter, int32_t block,
                   int32_t n_iter, double* x_inout, double* evals, dmrg_davidson_info* info);
 
+/* Size of the fixed device array used by dmrg_heff_apply_noalloc (32 MiB per GPU). */
+#define DMRG_NOALLOC_SCRATCH_BYTES (32 * 1024 * 1024)
+
+/* y = H_eff x for one vector, allocating no GPU memory.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory themselves,
+ * e.g. code whose GPU memory is owned and budgeted by a host framework's allocator, a
+ * plugin that only receives device buffers from its host application, or a loop where
+ * an allocation's implicit synchronisation would stall other work.
+ *   left .. b_off, n_terms : host arrays, exactly as for dmrg_heff_create
+ *   op_data (op_len doubles), x, y (dim doubles each): device pointers owned by the
+ *   caller, in the layouts of this header; y is fully overwritten.
+ * Everything else lives in one file-scope device array of DMRG_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library keeps until the process exits: the term tables (staged
+ * from the host arrays, which the call has finished reading when it returns) and one
+ * intermediate block of max(dim L) x max(dim R) doubles per CTA.  Problems with more than
+ * 512 sectors per block, or whose tables plus one such block exceed the array, are
+ * rejected with DMRG_ERR_INVALID_ARG.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  The call waits for earlier work on `stream`, queues the kernel and returns.
+ * All calls share the array: calls whose work overlaps on the GPU (e.g. on two streams
+ * without ordering) race and give wrong results.  Arithmetic: FP64, terms summed in
+ * order per output block. */
+int dmrg_heff_apply_noalloc(const int32_t* left, int32_t nl, const int32_t* right, int32_t nr,
+                            int32_t target_n, int32_t target_2sz,
+                            const double* coef, const int32_t* delta, const int32_t* parity,
+                            const int64_t* a_off, const int64_t* b_off, int64_t n_terms,
+                            const double* op_data, int64_t op_len,
+                            const double* x, double* y, void* stream);
+
 /* Release the handle and its device memory (NULL is ignored). */
 void dmrg_heff_destroy(dmrg_heff_t h);
 
