@@ -27,7 +27,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Hψ FP64-equiv TFLOP/s; Davidson time-to-E, split vs FP64 (|ΔE/E|≤1e-10)"
 UNIT = "TFLOP/s"
-SPLIT_PAIRS = 15   # BF16 slice-pair products per FP64-equivalent product (5 slices, i+j<=4)
+SPLIT_PAIRS = 21   # BF16 slice-pair products per FP64-equivalent product (6 slices, i+j<=5)
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes per launch of the dominant kernel from one ncu capture, keyed by the
 # sha256 of the kernel source it was taken on (a changed kernel reports null).

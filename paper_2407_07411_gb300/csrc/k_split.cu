@@ -5,7 +5,7 @@
 //             for int64 sources).
 //   k_umma    warp-specialised slice GEMM: one producer thread streams 72 KB stages
 //             with cp.async.bulk, one thread issues the 42 tcgen05.mma of each K tile
-//             into five TMEM accumulators, four epilogue warps drain the
+//             into five TMEM accumulators, eight epilogue warps drain the
 //             exact FP32 sums into int64 every 256 K and store / atomically add.
 //   k_finalize  stage-2 int64 sums -> FP64 wave-function blocks.
 // Every mbarrier wait is bounded; on timeout the CTA records DMRG_ERR_DEVICE_TIMEOUT in
@@ -22,7 +22,9 @@
 namespace dmrg {
 
 constexpr int UM_STAGES = 3;
-constexpr int UM_THREADS = 192;       // warp 0 producer, warp 1 MMA, warps 2-5 epilogue
+constexpr int UM_EPI_WARPS = 8;       // two per TMEM lane quarter, each drains 32 of the 64 columns
+constexpr int UM_THREADS = 64 + 32 * UM_EPI_WARPS;   // warp 0 producer, warp 1 MMA, the rest epilogue
+constexpr int UM_EPI_COLS = SPL_TN / (UM_EPI_WARPS / 4);
 constexpr int UM_TMEM_COLS = 512;     // 5 accumulators x 64 columns (power-of-two allocation)
 constexpr int UM_TBUF = 1;            // TMEM accumulator sets (drain alternates when 2)
 constexpr uint32_t UM_L_BYTES = SPL_S * SPL_LT * 2;   // 48 KB
@@ -49,15 +51,20 @@ struct SplitState {
     SWork* work2 = nullptr;
     SSeg* segs = nullptr;
     SJob* jobs = nullptr;
-    SVBlock* vb = nullptr;      // [operator blocks | x blocks | mid blocks]
+    SSlab* slabs = nullptr;
+    SItem* items = nullptr;     // [operator items | x items | intermediate items]
+    STile* tiles = nullptr;     // [operator tiles | x tiles | intermediate tiles]
     SBlock* blocks = nullptr;
     SPart* parts = nullptr;
     int32_t* status = nullptr;
-    int64_t n_work1 = 0, n_work2 = 0, n_vb_op = 0, n_vb_x = 0, n_vb_mid = 0, n_blocks = 0;
+    int64_t n_work1 = 0, n_work2 = 0, n_blocks = 0;
+    int64_t it_op0 = 0, it_x0 = 0, it_mid0 = 0, it_end = 0;      // item ranges
+    int64_t tl_op0 = 0, tl_x0 = 0, tl_mid0 = 0, tl_end = 0;      // tile ranges
     int64_t ap_sl_vs = 0, ap_ex_vs = 0, s1_vs = 0, s2_vs = 0;
     int kid_x = -1, kid_s1 = -1, kid_mid = -1, kid_s2 = -1, kid_fin = -1;
     ~SplitState() {
-        void* p[] = {op_sl, op_ex, ap_sl, ap_ex, s1, s2, gemms, work1, work2, segs, jobs, vb, blocks, parts, status};
+        void* p[] = {op_sl, op_ex, ap_sl, ap_ex, s1, s2, gemms, work1, work2, segs, jobs, slabs, items, tiles, blocks,
+                     parts, status};
         for (void* q : p)
             if (q) cudaFree(q);
     }
@@ -125,15 +132,17 @@ __device__ __forceinline__ uint16_t digit_bf16(int d, int k) {
 
 // Position of (vector v, K index K) inside a job's tile array (bf16 elements), slice s.
 __device__ __forceinline__ int64_t tile_pos(const SJob& J, int v, int K, int s) {
-    const int vt = v / J.rows_tile, vr = v % J.rows_tile, kt = K / SPL_TK, kr = K % SPL_TK;
+    const int sh = J.rows_tile == SPL_TM ? 7 : 6;   // rows_tile is 128 (L) or 64 (R)
+    const int vt = v >> sh, vr = v & (J.rows_tile - 1), kt = K / SPL_TK, kr = K % SPL_TK;
     const int64_t tile = (int64_t(vt) * J.kt + kt) * SPL_S + s;
     return J.out_tiles + tile * (int64_t(J.rows_tile) * SPL_TK) + ((vr >> 3) * 4 + (kr >> 3)) * 64 + (vr & 7) * 8 +
            (kr & 7);
 }
 
 struct SliceArgs {
-    const SVBlock* vb;
-    int64_t n_vb;
+    const SItem* items;
+    int64_t n_items;
+    const SSlab* slabs;
     const SJob* jobs;
     const SSeg* segs;
     const double* ops;
@@ -150,70 +159,132 @@ struct SliceArgs {
     int nvec;
 };
 
-__global__ void __launch_bounds__(256) k_slice(SliceArgs a) {
+// Pass 1 (FP64 sources): every source row (term t, vector v) raises its vector's
+// exponent with an integer atomicMax (exact, so the result does not depend on order).
+// Exponents of int64 intermediates are raised by the stage-1 epilogue instead.
+__global__ void __launch_bounds__(256) k_slice_max(SliceArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t n_items = a.n_vb * a.nvec;
-    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const SVBlock B = a.vb[item / a.nvec];
+    for (int64_t item = blockIdx.x; item < a.n_items * a.nvec; item += gridDim.x) {
+        const SItem I = a.items[item / a.nvec];
         const int v = int(item % a.nvec);
-        const SJob J = a.jobs[B.job];
-        const int vec = B.v0 + warp;
-        if (vec >= J.npad) continue;
-        const bool valid = vec < J.nvalid;
-        uint16_t* out = (J.out_buf ? a.ap_sl + int64_t(v) * a.ap_sl_vs : a.op_sl);
-        int32_t* oex = (J.out_buf ? a.ap_ex + int64_t(v) * a.ap_ex_vs : a.op_ex);
-        const double* x = a.x + int64_t(v) * a.x_vs;
-        const int64_t* s1 = a.s1 + int64_t(v) * a.s1_vs;
-        const int32_t* cex = a.ap_ex + int64_t(v) * a.ap_ex_vs;   // stage-1 R exponents
-        // pass 1: exponent of the vector
-        int E = INT_MIN;
-        if (valid) {
-            for (int s = J.seg0; s < J.seg0 + J.nseg; ++s) {
-                const SSeg g = a.segs[s];
-                for (int t = 0; t < g.nt; ++t) {
-                    const int64_t base = g.off + t * g.ts + int64_t(vec) * g.vs;
-                    for (int k = lane; k < g.kc; k += 32) {
-                        int e;
-                        if (g.is_i64) {
-                            const int eF = a.op_ex[g.er_off + int64_t(t) * g.er_ts + vec] + cex[g.ec_off + k] - g.e_off;
-                            e = exp_i64(s1[base + k * g.ks], eF);
-                        } else {
-                            e = exp_f64((g.space == SP_OPS ? a.ops : x)[base + k * g.ks]);
-                        }
-                        E = max(E, e);
-                    }
+        const SSlab S = a.slabs[I.slab];
+        const SJob J = a.jobs[S.job];
+        const SSeg g = a.segs[S.seg];
+        const double* src = g.space == SP_OPS ? a.ops : a.x + int64_t(v) * a.x_vs;
+        int32_t* oex = J.out_buf ? a.ap_ex + int64_t(v) * a.ap_ex_vs : a.op_ex;
+        for (int rr = warp; rr < I.nrows; rr += 8) {
+            const int64_t r = I.r0 + rr;
+            const int t = int(r / J.nvalid), vec = int(r - int64_t(t) * J.nvalid);
+            const int64_t base = g.off + t * g.ts + int64_t(vec) * g.vs;
+            int E = INT_MIN;
+            for (int k = lane; k < g.kc; k += 32) E = max(E, exp_f64(src[base + k * g.ks]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+            if (lane == 0 && E != INT_MIN) atomicMax(oex + J.out_exp + vec, E);
+        }
+    }
+}
+
+struct TileArgs {
+    const STile* tiles;
+    int64_t n_tiles;
+    const SJob* jobs;
+    const SSeg* segs;
+    const double* ops;
+    const double* x;
+    int64_t x_vs;
+    const int64_t* s1;
+    int64_t s1_vs;
+    uint16_t* op_sl;
+    uint16_t* ap_sl;
+    int64_t ap_sl_vs;
+    const int32_t* op_ex;
+    const int32_t* ap_ex;
+    int64_t ap_ex_vs;
+    int nvec;
+};
+
+// Pass 2: digits of 8 vectors x 256 K of one job relative to the vectors' exponents.
+// Each thread decodes one K column (segment, term, entry) and forms the digits of its
+// 8 entries; the CTA assembles whole 8x8 core matrices of every slice in shared memory
+// and writes them as contiguous 512-byte runs (positions outside the valid vectors and
+// K stay zero from set-up).
+__global__ void __launch_bounds__(SPL_TILE_K) k_slice_digits(TileArgs a) {
+    __shared__ __align__(16) uint16_t sd[SPL_S][8][SPL_TILE_K];
+    __shared__ int32_t s_E[8];
+    const int tid = threadIdx.x;
+    for (int64_t item = blockIdx.x; item < a.n_tiles * a.nvec; item += gridDim.x) {
+        const STile T = a.tiles[item / a.nvec];
+        const int v = int(item % a.nvec);
+        const SJob J = a.jobs[T.job];
+        const int32_t* oex = J.out_buf ? a.ap_ex + int64_t(v) * a.ap_ex_vs : a.op_ex;
+        if (tid < 8) {
+            const int vec = 8 * T.vg + tid;
+            s_E[tid] = vec < J.nvalid ? oex[J.out_exp + vec] : 0;
+        }
+        __syncthreads();
+        const int K = T.k0 + tid;
+        int d[8][SPL_S];
+#pragma unroll
+        for (int vv = 0; vv < 8; ++vv)
+#pragma unroll
+            for (int q = 0; q < SPL_S; ++q) d[vv][q] = 0;
+        if (K < J.K) {
+            int kb = 0, sg = J.seg0;
+            for (; sg < J.seg0 + J.nseg - 1; ++sg) {
+                const int ext = a.segs[sg].kc * a.segs[sg].nt;
+                if (K < kb + ext) break;
+                kb += ext;
+            }
+            const SSeg g = a.segs[sg];
+            const int t = (K - kb) / g.kc, k = (K - kb) - t * g.kc;
+            const int64_t base = g.off + t * g.ts + k * g.ks;
+            const int nv = min(8, J.nvalid - 8 * T.vg);
+            if (g.is_i64) {   // all loads first, then the integer digit arithmetic
+                const int64_t* s1 = a.s1 + int64_t(v) * a.s1_vs + base + int64_t(8 * T.vg) * g.vs;
+                const int32_t* er = a.op_ex + g.er_off + int64_t(t) * g.er_ts + 8 * T.vg;
+                const int ec = a.ap_ex[int64_t(v) * a.ap_ex_vs + g.ec_off + k] - g.e_off;
+                long long F[8];
+                int e[8];
+#pragma unroll
+                for (int vv = 0; vv < 8; ++vv) {
+                    F[vv] = vv < nv ? s1[int64_t(vv) * g.vs] : 0;
+                    e[vv] = vv < nv ? er[vv] : 0;
                 }
+#pragma unroll
+                for (int vv = 0; vv < 8; ++vv)
+                    if (F[vv] != 0) digits_i64(F[vv], e[vv] + ec, s_E[vv], d[vv]);
+            } else {
+                const double* src = (g.space == SP_OPS ? a.ops : a.x + int64_t(v) * a.x_vs) + base +
+                                    int64_t(8 * T.vg) * g.vs;
+                double xv[8];
+#pragma unroll
+                for (int vv = 0; vv < 8; ++vv) xv[vv] = vv < nv ? src[int64_t(vv) * g.vs] : 0.0;
+#pragma unroll
+                for (int vv = 0; vv < 8; ++vv) digits_f64(xv[vv], s_E[vv], d[vv]);
             }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
-        const bool zero = E == INT_MIN;
-        if (lane == 0) oex[J.out_exp + vec] = zero ? 0 : E;
-        // pass 2: digits
-        int K0 = 0;
-        if (valid && !zero) {
-            for (int s = J.seg0; s < J.seg0 + J.nseg; ++s) {
-                const SSeg g = a.segs[s];
-                for (int t = 0; t < g.nt; ++t, K0 += g.kc) {
-                    const int64_t base = g.off + t * g.ts + int64_t(vec) * g.vs;
-                    for (int k = lane; k < g.kc; k += 32) {
-                        int d[SPL_S];
-                        if (g.is_i64) {
-                            const int eF = a.op_ex[g.er_off + int64_t(t) * g.er_ts + vec] + cex[g.ec_off + k] - g.e_off;
-                            digits_i64(s1[base + k * g.ks], eF, E, d);
-                        } else {
-                            digits_f64((g.space == SP_OPS ? a.ops : x)[base + k * g.ks], E, d);
-                        }
+        for (int vv = 0; vv < 8; ++vv)
 #pragma unroll
-                        for (int q = 0; q < SPL_S; ++q) out[tile_pos(J, vec, K0 + k, q)] = digit_bf16(d[q], q);
-                    }
-                }
-            }
+            for (int q = 0; q < SPL_S; ++q) sd[q][vv][tid] = digit_bf16(d[vv][q], q);
+        __syncthreads();
+        // write: per slice and K tile, the 4 core matrices of this 8-vector group are 512
+        // contiguous bytes: core kg holds rows vv = 0..7 of K [32 kt + 8 kg, +8)
+        uint16_t* out = J.out_buf ? a.ap_sl + int64_t(v) * a.ap_sl_vs : a.op_sl;
+        const int kt0 = T.k0 / SPL_TK;
+        const int nkt = min(SPL_TILE_K / SPL_TK, J.kt - kt0);
+        const int64_t tile_elems = int64_t(J.rows_tile) * SPL_TK;
+        const int vt = (8 * T.vg) / J.rows_tile, rg = ((8 * T.vg) % J.rows_tile) >> 3;
+        for (int c = tid; c < SPL_S * nkt * 32; c += SPL_TILE_K) {   // 32 chunks of 16 B per slice-tile
+            const int q = c / (nkt * 32), rem = c - q * (nkt * 32), kt = rem >> 5, ch = rem & 31;
+            const int kg = ch >> 3, vv = ch & 7;
+            const int64_t dst = J.out_tiles + ((int64_t(vt) * J.kt + kt0 + kt) * SPL_S + q) * tile_elems +
+                                (rg * 4 + kg) * 64 + vv * 8;
+            const uint4 val = *reinterpret_cast<const uint4*>(&sd[q][vv][kt * SPL_TK + kg * 8]);
+            *reinterpret_cast<uint4*>(out + dst) = val;
         }
-        const int Kpad = J.kt * SPL_TK;
-        for (int K = (valid && !zero) ? K0 + lane : lane; K < Kpad; K += 32)
-#pragma unroll
-            for (int q = 0; q < SPL_S; ++q) out[tile_pos(J, vec, K, q)] = 0;
+        __syncthreads();
     }
 }
 
@@ -307,6 +378,9 @@ struct UmmaArgs {
     int64_t s1_vs;
     int64_t* s2;
     int64_t s2_vs;
+    const int32_t* op_ex;
+    int32_t* ap_ex;
+    int64_t ap_ex_vs;
     int nvec;
     int* status;
 };
@@ -332,7 +406,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
         }
         for (int b = 0; b < UM_TBUF; ++b) {
             mbar_init(&sm.tfull[b], 1);
-            mbar_init(&sm.tempty[b], 128);
+            mbar_init(&sm.tempty[b], 32 * UM_EPI_WARPS);
         }
         mbar_init(&sm.done, 1);
         sm.abort = 0;
@@ -404,9 +478,10 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
         umma_commit(&sm.done);   // completes when every MMA issued above has finished
         mbar_wait_final(&sm.done, 0);
     } else if (warp >= 2) {
-        // ---- epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (tile rows)
-        const int q = warp & 3;
-        const int row = 32 * q + lane;
+        // ---- epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (tile rows) and the column
+        // half (w-2)/4 of every accumulator
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int row = 32 * q + lane, col0 = h * UM_EPI_COLS;
         const uint32_t lane_addr = uint32_t(32 * q) << 16;
         int64_t dchunk = 0;
         bool ok = true;
@@ -415,16 +490,16 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
             const int v = int(it % a.nvec);
             const int fs = a.gemms[W.gemm].fshift;
             const float scale_f = __int_as_float((127 + fs) << 23);   // 2^fs
-            long long acc[SPL_TN];
+            long long acc[UM_EPI_COLS];
 #pragma unroll
-            for (int j = 0; j < SPL_TN; ++j) acc[j] = 0;
+            for (int j = 0; j < UM_EPI_COLS; ++j) acc[j] = 0;
             for (int kc0 = W.k0; kc0 < W.k1; kc0 += SPL_DRAIN_KT, ++dchunk) {
                 const int b = int(dchunk % UM_TBUF);
                 if (!(ok = mbar_wait(sm, &sm.tfull[b], uint32_t((dchunk / UM_TBUF) & 1), a.status))) break;
                 tc_fence_after();
-                const uint32_t base = tmem + lane_addr + uint32_t(b) * (SPL_ACCS * SPL_TN);
+                const uint32_t base = tmem + lane_addr + uint32_t(b) * (SPL_ACCS * SPL_TN) + col0;
 #pragma unroll
-                for (int c0 = 0; c0 < SPL_TN; c0 += 8) {
+                for (int c0 = 0; c0 < UM_EPI_COLS; c0 += 8) {
                     uint32_t r0[8], r1[8], r2[8], r3[8], r4[8];
                     tmem_ld8(base + c0, r0);
                     tmem_ld8(base + SPL_TN + c0, r1);
@@ -449,19 +524,32 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
             const SGemm G = a.gemms[W.gemm];
             const int r = W.mtile * SPL_TM + row;
             if (r < G.M) {
+                const int cbase = W.ntile * SPL_TN + col0;
                 if (G.kind == 0) {
                     int64_t* D = a.s1 + int64_t(v) * a.s1_vs + G.d_off + int64_t(r) * G.ldd;
+                    const int32_t* cex = a.ap_ex + int64_t(v) * a.ap_ex_vs + G.ec_off;
+                    int emax = INT_MIN;
 #pragma unroll
-                    for (int j = 0; j < SPL_TN; ++j) {
-                        const int c = W.ntile * SPL_TN + j;
-                        if (c < G.N) D[c] = G.sign > 0 ? acc[j] : -acc[j];
+                    for (int j = 0; j < UM_EPI_COLS; ++j) {
+                        const int c = cbase + j;
+                        if (c < G.N) {
+                            D[c] = G.sign > 0 ? acc[j] : -acc[j];
+                            if (acc[j] != 0) {
+                                const unsigned long long u = acc[j] < 0 ? static_cast<unsigned long long>(-acc[j])
+                                                                        : static_cast<unsigned long long>(acc[j]);
+                                emax = max(emax, (64 - __clzll(u)) + cex[c]);
+                            }
+                        }
                     }
+                    if (emax != INT_MIN && G.x2_exp >= 0)
+                        atomicMax(a.ap_ex + int64_t(v) * a.ap_ex_vs + G.x2_exp + r % G.x2_period,
+                                  emax + a.op_ex[G.er_off + r] - (14 + G.fshift));
                 } else {
                     unsigned long long* D = reinterpret_cast<unsigned long long*>(a.s2 + int64_t(v) * a.s2_vs +
                                                                                   G.d_off + int64_t(r) * G.ldd);
 #pragma unroll
-                    for (int j = 0; j < SPL_TN; ++j) {
-                        const int c = W.ntile * SPL_TN + j;
+                    for (int j = 0; j < UM_EPI_COLS; ++j) {
+                        const int c = cbase + j;
                         if (c < G.N && acc[j] != 0) atomicAdd(D + c, static_cast<unsigned long long>(acc[j]));
                     }
                 }
@@ -557,10 +645,29 @@ int validate_split_plan(const Plan& P, const SplitHost& H, std::string* err) {
             if (int64_t(x.mtile) * SPL_TM >= G.M || int64_t(x.ntile) * SPL_TN >= G.N) return false;
             const int64_t dend = G.d_off + int64_t(G.M - 1) * G.ldd + G.N;
             if (G.ldd < G.N || dend > (G.kind == 0 ? H.s1_vs : H.s2_vs)) return false;
+            if (G.kind == 0) {   // stage-1 epilogue exponent reads and raises
+                if (G.x2_exp < 0 || G.x2_period <= 0 || G.x2_exp + G.x2_period > H.ap_ex_vs) return false;
+                if (G.er_off < 0 || G.er_off + G.M > H.op_ex || G.ec_off < 0 || G.ec_off + G.N > H.ap_ex_vs)
+                    return false;
+            }
         }
         return true;
     };
     if (!check_work(H.w1) || !check_work(H.w2)) return bad("gemm work");
+    for (const STile& T : H.tiles) {
+        if (T.job < 0 || T.job >= int32_t(H.jobs.size())) return bad("slice tile job");
+        const SJob& J = H.jobs[T.job];
+        if (T.vg < 0 || 8 * T.vg >= J.nvalid || 8 * T.vg + 8 > J.npad || J.rows_tile % 8) return bad("slice tile rows");
+        if (T.k0 < 0 || T.k0 >= J.K || T.k0 % SPL_TILE_K) return bad("slice tile K");
+    }
+    for (const SItem& I : H.items) {
+        if (I.slab < 0 || I.slab >= int32_t(H.slabs.size())) return bad("slice item");
+        const SSlab& Sl = H.slabs[I.slab];
+        if (I.r0 < 0 || I.nrows <= 0 || I.r0 + I.nrows > Sl.rows) return bad("slice item rows");
+        const SJob& J = H.jobs[Sl.job];
+        if (Sl.seg < J.seg0 || Sl.seg >= J.seg0 + J.nseg || Sl.rows != int64_t(H.segs[Sl.seg].nt) * J.nvalid)
+            return bad("slice slab");
+    }
     for (const SBlock& B : H.blocks)
         for (int p = B.p0; p < B.p0 + B.np; ++p) {
             const SPart& Q = H.parts[p];
@@ -638,6 +745,7 @@ int build_split_plan(const Plan& P, SplitHost& H, std::string* err) {
         m.kt = int32_t(cdiv(G.order == 0 ? G.b : G.c, SPL_TK));
         m.d_off = G.scratch; m.ldd = m.N; m.kind = 0; m.sign = G.sign < 0 ? -1 : 1;
         m.fshift = fshift_for(G.order == 0 ? G.b : G.c);
+        m.er_off = le; m.ec_off = re; m.x2_period = G.order == 0 ? G.a : G.d; m.x2_exp = -1;
         s1_lexp[g] = le; s1_rexp[g] = re; s1_eoff[g] = 14 + m.fshift;
         const int32_t gi = int32_t(gemms.size());
         gemms.push_back(m);
@@ -682,6 +790,8 @@ int build_split_plan(const Plan& P, SplitHost& H, std::string* err) {
             const int lbuf = order == 0 ? 1 : 0, rbuf = order == 0 ? 0 : 1;
             int32_t lj = add_job(lbuf, SPL_TM, m.M, K, lseg, &lt, &le);
             int32_t rj = add_job(rbuf, SPL_TN, m.N, K, rseg, &rt, &re);
+            for (int32_t g : by_out[o])   // stage-1 GEMMs whose rows feed this job's vectors
+                if (P.groups[g].order == order) gemms[g].x2_exp = order == 0 ? le : re;
             (lbuf ? mid_jobs : op_jobs).push_back(lj);
             (rbuf ? mid_jobs : op_jobs).push_back(rj);
             m.l_tiles = lt; m.r_tiles = rt; m.l_buf = lbuf; m.r_buf = rbuf;
@@ -690,28 +800,65 @@ int build_split_plan(const Plan& P, SplitHost& H, std::string* err) {
             parts.push_back({s2, le, re, lbuf, rbuf, 14 + m.fshift, 0});
             blocks[o].np += 1;
             s2 += int64_t(m.M) * m.N;
-            const int32_t gi = int32_t(gemms.size());
             gemms.push_back(m);
+        }
+    }
+    // stage-2 work: output tiles x K chunks; the chunk (a multiple of the drain length,
+    // at most SPL_S2_KCHUNK K tiles) shrinks until there are >= 4 items per SM
+    {
+        int64_t tile_kt = 0;
+        for (size_t gi = P.groups.size(); gi < gemms.size(); ++gi)
+            tile_kt += cdiv(gemms[gi].M, SPL_TM) * cdiv(gemms[gi].N, SPL_TN) * int64_t(gemms[gi].kt);
+        int chunk = SPL_S2_KCHUNK;
+        while (chunk > SPL_DRAIN_KT && tile_kt / chunk < 4 * 152) chunk /= 2;
+        for (size_t gi = P.groups.size(); gi < gemms.size(); ++gi) {
+            const SGemm& m = gemms[gi];
             for (int mt = 0; mt < cdiv(m.M, SPL_TM); ++mt)
                 for (int nt = 0; nt < cdiv(m.N, SPL_TN); ++nt)
-                    for (int k0 = 0; k0 < m.kt; k0 += SPL_S2_KCHUNK)
-                        w2.push_back({gi, mt, nt, k0, std::min(m.kt, k0 + SPL_S2_KCHUNK), 0});
+                    for (int k0 = 0; k0 < m.kt; k0 += chunk)
+                        w2.push_back({int32_t(gi), mt, nt, k0, std::min(m.kt, k0 + chunk), 0});
         }
     }
     auto by_cost = [](const SWork& x, const SWork& y) { return (x.k1 - x.k0) > (y.k1 - y.k0); };
     std::stable_sort(w1.begin(), w1.end(), by_cost);
     std::stable_sort(w2.begin(), w2.end(), by_cost);
-    std::vector<SVBlock>& vb = H.vb;
-    auto add_vb = [&](const std::vector<int32_t>& js) {
-        for (int32_t j : js)
-            for (int v0 = 0; v0 < jobs[j].npad; v0 += 8) vb.push_back({j, v0});
+    std::vector<SSlab>& slabs = H.slabs;
+    std::vector<SItem>& items = H.items;
+    auto add_items = [&](const std::vector<int32_t>& js) {
+        for (int32_t j : js) {
+            int32_t kb = 0;
+            for (int sg = jobs[j].seg0; sg < jobs[j].seg0 + jobs[j].nseg; ++sg) {
+                const int64_t n = int64_t(segs[sg].nt) * jobs[j].nvalid;
+                if (n > 0) {
+                    const int32_t sl = int32_t(slabs.size());
+                    slabs.push_back({n, j, sg, kb, 0});
+                    for (int64_t r0 = 0; r0 < n; r0 += SPL_ROWS_PER_ITEM)
+                        items.push_back({r0, sl, int32_t(std::min<int64_t>(SPL_ROWS_PER_ITEM, n - r0))});
+                }
+                kb += segs[sg].kc * segs[sg].nt;
+            }
+        }
     };
-    add_vb(op_jobs);
-    H.n_vb_op = int64_t(vb.size());
-    add_vb(x_jobs);
-    H.n_vb_x = int64_t(vb.size()) - H.n_vb_op;
-    add_vb(mid_jobs);
-    H.n_vb_mid = int64_t(vb.size()) - H.n_vb_op - H.n_vb_x;
+    H.it_op0 = 0;
+    add_items(op_jobs);
+    H.it_x0 = int64_t(items.size());
+    add_items(x_jobs);
+    H.it_mid0 = int64_t(items.size());
+    add_items(mid_jobs);
+    H.it_end = int64_t(items.size());
+    std::vector<STile>& tiles = H.tiles;
+    auto add_tiles = [&](const std::vector<int32_t>& js) {
+        for (int32_t j : js)
+            for (int vg = 0; 8 * vg < jobs[j].nvalid; ++vg)
+                for (int k0 = 0; k0 < jobs[j].K; k0 += SPL_TILE_K) tiles.push_back({j, vg, k0, 0});
+    };
+    H.tl_op0 = 0;
+    add_tiles(op_jobs);
+    H.tl_x0 = int64_t(tiles.size());
+    add_tiles(x_jobs);
+    H.tl_mid0 = int64_t(tiles.size());
+    add_tiles(mid_jobs);
+    H.tl_end = int64_t(tiles.size());
     H.op_sl = op_sl;
     H.op_ex = op_ex + 1;
     H.ap_sl_vs = cdiv(ap_sl, 64) * 64;
@@ -736,11 +883,12 @@ int Handle::init_split(const double*, const int64_t*, const int64_t*, const doub
     const std::vector<SWork>& w2 = H.w2;
     const std::vector<SBlock>& blocks = H.blocks;
     const std::vector<SPart>& parts = H.parts;
-    const std::vector<SVBlock>& vb = H.vb;
+    const std::vector<SSlab>& slabs = H.slabs;
+    const std::vector<SItem>& items = H.items;
+    const std::vector<STile>& tiles = H.tiles;
     const int64_t op_sl = H.op_sl, op_ex = H.op_ex;
-    S->n_vb_op = H.n_vb_op;
-    S->n_vb_x = H.n_vb_x;
-    S->n_vb_mid = H.n_vb_mid;
+    S->it_op0 = H.it_op0; S->it_x0 = H.it_x0; S->it_mid0 = H.it_mid0; S->it_end = H.it_end;
+    S->tl_op0 = H.tl_op0; S->tl_x0 = H.tl_x0; S->tl_mid0 = H.tl_mid0; S->tl_end = H.tl_end;
     S->n_work1 = int64_t(w1.size());
     S->n_work2 = int64_t(w2.size());
     S->n_blocks = int64_t(blocks.size());
@@ -775,7 +923,9 @@ int Handle::init_split(const double*, const int64_t*, const int64_t*, const doub
         (rc = up((void**)&S->work2, w2.data(), sizeof(SWork) * w2.size(), "split work")) ||
         (rc = up((void**)&S->segs, segs.data(), sizeof(SSeg) * segs.size(), "slice segments")) ||
         (rc = up((void**)&S->jobs, jobs.data(), sizeof(SJob) * jobs.size(), "slice jobs")) ||
-        (rc = up((void**)&S->vb, vb.data(), sizeof(SVBlock) * vb.size(), "slice blocks")) ||
+        (rc = up((void**)&S->slabs, slabs.data(), sizeof(SSlab) * slabs.size(), "slice slabs")) ||
+        (rc = up((void**)&S->items, items.data(), sizeof(SItem) * items.size(), "slice items")) ||
+        (rc = up((void**)&S->tiles, tiles.data(), sizeof(STile) * tiles.size(), "slice tiles")) ||
         (rc = up((void**)&S->blocks, blocks.data(), sizeof(SBlock) * blocks.size(), "output blocks")) ||
         (rc = up((void**)&S->parts, parts.data(), sizeof(SPart) * parts.size(), "output parts")) ||
         (rc = al((void**)&S->status, sizeof(int32_t), "status")))
@@ -789,12 +939,19 @@ int Handle::init_split(const double*, const int64_t*, const int64_t*, const doub
     S->kid_mid = prof.kernel_id("split_slice/intermediate");
     S->kid_s2 = prof.kernel_id("umma_slices/stage2");
     S->kid_fin = prof.kernel_id("split_finalize");
+    // slice buffers start at zero (padding is never written again), exponents at "none"
+    if (op_sl > 0 && (e = cudaMemset(S->op_sl, 0, sizeof(uint16_t) * op_sl)) != cudaSuccess) return cuda_fail(e, "zero slices");
+    if (S->ap_sl_vs > 0 && (e = cudaMemset(S->ap_sl, 0, sizeof(uint16_t) * S->ap_sl_vs * nv)) != cudaSuccess)
+        return cuda_fail(e, "zero slices");
+    if ((e = cudaMemset(S->op_ex, 0xC0, sizeof(int32_t) * op_ex)) != cudaSuccess) return cuda_fail(e, "exponents");
     // operator slices, once
-    if (S->n_vb_op > 0) {
-        SliceArgs sa{S->vb, S->n_vb_op, S->jobs, S->segs, d_ops, nullptr, 0, nullptr, 0, S->op_sl, S->ap_sl, 0,
-                     S->op_ex, S->ap_ex, 0, 1};
-        const int64_t grid = std::min<int64_t>(S->n_vb_op, int64_t(n_sm) * 8);
-        k_slice<<<unsigned(grid), 256>>>(sa);
+    if (S->it_x0 > S->it_op0) {
+        SliceArgs sa{S->items + S->it_op0, S->it_x0 - S->it_op0, S->slabs, S->jobs, S->segs, d_ops, nullptr, 0,
+                     nullptr, 0, S->op_sl, S->ap_sl, 0, S->op_ex, S->ap_ex, 0, 1};
+        TileArgs ta{S->tiles + S->tl_op0, S->tl_x0 - S->tl_op0, S->jobs, S->segs, d_ops, nullptr, 0, nullptr, 0,
+                    S->op_sl, S->ap_sl, 0, S->op_ex, S->ap_ex, 0, 1};
+        k_slice_max<<<unsigned(std::min<int64_t>(S->it_x0 - S->it_op0, int64_t(n_sm) * 16)), 256>>>(sa);
+        k_slice_digits<<<unsigned(std::min<int64_t>(S->tl_x0 - S->tl_op0, int64_t(n_sm) * 16)), SPL_TILE_K>>>(ta);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return cuda_fail(e, "operator slicing");
@@ -806,27 +963,35 @@ int Handle::apply_split(const double* x, double* y, int32_t nvec, cudaStream_t s
     SplitState* S = split;
     Profiler::Pending pe;
     cudaError_t e;
-    const int64_t slice_grid_cap = int64_t(n_sm) * 8;
-    auto slice = [&](int64_t vb0, int64_t nvb, int kid) {
-        if (nvb == 0) return cudaSuccess;
-        SliceArgs sa{S->vb + vb0, nvb, S->jobs, S->segs, d_ops, x, plan.dim, S->s1, S->s1_vs, S->op_sl, S->ap_sl,
-                     S->ap_sl_vs, S->op_ex, S->ap_ex, S->ap_ex_vs, nvec};
+    const int64_t slice_grid_cap = int64_t(n_sm) * 16;
+    auto slice = [&](int64_t i0, int64_t i1, int64_t t0, int64_t t1, bool with_max, int kid) {
+        if (t1 == t0) return cudaSuccess;
+        SliceArgs sa{S->items + i0, i1 - i0, S->slabs, S->jobs, S->segs, d_ops, x, plan.dim, S->s1, S->s1_vs,
+                     S->op_sl, S->ap_sl, S->ap_sl_vs, S->op_ex, S->ap_ex, S->ap_ex_vs, nvec};
+        TileArgs ta{S->tiles + t0, t1 - t0, S->jobs, S->segs, d_ops, x, plan.dim, S->s1, S->s1_vs, S->op_sl,
+                    S->ap_sl, S->ap_sl_vs, S->op_ex, S->ap_ex, S->ap_ex_vs, nvec};
         prof.begin(kid, st, 0.0, 0.0, &pe);
-        k_slice<<<unsigned(std::min(nvb * nvec, slice_grid_cap)), 256, 0, st>>>(sa);
+        if (with_max && i1 > i0)
+            k_slice_max<<<unsigned(std::min<int64_t>((i1 - i0) * nvec, slice_grid_cap)), 256, 0, st>>>(sa);
+        k_slice_digits<<<unsigned(std::min<int64_t>((t1 - t0) * nvec, slice_grid_cap)), SPL_TILE_K, 0, st>>>(ta);
         prof.end(pe, st);
         return cudaGetLastError();
     };
     auto gemm = [&](const SWork* w, int64_t nw, int kid, double flops) {
         if (nw == 0) return cudaSuccess;
-        UmmaArgs ua{w, nw, S->gemms, S->op_sl, S->ap_sl, S->ap_sl_vs, S->s1, S->s1_vs, S->s2, S->s2_vs, nvec, S->status};
+        UmmaArgs ua{w, nw, S->gemms, S->op_sl, S->ap_sl, S->ap_sl_vs, S->s1, S->s1_vs, S->s2, S->s2_vs,
+                    S->op_ex, S->ap_ex, S->ap_ex_vs, nvec, S->status};
         prof.begin(kid, st, flops * nvec, 0.0, &pe);
         k_umma<<<unsigned(std::min<int64_t>(nw * nvec, n_sm)), UM_THREADS, sizeof(UmmaSmem), st>>>(ua);
         prof.end(pe, st);
         return cudaGetLastError();
     };
-    if ((e = slice(S->n_vb_op, S->n_vb_x, S->kid_x)) != cudaSuccess) return cuda_fail(e, "slice x");
+    if ((e = cudaMemsetAsync(S->ap_ex, 0xC0, sizeof(int32_t) * S->ap_ex_vs * nvec, st)) != cudaSuccess)
+        return cuda_fail(e, "reset exponents");
+    if ((e = slice(S->it_x0, S->it_mid0, S->tl_x0, S->tl_mid0, true, S->kid_x)) != cudaSuccess)
+        return cuda_fail(e, "slice x");
     if ((e = gemm(S->work1, S->n_work1, S->kid_s1, s1_flops)) != cudaSuccess) return cuda_fail(e, "stage-1 slice gemm");
-    if ((e = slice(S->n_vb_op + S->n_vb_x, S->n_vb_mid, S->kid_mid)) != cudaSuccess)
+    if ((e = slice(S->it_mid0, S->it_end, S->tl_mid0, S->tl_end, false, S->kid_mid)) != cudaSuccess)
         return cuda_fail(e, "slice intermediates");
     if (S->s2_vs > 0 && (e = cudaMemsetAsync(S->s2, 0, sizeof(int64_t) * S->s2_vs * nvec, st)) != cudaSuccess)
         return cuda_fail(e, "zero stage-2 sums");

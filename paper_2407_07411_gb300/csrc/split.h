@@ -57,7 +57,11 @@ struct SGemm {
     int32_t kind;               // 0: store sign*F (stage 1), 1: atomic add (stage 2)
     int32_t sign;
     int32_t fshift;             // s: F = round(2^s * accumulated slice sums)
-    int32_t pad;
+    int32_t x2_period;          // stage 1: row r feeds vector r % x2_period of its stage-2 operand
+    // stage 1: the epilogue raises the exponents of the stage-2 vectors its rows feed,
+    //   ap_exp[x2_exp + r % x2_period] = max(..., msb(F)+1 + op_exp[er_off + r]
+    //                                         + ap_exp[ec_off + col] - (14 + s))
+    int64_t x2_exp, er_off, ec_off;
 };
 
 struct SWork { int32_t gemm, mtile, ntile, k0, k1, pad; };
@@ -83,7 +87,14 @@ struct SJob {
     int32_t seg0, nseg;
 };
 
-struct SVBlock { int32_t job, v0; };   // 8 vectors of one job (one per warp)
+// Rows (term t, vector v) of one segment of one job.
+struct SSlab { int64_t rows; int32_t job, seg, kbase, pad; };
+// A run of up to SPL_ROWS_PER_ITEM rows of one slab, the unit of work of the slicer.
+struct SItem { int64_t r0; int32_t slab, nrows; };
+constexpr int SPL_ROWS_PER_ITEM = 64;
+// Output tile of the digit pass: vectors [8 vg, 8 vg + 8) x K [k0, k0 + SPL_TILE_K) of one job.
+struct STile { int32_t job, vg, k0, pad; };
+constexpr int SPL_TILE_K = 256;
 
 // Output block of the wave function and the stage-2 sums that land on it.
 struct SBlock { int64_t y_off; int32_t rows, cols, p0, np; };
@@ -97,8 +108,11 @@ struct SplitHost {
     std::vector<SWork> w1, w2;
     std::vector<SBlock> blocks;
     std::vector<SPart> parts;
-    std::vector<SVBlock> vb;
-    int64_t n_vb_op = 0, n_vb_x = 0, n_vb_mid = 0;
+    std::vector<SSlab> slabs;
+    std::vector<SItem> items;   // [operator items | x items | intermediate items] (exponent pass)
+    int64_t it_op0 = 0, it_x0 = 0, it_mid0 = 0, it_end = 0;
+    std::vector<STile> tiles;   // [operator tiles | x tiles | intermediate tiles] (digit pass)
+    int64_t tl_op0 = 0, tl_x0 = 0, tl_mid0 = 0, tl_end = 0;
     int64_t op_sl = 0, op_ex = 0, ap_sl_vs = 0, ap_ex_vs = 0, s1_vs = 0, s2_vs = 0;
 };
 
