@@ -36,6 +36,13 @@ int dmrg_heff_profile_read(dmrg_heff_t h, dmrg_kernel_stat* stats, int32_t* n);
  * device in TFLOP/s: every SM runs independent MMA chains for ~20 ms. */
 int dmrg_probe_fp64_peak(double* tflops);
 
+/* Failure-detection self-test: one GPU thread waits, with the same bounded mbarrier wait
+ * the slice-GEMM kernel uses, on a barrier that nothing arrives at, for at most
+ * wait_cycles SM clock cycles (1 .. 2^34).  Returns DMRG_ERR_DEVICE_TIMEOUT when the wait
+ * ran out and the status word was written, as designed; the CUDA context stays usable.
+ * The paper has no counterpart. */
+int dmrg_selftest_wait_timeout(int64_t wait_cycles);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,8 @@ _PREC = {"fp64": PREC_FP64, "split_bf16": PREC_SPLIT_BF16, "split": PREC_SPLIT_B
 SYMBOLS = ("dmrg_heff_create", "dmrg_heff_dim", "dmrg_heff_flops", "dmrg_heff_plan_dump",
            "dmrg_heff_apply", "dmrg_heff_apply_host", "dmrg_heff_diagonal", "dmrg_davidson",
            "dmrg_heff_destroy", "dmrg_strerror", "dmrg_last_error", "dmrg_heff_profile",
-           "dmrg_heff_profile_read", "dmrg_probe_fp64_peak", "dmrg_heff_apply_noalloc")
+           "dmrg_heff_profile_read", "dmrg_probe_fp64_peak", "dmrg_heff_apply_noalloc",
+           "dmrg_selftest_wait_timeout")
 
 
 class Opts(ctypes.Structure):
@@ -73,6 +74,7 @@ _lib.dmrg_last_error.restype = ctypes.c_char_p
 _lib.dmrg_heff_profile.argtypes = [_P, _i32]
 _lib.dmrg_heff_profile_read.argtypes = [_P, ctypes.POINTER(KernelStat), ctypes.POINTER(_i32)]
 _lib.dmrg_probe_fp64_peak.argtypes = [ctypes.POINTER(_f64)]
+_lib.dmrg_selftest_wait_timeout.argtypes = [_i64]
 _lib.dmrg_heff_apply_noalloc.argtypes = [_P, _i32, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _i64, _P, _i64,
                                          _P, _P, _P]
 _lib.dmrg_heff_apply_noalloc.restype = ctypes.c_int

@@ -27,6 +27,8 @@ struct DavidsonState {
     double *V = nullptr, *W = nullptr, *X = nullptr, *R = nullptr, *C = nullptr, *T = nullptr;
     double *diag = nullptr, *S = nullptr, *U = nullptr, *theta = nullptr, *small = nullptr, *partial = nullptr;
     int64_t n_chunks = 0;
+    int mmax = 0, kbmax = 0, block = 0, k_eig = 0;   // sizes the buffers were allocated for
+    bool diag_ready = false;
     ~DavidsonState() {
         double* p[] = {V, W, X, R, C, T, diag, S, U, theta, small, partial};
         for (double* q : p)
@@ -154,7 +156,6 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ S, in
     double* Z = sm + MAX_BASIS * ld;     // eigenvectors, M x ld
     __shared__ double cs[MAX_BASIS / 2], sn[MAX_BASIS / 2];
     __shared__ int pp[MAX_BASIS / 2], qq[MAX_BASIS / 2];
-    __shared__ double s_off, s_tot;
     __shared__ int order[MAX_BASIS];
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int e = tid; e < M * M; e += nt) {
@@ -164,33 +165,25 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ S, in
     }
     __syncthreads();
     const int half = M / 2;
-    for (int sweep = 0; sweep < 60; ++sweep) {
-        if (tid == 0) { s_off = 0.0; s_tot = 0.0; }
+    __shared__ int s_rot;
+    for (int sweep = 0; sweep < 40 && M >= 2; ++sweep) {
+        if (tid == 0) s_rot = 0;
         __syncthreads();
-        double off = 0.0, tot = 0.0;
-        for (int e = tid; e < M * M; e += nt) {
-            const int i = e / M, j = e % M;
-            const double a = A[i * ld + j];
-            tot += a * a;
-            if (i != j) off += a * a;
-        }
-        atomicAdd(&s_off, off);   // convergence test only; rotations are order-free
-        atomicAdd(&s_tot, tot);
-        __syncthreads();
-        if (!(s_off > 1e-32 * s_tot) || M < 2) break;
         for (int r = 0; r < M - 1; ++r) {
             if (tid < half) {
                 const int k = tid;
                 const int a = k == 0 ? 0 : ((k - 1 + r) % (M - 1)) + 1;
                 const int b = ((M - 2 - k + r) % (M - 1)) + 1;
                 const int p = min(a, b), q = max(a, b);
-                const double apq = A[p * ld + q];
+                const double apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
                 double c = 1.0, s = 0.0;
-                if (fabs(apq) > 1e-300) {
-                    const double tau = (A[q * ld + q] - A[p * ld + p]) / (2.0 * apq);
+                // rotate only while the off-diagonal entry is above rounding level
+                if (fabs(apq) > 1e-18 * sqrt(fabs(app * aqq)) + 1e-300) {
+                    const double tau = (aqq - app) / (2.0 * apq);
                     const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
                     c = 1.0 / sqrt(1.0 + t * t);
                     s = t * c;
+                    s_rot = 1;
                 }
                 pp[k] = p; qq[k] = q; cs[k] = c; sn[k] = s;
             }
@@ -217,6 +210,8 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ S, in
             }
             __syncthreads();
         }
+        if (s_rot == 0) break;   // a sweep without rotations: converged to rounding level
+        __syncthreads();
     }
     if (tid == 0) {                      // ascending order of the m real eigenvalues
         for (int i = 0; i < m; ++i) order[i] = i;
@@ -341,28 +336,39 @@ extern "C" int dmrg_davidson(dmrg_heff_t hh, int32_t k_eig, double tol, int32_t 
     if (dim < int64_t(k_eig) + block) return fail(DMRG_ERR_INVALID_ARG, "problem smaller than k_eig + block");
     if (!x_inout || !evals) return fail(DMRG_ERR_INVALID_ARG, "null x_inout or evals");
 
-    h->release_davidson();
-    h->dav = new DavidsonState();
+    const int kbmax = k_eig > block ? k_eig : block;
+    if (h->dav && (h->dav->mmax != mmax || h->dav->kbmax != kbmax || h->dav->block != block ||
+                   h->dav->k_eig != k_eig))
+        h->release_davidson();   // buffers are kept between calls of the same shape
+    int rc;
+    const size_t jac_smem = sizeof(double) * 2 * MAX_BASIS * (MAX_BASIS + 1);
+    cudaStream_t st = nullptr;
+    if (!h->dav) {
+        h->dav = new DavidsonState();
+        DavidsonState* s = h->dav;
+        s->n_chunks = (dim + DOT_CHUNK - 1) / DOT_CHUNK;
+        s->mmax = mmax; s->kbmax = kbmax; s->block = block; s->k_eig = k_eig;
+        auto al = [&](double** p, int64_t n, const char* w) {
+            cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(double) * (n > 0 ? n : 1));
+            return e == cudaSuccess ? DMRG_OK : cuda_fail(e, w);
+        };
+        if ((rc = al(&s->V, int64_t(mmax) * dim, "V")) || (rc = al(&s->W, int64_t(mmax) * dim, "W")) ||
+            (rc = al(&s->X, int64_t(kbmax) * dim, "X")) || (rc = al(&s->R, int64_t(kbmax) * dim, "R")) ||
+            (rc = al(&s->C, int64_t(block) * dim, "C")) || (rc = al(&s->T, int64_t(k_eig + block) * dim, "T")) ||
+            (rc = al(&s->diag, dim, "diag")) || (rc = al(&s->S, mmax * mmax, "S")) ||
+            (rc = al(&s->U, mmax * mmax, "U")) || (rc = al(&s->theta, mmax, "theta")) ||
+            (rc = al(&s->small, 4096, "small")) || (rc = al(&s->partial, s->n_chunks * MAX_BASIS * MAXQ, "partials"))) {
+            h->release_davidson();
+            return rc;
+        }
+        cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, int(jac_smem));
+    }
     DavidsonState* s = h->dav;
     Run run{h, s, dim, mmax};
-    s->n_chunks = (dim + DOT_CHUNK - 1) / DOT_CHUNK;
-    const int kbmax = k_eig > block ? k_eig : block;
-    auto al = [&](double** p, int64_t n, const char* w) {
-        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(double) * (n > 0 ? n : 1));
-        return e == cudaSuccess ? DMRG_OK : cuda_fail(e, w);
-    };
-    int rc;
-    if ((rc = al(&s->V, int64_t(mmax) * dim, "V")) || (rc = al(&s->W, int64_t(mmax) * dim, "W")) ||
-        (rc = al(&s->X, int64_t(kbmax) * dim, "X")) || (rc = al(&s->R, int64_t(kbmax) * dim, "R")) ||
-        (rc = al(&s->C, int64_t(block) * dim, "C")) || (rc = al(&s->T, int64_t(k_eig + block) * dim, "T")) ||
-        (rc = al(&s->diag, dim, "diag")) || (rc = al(&s->S, mmax * mmax, "S")) || (rc = al(&s->U, mmax * mmax, "U")) ||
-        (rc = al(&s->theta, mmax, "theta")) || (rc = al(&s->small, 4096, "small")) ||
-        (rc = al(&s->partial, s->n_chunks * MAX_BASIS * MAXQ, "partials")))
-        return rc;
-    const size_t jac_smem = sizeof(double) * 2 * MAX_BASIS * (MAX_BASIS + 1);
-    cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, int(jac_smem));
-    cudaStream_t st = nullptr;
-    if ((rc = h->diagonal(s->diag, st))) return rc;
+    if (!s->diag_ready) {
+        if ((rc = h->diagonal(s->diag, st))) return rc;
+        s->diag_ready = true;
+    }
 
     // start block
     int m = 0;
@@ -449,6 +455,5 @@ extern "C" int dmrg_davidson(dmrg_heff_t hh, int32_t k_eig, double tol, int32_t 
         info->resid_max = rmax;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     }
-    h->release_davidson();
     return converged || n_iter > 0 ? DMRG_OK : DMRG_ERR_NOT_CONVERGED;
 }

@@ -313,18 +313,24 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t ph) {
     return ok != 0;
 }
 
-// Bounded wait; false on timeout or when another role has aborted.
-__device__ __forceinline__ bool mbar_wait(UmmaSmem& sm, uint64_t* b, uint32_t ph, int* status) {
+// Bounded wait; false on timeout (recorded in *abort and the status word) or when
+// another role of the CTA has aborted.
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t* b, uint32_t ph, long long limit, volatile int* abort,
+                                                int* status) {
     const long long t0 = clock64();
     while (!mbar_try(b, ph)) {
-        if (sm.abort) return false;
-        if (clock64() - t0 > UM_WAIT_CYCLES) {
-            sm.abort = 1;
+        if (*abort) return false;
+        if (clock64() - t0 > limit) {
+            *abort = 1;
             atomicExch(status, DMRG_ERR_DEVICE_TIMEOUT);
             return false;
         }
     }
     return true;
+}
+
+__device__ __forceinline__ bool mbar_wait(UmmaSmem& sm, uint64_t* b, uint32_t ph, int* status) {
+    return mbar_wait_limit(b, ph, UM_WAIT_CYCLES, &sm.abort, status);
 }
 
 __device__ __forceinline__ bool mbar_wait_final(uint64_t* b, uint32_t ph) {
@@ -561,6 +567,19 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UM_TMEM_COLS));
+    }
+}
+
+// Self-test of the timeout path: one thread waits on an mbarrier that nothing arrives
+// at, with the bounded wait of the slice GEMM.
+__global__ void k_wait_selftest(int* status, long long limit) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ volatile int abort;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (mbar_wait_limit(&bar, 0, limit, &abort, status)) atomicExch(status, 1);
     }
 }
 
@@ -1017,6 +1036,29 @@ int Handle::check_status() {
     }
     return DMRG_OK;
 }
+
+}  // namespace dmrg
+
+extern "C" int dmrg_selftest_wait_timeout(int64_t wait_cycles) {
+    using namespace dmrg;
+    if (wait_cycles < 1 || wait_cycles > (int64_t(1) << 34)) return fail(DMRG_ERR_INVALID_ARG, "wait_cycles range");
+    int* st = nullptr;
+    cudaError_t e = cudaMalloc(&st, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "self-test status");
+    int v = 0;
+    e = cudaMemset(st, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 32>>>(st, static_cast<long long>(wait_cycles));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&v, st, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(st);
+    if (e != cudaSuccess) return cuda_fail(e, "self-test");
+    if (v == DMRG_ERR_DEVICE_TIMEOUT) return fail(DMRG_ERR_DEVICE_TIMEOUT, "bounded wait ran out (self-test)");
+    return v == 1 ? DMRG_OK : fail(DMRG_ERR_CUDA, "self-test status not written");
+}
+
+namespace dmrg {
 
 void Handle::release_split() {
     delete split;
