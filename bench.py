@@ -34,6 +34,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 NCU_TRAFFIC = {
     # k_fp64_tiles, mid workload: (280.8 + 358.1) / 2 MB per launch (profiles/fp64_tiles_mid.md)
     "7ea6b95187a63352e09b039a09918be5e89d2a14561ebf2f4d93d0eae118ec22": 319.5e6,
+    # k_umma, mid workload: (495.3 + 1417.1) / 2 MB per launch (profiles/split_umma_mid.md)
+    "c67c0afcc471dfd948533386ab0c1ea267f83204aecd40649b7d86b3ad7a42e8": 956.2e6,
 }
 
 
