@@ -71,6 +71,10 @@ typedef struct {
 /* Build only the host-side plan: no device memory is touched, so the handle works
  * without a GPU; only dmrg_heff_dim, _flops, _plan_dump and _destroy may be called. */
 #define DMRG_FLAG_PLAN_ONLY 1
+/* Launch every apply kernel directly instead of replaying a CUDA graph.  By default
+ * each apply is captured once per (x, y, nvec) into a graph (up to 64 per handle) and
+ * replayed; per-kernel timing (dmrg_heff_profile) also launches directly. */
+#define DMRG_FLAG_NO_GRAPH 2
 
 typedef struct {
     /* outputs */
@@ -118,7 +122,8 @@ int dmrg_heff_plan_dump(dmrg_heff_t h, int64_t* buf, int64_t* n_rows);
 
 /* y = H_eff x for nvec vectors (1 <= nvec <= max_nvec); x, y device pointers of
  * nvec*dim doubles, x and y must not overlap; runs asynchronously on `stream`
- * (a cudaStream_t, NULL = legacy default stream) as one CUDA-graph launch. */
+ * (a cudaStream_t, NULL = legacy default stream) as one CUDA-graph launch (the graph is
+ * captured at the first call with these x, y, nvec; see DMRG_FLAG_NO_GRAPH). */
 int dmrg_heff_apply(dmrg_heff_t h, const double* x, double* y, int32_t nvec, void* stream);
 
 /* Same as dmrg_heff_apply with host x and y: copies x in, applies, copies y out and

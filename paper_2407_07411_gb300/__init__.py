@@ -23,6 +23,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 PREC_FP64 = 0
 PREC_SPLIT_BF16 = 1
 FLAG_PLAN_ONLY = 1
+FLAG_NO_GRAPH = 2
 _PREC = {"fp64": PREC_FP64, "split_bf16": PREC_SPLIT_BF16, "split": PREC_SPLIT_BF16}
 
 #: Every symbol the C ABI exports (include/dmrg_heff.h).
@@ -124,7 +125,8 @@ class HEff:
     """Handle of one effective Hamiltonian on the current CUDA device."""
 
     def __init__(self, left, right, target, coef, delta, parity, a_off, b_off, op_data,
-                 precision: str = "fp64", max_nvec: int = 1, n_slices: int = 0, plan_only: bool = False):
+                 precision: str = "fp64", max_nvec: int = 1, n_slices: int = 0, plan_only: bool = False,
+                 graphs: bool = True):
         self._h = None
         arr = lambda a, dt: np.ascontiguousarray(np.asarray(a, dtype=dt))
         self._left = arr(left, np.int32).reshape(-1, 3)
@@ -136,7 +138,7 @@ class HEff:
         b_off = arr(b_off, np.int64).reshape(T, len(self._right))
         op_data = arr(op_data, np.float64)
         opts = Opts(_PREC[precision] if isinstance(precision, str) else int(precision), n_slices, max_nvec,
-                    FLAG_PLAN_ONLY if plan_only else 0)
+                    (FLAG_PLAN_ONLY if plan_only else 0) | (0 if graphs else FLAG_NO_GRAPH))
         h = ctypes.c_void_p()
         _check(_lib.dmrg_heff_create(_ptr(self._left), len(self._left), _ptr(self._right), len(self._right),
                                      int(target[0]), int(target[1]), _ptr(coef), _ptr(delta), _ptr(parity),

@@ -29,6 +29,18 @@ struct DiagJob {
 struct SplitState;
 struct DavidsonState;
 
+// One instantiated CUDA graph of an apply for a given (x, y, nvec), and the launch
+// accounting it stands for.
+struct GraphEntry {
+    const double* x;
+    double* y;
+    int32_t nvec;
+    cudaGraphExec_t exec;
+    uint64_t last_use;
+    std::vector<int> kids;
+    std::vector<double> flops, bytes;
+};
+
 // Launch accounting of one handle: counts, algorithmic flops/bytes and (when
 // timing) CUDA-event pairs recorded on the launching stream.
 struct Profiler {
@@ -41,6 +53,9 @@ struct Profiler {
     size_t pool_used = 0;
     std::vector<Rec> recs;
     bool timing = false;
+    bool counting = true;            // false while an apply is being captured
+    std::vector<int> cap_kids;       // launches seen during a capture
+    std::vector<double> cap_flops, cap_bytes;
     int kernel_id(const char* name);
     cudaEvent_t take_event();
     void begin(int id, cudaStream_t st, double f, double b, Pending* p);
@@ -72,6 +87,13 @@ struct Handle : dmrg_heff {
     SplitState* split = nullptr;
     DavidsonState* dav = nullptr;
     Profiler prof;
+    // CUDA graphs of the apply (DMRG_FLAG_NO_GRAPH disables them)
+    bool use_graphs = true;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<GraphEntry> graphs;
+    uint64_t graph_clock = 0;
+    int apply_graph(const double* x, double* y, int32_t nvec, cudaStream_t st);
+    int apply_direct(const double* x, double* y, int32_t nvec, cudaStream_t st);
     int kid_s1 = -1, kid_s2 = -1, kid_red = -1;
     double s1_flops = 0, s2_flops = 0, s1_bytes = 0, s2_bytes = 0;
 

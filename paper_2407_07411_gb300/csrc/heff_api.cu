@@ -99,8 +99,60 @@ int Handle::apply(const double* x, double* y, int32_t nvec, cudaStream_t st) {
     const char* yb = reinterpret_cast<const char*>(y);
     const size_t bytes = sizeof(double) * plan.dim * nvec;
     if (xb < yb + bytes && yb < xb + bytes) return fail(DMRG_ERR_INVALID_ARG, "x and y overlap");
+    if (use_graphs && !prof.timing) return apply_graph(x, y, nvec, st);
+    return apply_direct(x, y, nvec, st);
+}
+
+int Handle::apply_direct(const double* x, double* y, int32_t nvec, cudaStream_t st) {
     if (precision == DMRG_PREC_FP64) return apply_fp64(x, y, nvec, st);
     return apply_split(x, y, nvec, st);
+}
+
+// Replays the instantiated graph of this (x, y, nvec), capturing it on the handle's own
+// stream first if needed (least recently used graph evicted beyond 64).
+int Handle::apply_graph(const double* x, double* y, int32_t nvec, cudaStream_t st) {
+    GraphEntry* g = nullptr;
+    for (GraphEntry& e : graphs)
+        if (e.x == x && e.y == y && e.nvec == nvec) g = &e;
+    cudaError_t e;
+    if (!g) {
+        if (!cap_stream && (e = cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "capture stream");
+        if (graphs.size() >= 64) {
+            size_t lru = 0;
+            for (size_t i = 1; i < graphs.size(); ++i)
+                if (graphs[i].last_use < graphs[lru].last_use) lru = i;
+            cudaGraphExecDestroy(graphs[lru].exec);
+            graphs.erase(graphs.begin() + lru);
+        }
+        if ((e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return cuda_fail(e, "begin capture");
+        prof.counting = false;
+        prof.cap_kids.clear(); prof.cap_flops.clear(); prof.cap_bytes.clear();
+        const int rc = apply_direct(x, y, nvec, cap_stream);
+        prof.counting = true;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(cap_stream, &graph);
+        if (rc != DMRG_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "end capture");
+        GraphEntry ge{x, y, nvec, nullptr, 0, prof.cap_kids, prof.cap_flops, prof.cap_bytes};
+        e = cudaGraphInstantiate(&ge.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "instantiate graph");
+        graphs.push_back(ge);
+        g = &graphs.back();
+    }
+    g->last_use = ++graph_clock;
+    if ((e = cudaGraphLaunch(g->exec, st)) != cudaSuccess) return cuda_fail(e, "graph launch");
+    for (size_t i = 0; i < g->kids.size(); ++i) {
+        prof.launches[g->kids[i]] += 1;
+        prof.flops[g->kids[i]] += g->flops[i];
+        prof.bytes[g->kids[i]] += g->bytes[i];
+    }
+    return DMRG_OK;
 }
 
 Handle::~Handle() {
@@ -110,6 +162,8 @@ Handle::~Handle() {
         if (p) cudaFree(p);
     release_split();
     release_davidson();
+    for (GraphEntry& g : graphs) cudaGraphExecDestroy(g.exec);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
 }
 
 }  // namespace dmrg
@@ -129,7 +183,7 @@ int dmrg_heff_create(const int32_t* left, int32_t nl, const int32_t* right, int3
     if (opts) o = *opts;
     if (o.precision != DMRG_PREC_FP64 && o.precision != DMRG_PREC_SPLIT_BF16)
         return dmrg::fail(DMRG_ERR_INVALID_ARG, "unknown precision");
-    if (o.max_nvec < 1 || o.max_nvec > 64 || (o.flags & ~DMRG_FLAG_PLAN_ONLY) != 0)
+    if (o.max_nvec < 1 || o.max_nvec > 64 || (o.flags & ~(DMRG_FLAG_PLAN_ONLY | DMRG_FLAG_NO_GRAPH)) != 0)
         return dmrg::fail(DMRG_ERR_INVALID_ARG, "max_nvec must be in [1, 64], unknown flags must be 0");
     if (op_len > 0 && !op_data) return dmrg::fail(DMRG_ERR_INVALID_ARG, "null op_data");
     Handle* h = new (std::nothrow) Handle();
@@ -145,6 +199,7 @@ int dmrg_heff_create(const int32_t* left, int32_t nl, const int32_t* right, int3
     h->max_nvec = o.max_nvec;
     h->n_slices = o.n_slices;
     h->plan_only = (o.flags & DMRG_FLAG_PLAN_ONLY) != 0;
+    h->use_graphs = (o.flags & DMRG_FLAG_NO_GRAPH) == 0;
     if (h->plan_only) {
         if (o.precision == DMRG_PREC_SPLIT_BF16) {   // host-side split plan and its bounds proof
             dmrg::SplitHost sh;

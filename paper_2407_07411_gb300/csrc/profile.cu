@@ -26,8 +26,12 @@ cudaEvent_t Profiler::take_event() {
 }
 
 void Profiler::begin(int id, cudaStream_t st, double f, double b, Pending* p) {
-    launches[id] += 1; flops[id] += f; bytes[id] += b;
     p->id = id; p->start = p->stop = nullptr;
+    if (!counting) {   // capturing a graph: remember the launch, count it at replay
+        cap_kids.push_back(id); cap_flops.push_back(f); cap_bytes.push_back(b);
+        return;
+    }
+    launches[id] += 1; flops[id] += f; bytes[id] += b;
     if (!timing) return;
     p->start = take_event();
     if (p->start) cudaEventRecord(p->start, st);
