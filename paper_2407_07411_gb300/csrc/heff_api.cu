@@ -202,13 +202,15 @@ int dmrg_heff_create(const int32_t* left, int32_t nl, const int32_t* right, int3
     h->use_graphs = (o.flags & DMRG_FLAG_NO_GRAPH) == 0;
     if (h->plan_only) {
         if (o.precision == DMRG_PREC_SPLIT_BF16) {   // host-side split plan and its bounds proof
-            dmrg::SplitHost sh;
-            rc = dmrg::build_split_plan(h->plan, sh, &err);
-            if (rc != DMRG_OK) {
-                delete h;
-                return dmrg::fail(rc, err);
+            for (int nv = 1; nv <= h->max_nvec; ++nv) {
+                dmrg::SplitHost sh;
+                rc = dmrg::build_split_plan(h->plan, nv, sh, &err);
+                if (rc != DMRG_OK) {
+                    delete h;
+                    return dmrg::fail(rc, err);
+                }
+                h->split_host_bytes = sh.op_sl * 2 + sh.ap_sl_vs * 2 + sh.s1_vs * 8 + sh.s2_vs * 8;
             }
-            h->split_host_bytes = sh.op_sl * 2 + sh.ap_sl_vs * 2 + sh.s1_vs * 8 + sh.s2_vs * 8;
         }
         *out = h;
         return DMRG_OK;

@@ -1,8 +1,10 @@
 // Split-precision (Ozaki) H_eff*psi on the tcgen05 tensor cores (the arithmetic is
 // described in split.h).  Kernels:
-//   k_slice   FP64 or int64 operand vectors -> 5 BF16 digit slices in the UMMA
-//             canonical K-major layout, plus the vector's exponent (integer ops only
-//             for int64 sources).
+//   k_slice_max, k_slice_digits
+//             FP64 or int64 operand vectors -> 6 BF16 digit slices in the UMMA
+//             canonical K-major layout, plus the vectors' exponents (integer ops only
+//             for int64 sources).  The nvec vectors of an apply are stacked inside
+//             every GEMM (along N in stage 1, along M or N in stage 2).
 //   k_umma    warp-specialised slice GEMM: one producer thread streams 72 KB stages
 //             with cp.async.bulk, one thread issues the 42 tcgen05.mma of each K tile
 //             into five TMEM accumulators, eight epilogue warps drain the
@@ -39,13 +41,8 @@ struct UmmaSmem {
     volatile int abort;
 };
 
-struct SplitState {
-    uint16_t* op_sl = nullptr;
-    int32_t* op_ex = nullptr;
-    uint16_t* ap_sl = nullptr;
-    int32_t* ap_ex = nullptr;
-    int64_t* s1 = nullptr;
-    int64_t* s2 = nullptr;
+// Device descriptors of the split plan for one number of stacked vectors.
+struct SplitDevPlan {
     SGemm* gemms = nullptr;
     SWork* work1 = nullptr;
     SWork* work2 = nullptr;
@@ -56,15 +53,31 @@ struct SplitState {
     STile* tiles = nullptr;     // [operator tiles | x tiles | intermediate tiles]
     SBlock* blocks = nullptr;
     SPart* parts = nullptr;
-    int32_t* status = nullptr;
     int64_t n_work1 = 0, n_work2 = 0, n_blocks = 0;
     int64_t it_op0 = 0, it_x0 = 0, it_mid0 = 0, it_end = 0;      // item ranges
     int64_t tl_op0 = 0, tl_x0 = 0, tl_mid0 = 0, tl_end = 0;      // tile ranges
-    int64_t ap_sl_vs = 0, ap_ex_vs = 0, s1_vs = 0, s2_vs = 0;
+    int64_t ap_ex_len = 0, s2_len = 0;
+    double s1_bytes = 0, s2_bytes = 0;                           // algorithmic DRAM bytes
+    void release() {
+        void* p[] = {gemms, work1, work2, segs, jobs, slabs, items, tiles, blocks, parts};
+        for (void* q : p)
+            if (q) cudaFree(q);
+    }
+};
+
+struct SplitState {
+    uint16_t* op_sl = nullptr;   // operator slices (shared by every plan)
+    int32_t* op_ex = nullptr;
+    uint16_t* ap_sl = nullptr;   // per-apply buffers, sized for the largest plan
+    int32_t* ap_ex = nullptr;
+    int64_t* s1 = nullptr;
+    int64_t* s2 = nullptr;
+    int32_t* status = nullptr;
+    std::vector<SplitDevPlan> plans;   // plans[nv - 1]
     int kid_x = -1, kid_s1 = -1, kid_mid = -1, kid_s2 = -1, kid_fin = -1;
     ~SplitState() {
-        void* p[] = {op_sl, op_ex, ap_sl, ap_ex, s1, s2, gemms, work1, work2, segs, jobs, slabs, items, tiles, blocks,
-                     parts, status};
+        for (SplitDevPlan& d : plans) d.release();
+        void* p[] = {op_sl, op_ex, ap_sl, ap_ex, s1, s2, status};
         for (void* q : p)
             if (q) cudaFree(q);
     }
@@ -175,7 +188,8 @@ __global__ void __launch_bounds__(256) k_slice_max(SliceArgs a) {
         for (int rr = warp; rr < I.nrows; rr += 8) {
             const int64_t r = I.r0 + rr;
             const int t = int(r / J.nvalid), vec = int(r - int64_t(t) * J.nvalid);
-            const int64_t base = g.off + t * g.ts + int64_t(vec) * g.vs;
+            const int vg = vec / g.vper, vr = vec - vg * g.vper;
+            const int64_t base = g.off + t * g.ts + vg * g.vgs + int64_t(vr) * g.vs;
             int E = INT_MIN;
             for (int k = lane; k < g.kc; k += 32) E = max(E, exp_f64(src[base + k * g.ks]));
 #pragma unroll
@@ -204,87 +218,100 @@ struct TileArgs {
     int nvec;
 };
 
-// Pass 2: digits of 8 vectors x 256 K of one job relative to the vectors' exponents.
-// Each thread decodes one K column (segment, term, entry) and forms the digits of its
-// 8 entries; the CTA assembles whole 8x8 core matrices of every slice in shared memory
-// and writes them as contiguous 512-byte runs (positions outside the valid vectors and
-// K stay zero from set-up).
-__global__ void __launch_bounds__(SPL_TILE_K) k_slice_digits(TileArgs a) {
-    __shared__ __align__(16) uint16_t sd[SPL_S][8][SPL_TILE_K];
-    __shared__ int32_t s_E[8];
-    const int tid = threadIdx.x;
-    for (int64_t item = blockIdx.x; item < a.n_tiles * a.nvec; item += gridDim.x) {
+// Pass 2: digits of 8 vectors x 256 K of one job relative to the vectors' exponents,
+// one warp per such item.  For each 32-K sub-tile every lane decodes one K column
+// (segment, term, entry) and forms the digits of its 8 entries; the warp assembles the
+// 8x8 core matrices of every slice in its own shared-memory patch and writes them as
+// 16-byte chunks (512 contiguous bytes per slice and sub-tile).  Positions outside the
+// valid vectors and K stay zero from set-up.
+constexpr int DIG_WARPS = 8;
+
+__global__ void __launch_bounds__(32 * DIG_WARPS) k_slice_digits(TileArgs a) {
+    __shared__ __align__(16) uint16_t sd_all[DIG_WARPS][SPL_S][8][SPL_TK];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint16_t (*sd)[8][SPL_TK] = sd_all[warp];
+    const int64_t n_items = a.n_tiles * a.nvec;
+    for (int64_t item = int64_t(blockIdx.x) * DIG_WARPS + warp; item < n_items;
+         item += int64_t(gridDim.x) * DIG_WARPS) {
         const STile T = a.tiles[item / a.nvec];
         const int v = int(item % a.nvec);
         const SJob J = a.jobs[T.job];
         const int32_t* oex = J.out_buf ? a.ap_ex + int64_t(v) * a.ap_ex_vs : a.op_ex;
-        if (tid < 8) {
-            const int vec = 8 * T.vg + tid;
-            s_E[tid] = vec < J.nvalid ? oex[J.out_exp + vec] : 0;
-        }
-        __syncthreads();
-        const int K = T.k0 + tid;
-        int d[8][SPL_S];
+        const int nv = min(8, J.nvalid - 8 * T.vg);
+        int E[8];
 #pragma unroll
-        for (int vv = 0; vv < 8; ++vv)
-#pragma unroll
-            for (int q = 0; q < SPL_S; ++q) d[vv][q] = 0;
-        if (K < J.K) {
-            int kb = 0, sg = J.seg0;
-            for (; sg < J.seg0 + J.nseg - 1; ++sg) {
-                const int ext = a.segs[sg].kc * a.segs[sg].nt;
-                if (K < kb + ext) break;
-                kb += ext;
-            }
-            const SSeg g = a.segs[sg];
-            const int t = (K - kb) / g.kc, k = (K - kb) - t * g.kc;
-            const int64_t base = g.off + t * g.ts + k * g.ks;
-            const int nv = min(8, J.nvalid - 8 * T.vg);
-            if (g.is_i64) {   // all loads first, then the integer digit arithmetic
-                const int64_t* s1 = a.s1 + int64_t(v) * a.s1_vs + base + int64_t(8 * T.vg) * g.vs;
-                const int32_t* er = a.op_ex + g.er_off + int64_t(t) * g.er_ts + 8 * T.vg;
-                const int ec = a.ap_ex[int64_t(v) * a.ap_ex_vs + g.ec_off + k] - g.e_off;
-                long long F[8];
-                int e[8];
-#pragma unroll
-                for (int vv = 0; vv < 8; ++vv) {
-                    F[vv] = vv < nv ? s1[int64_t(vv) * g.vs] : 0;
-                    e[vv] = vv < nv ? er[vv] : 0;
-                }
-#pragma unroll
-                for (int vv = 0; vv < 8; ++vv)
-                    if (F[vv] != 0) digits_i64(F[vv], e[vv] + ec, s_E[vv], d[vv]);
-            } else {
-                const double* src = (g.space == SP_OPS ? a.ops : a.x + int64_t(v) * a.x_vs) + base +
-                                    int64_t(8 * T.vg) * g.vs;
-                double xv[8];
-#pragma unroll
-                for (int vv = 0; vv < 8; ++vv) xv[vv] = vv < nv ? src[int64_t(vv) * g.vs] : 0.0;
-#pragma unroll
-                for (int vv = 0; vv < 8; ++vv) digits_f64(xv[vv], s_E[vv], d[vv]);
-            }
-        }
-#pragma unroll
-        for (int vv = 0; vv < 8; ++vv)
-#pragma unroll
-            for (int q = 0; q < SPL_S; ++q) sd[q][vv][tid] = digit_bf16(d[vv][q], q);
-        __syncthreads();
-        // write: per slice and K tile, the 4 core matrices of this 8-vector group are 512
-        // contiguous bytes: core kg holds rows vv = 0..7 of K [32 kt + 8 kg, +8)
+        for (int vv = 0; vv < 8; ++vv) E[vv] = vv < nv ? oex[J.out_exp + 8 * T.vg + vv] : 0;
         uint16_t* out = J.out_buf ? a.ap_sl + int64_t(v) * a.ap_sl_vs : a.op_sl;
-        const int kt0 = T.k0 / SPL_TK;
-        const int nkt = min(SPL_TILE_K / SPL_TK, J.kt - kt0);
         const int64_t tile_elems = int64_t(J.rows_tile) * SPL_TK;
         const int vt = (8 * T.vg) / J.rows_tile, rg = ((8 * T.vg) % J.rows_tile) >> 3;
-        for (int c = tid; c < SPL_S * nkt * 32; c += SPL_TILE_K) {   // 32 chunks of 16 B per slice-tile
-            const int q = c / (nkt * 32), rem = c - q * (nkt * 32), kt = rem >> 5, ch = rem & 31;
-            const int kg = ch >> 3, vv = ch & 7;
-            const int64_t dst = J.out_tiles + ((int64_t(vt) * J.kt + kt0 + kt) * SPL_S + q) * tile_elems +
-                                (rg * 4 + kg) * 64 + vv * 8;
-            const uint4 val = *reinterpret_cast<const uint4*>(&sd[q][vv][kt * SPL_TK + kg * 8]);
-            *reinterpret_cast<uint4*>(out + dst) = val;
+        const int kt0 = T.k0 / SPL_TK;
+        const int nkt = min(SPL_TILE_K / SPL_TK, J.kt - kt0);
+        for (int kt = 0; kt < nkt; ++kt) {
+            const int K = T.k0 + kt * SPL_TK + lane;
+            int d[8][SPL_S];
+#pragma unroll
+            for (int vv = 0; vv < 8; ++vv)
+#pragma unroll
+                for (int q = 0; q < SPL_S; ++q) d[vv][q] = 0;
+            if (K < J.K) {
+                int kb = 0, sg = J.seg0;
+                for (; sg < J.seg0 + J.nseg - 1; ++sg) {
+                    const int ext = a.segs[sg].kc * a.segs[sg].nt;
+                    if (K < kb + ext) break;
+                    kb += ext;
+                }
+                const SSeg g = a.segs[sg];
+                const int t = (K - kb) / g.kc, k = (K - kb) - t * g.kc;
+                const int64_t base = g.off + t * g.ts + k * g.ks;
+                int vg = (8 * T.vg) / g.vper, vr = 8 * T.vg - vg * g.vper;
+                if (g.is_i64) {   // loads first, then the integer digit arithmetic
+                    const int64_t* s1 = a.s1 + int64_t(v) * a.s1_vs;
+                    const int32_t* cex = a.ap_ex + int64_t(v) * a.ap_ex_vs + g.ec_off + k;
+                    const int32_t* er = a.op_ex + g.er_off + int64_t(t) * g.er_ts;
+                    long long F[8];
+                    int e[8];
+#pragma unroll
+                    for (int vv = 0; vv < 8; ++vv) {
+                        F[vv] = vv < nv ? s1[base + vg * g.vgs + int64_t(vr) * g.vs] : 0;
+                        e[vv] = vv < nv ? er[vr] + cex[int64_t(vg) * g.ec_vgs] - g.e_off : 0;
+                        if (++vr == g.vper) {
+                            vr = 0;
+                            ++vg;
+                        }
+                    }
+#pragma unroll
+                    for (int vv = 0; vv < 8; ++vv)
+                        if (F[vv] != 0) digits_i64(F[vv], e[vv], E[vv], d[vv]);
+                } else {
+                    const double* src = g.space == SP_OPS ? a.ops : a.x + int64_t(v) * a.x_vs;
+                    double xv[8];
+#pragma unroll
+                    for (int vv = 0; vv < 8; ++vv) {
+                        xv[vv] = vv < nv ? src[base + vg * g.vgs + int64_t(vr) * g.vs] : 0.0;
+                        if (++vr == g.vper) {
+                            vr = 0;
+                            ++vg;
+                        }
+                    }
+#pragma unroll
+                    for (int vv = 0; vv < 8; ++vv) digits_f64(xv[vv], E[vv], d[vv]);
+                }
+            }
+#pragma unroll
+            for (int vv = 0; vv < 8; ++vv)
+#pragma unroll
+                for (int q = 0; q < SPL_S; ++q) sd[q][vv][lane] = digit_bf16(d[vv][q], q);
+            __syncwarp();
+            // lane -> core matrix kg = lane / 8 (K [8 kg, +8)), row vv = lane % 8
+            const int kg = lane >> 3, vv = lane & 7;
+#pragma unroll
+            for (int q = 0; q < SPL_S; ++q) {
+                const int64_t dst = J.out_tiles + ((int64_t(vt) * J.kt + kt0 + kt) * SPL_S + q) * tile_elems +
+                                    (rg * 4 + kg) * 64 + vv * 8;
+                *reinterpret_cast<uint4*>(out + dst) = *reinterpret_cast<const uint4*>(&sd[q][vv][kg * 8]);
+            }
+            __syncwarp();
         }
-        __syncthreads();
     }
 }
 
@@ -534,11 +561,21 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
                 if (G.kind == 0) {
                     int64_t* D = a.s1 + int64_t(v) * a.s1_vs + G.d_off + int64_t(r) * G.ldd;
                     const int32_t* cex = a.ap_ex + int64_t(v) * a.ap_ex_vs + G.ec_off;
-                    int emax = INT_MIN;
+                    // stage-2 vector of entry (r, c): (c / colgroup) * period + r % period
+                    int32_t* x2 = a.ap_ex + int64_t(v) * a.ap_ex_vs + G.x2_exp + r % G.x2_period;
+                    const int eoff = a.op_ex[G.er_off + r] - (14 + G.fshift);
+                    int emax = INT_MIN, grp = cbase / G.x2_colgroup;
+                    int next = (grp + 1) * G.x2_colgroup;   // first column of the next group
 #pragma unroll
                     for (int j = 0; j < UM_EPI_COLS; ++j) {
                         const int c = cbase + j;
                         if (c < G.N) {
+                            if (c >= next) {
+                                if (emax != INT_MIN) atomicMax(x2 + grp * G.x2_period, emax + eoff);
+                                emax = INT_MIN;
+                                ++grp;
+                                next += G.x2_colgroup;
+                            }
                             D[c] = G.sign > 0 ? acc[j] : -acc[j];
                             if (acc[j] != 0) {
                                 const unsigned long long u = acc[j] < 0 ? static_cast<unsigned long long>(-acc[j])
@@ -547,9 +584,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
                             }
                         }
                     }
-                    if (emax != INT_MIN && G.x2_exp >= 0)
-                        atomicMax(a.ap_ex + int64_t(v) * a.ap_ex_vs + G.x2_exp + r % G.x2_period,
-                                  emax + a.op_ex[G.er_off + r] - (14 + G.fshift));
+                    if (emax != INT_MIN) atomicMax(x2 + grp * G.x2_period, emax + eoff);
                 } else {
                     unsigned long long* D = reinterpret_cast<unsigned long long*>(a.s2 + int64_t(v) * a.s2_vs +
                                                                                   G.d_off + int64_t(r) * G.ldd);
@@ -598,10 +633,11 @@ __global__ void k_finalize(const SBlock* __restrict__ blocks, const SPart* __res
         double sum = 0.0;
         for (int p = B.p0; p < B.p0 + B.np; ++p) {
             const SPart P = parts[p];
-            const long long F = S2[P.acc_off + e];
+            const int ri = v * P.rstack + i, cj = v * P.cstack + j;
+            const long long F = S2[P.acc_off + int64_t(ri) * P.ld + cj];
             if (F == 0) continue;
-            const int er = (P.er_buf ? aex : op_ex)[P.er_off + i];
-            const int ec = (P.ec_buf ? aex : op_ex)[P.ec_off + j];
+            const int er = (P.er_buf ? aex : op_ex)[P.er_off + ri];
+            const int ec = (P.ec_buf ? aex : op_ex)[P.ec_off + cj];
             sum += scalbn(static_cast<double>(F), er + ec - P.e_off);
         }
         y[int64_t(v) * dim + B.y_off + e] = sum;
@@ -642,13 +678,16 @@ int validate_split_plan(const Plan& P, const SplitHost& H, std::string* err) {
             const SSeg& g = H.segs[s];
             K += int64_t(g.kc) * g.nt;
             if (J.nvalid == 0 || g.kc <= 0 || g.nt <= 0) continue;
-            const int64_t last = g.off + (g.nt - 1) * g.ts + int64_t(J.nvalid - 1) * g.vs + int64_t(g.kc - 1) * g.ks;
-            const int64_t lim = g.space == SP_OPS ? P.ops_len : (g.space == SP_X ? P.dim : P.scratch_len);
+            if (g.vper < 1) return bad("vector grouping");
+            const int ngrp = (J.nvalid - 1) / g.vper, rmax = std::min(J.nvalid, g.vper) - 1;
+            const int64_t last = g.off + (g.nt - 1) * g.ts + ngrp * g.vgs + int64_t(rmax) * g.vs + int64_t(g.kc - 1) * g.ks;
+            const int64_t lim = g.space == SP_OPS ? P.ops_len
+                                                  : (g.space == SP_X ? P.dim * H.nv : P.scratch_len * H.nv);
             if (g.off < 0 || last >= lim) return bad("slice source");
             if (g.is_i64) {
                 if (g.space != SP_SCR) return bad("int64 source space");
-                if (g.er_off < 0 || g.er_off + int64_t(g.nt - 1) * g.er_ts + J.nvalid > H.op_ex) return bad("row exps");
-                if (g.ec_off < 0 || g.ec_off + g.kc > H.ap_ex_vs) return bad("col exps");
+                if (g.er_off < 0 || g.er_off + int64_t(g.nt - 1) * g.er_ts + rmax + 1 > H.op_ex) return bad("row exps");
+                if (g.ec_off < 0 || g.ec_off + int64_t(ngrp) * g.ec_vgs + g.kc > H.ap_ex_vs) return bad("col exps");
             }
         }
         if (K != J.K) return bad("job K");
@@ -665,7 +704,10 @@ int validate_split_plan(const Plan& P, const SplitHost& H, std::string* err) {
             const int64_t dend = G.d_off + int64_t(G.M - 1) * G.ldd + G.N;
             if (G.ldd < G.N || dend > (G.kind == 0 ? H.s1_vs : H.s2_vs)) return false;
             if (G.kind == 0) {   // stage-1 epilogue exponent reads and raises
-                if (G.x2_exp < 0 || G.x2_period <= 0 || G.x2_exp + G.x2_period > H.ap_ex_vs) return false;
+                const int64_t ngrp = G.x2_colgroup > 0 ? (G.N - 1) / G.x2_colgroup : -1;
+                if (G.x2_exp < 0 || G.x2_period <= 0 || ngrp < 0 ||
+                    G.x2_exp + (ngrp + 1) * G.x2_period > H.ap_ex_vs)
+                    return false;
                 if (G.er_off < 0 || G.er_off + G.M > H.op_ex || G.ec_off < 0 || G.ec_off + G.N > H.ap_ex_vs)
                     return false;
             }
@@ -690,14 +732,15 @@ int validate_split_plan(const Plan& P, const SplitHost& H, std::string* err) {
     for (const SBlock& B : H.blocks)
         for (int p = B.p0; p < B.p0 + B.np; ++p) {
             const SPart& Q = H.parts[p];
-            if (Q.acc_off + int64_t(B.rows) * B.cols > H.s2_vs) return bad("finalize sums");
-            if (Q.er_off + B.rows > (Q.er_buf ? H.ap_ex_vs : H.op_ex)) return bad("finalize row exps");
-            if (Q.ec_off + B.cols > (Q.ec_buf ? H.ap_ex_vs : H.op_ex)) return bad("finalize col exps");
+            const int64_t rmax = int64_t(H.nv - 1) * Q.rstack + B.rows, cmax = int64_t(H.nv - 1) * Q.cstack + B.cols;
+            if (Q.ld < cmax || Q.acc_off + (rmax - 1) * Q.ld + cmax > H.s2_vs) return bad("finalize sums");
+            if (Q.er_off + rmax > (Q.er_buf ? H.ap_ex_vs : H.op_ex)) return bad("finalize row exps");
+            if (Q.ec_off + cmax > (Q.ec_buf ? H.ap_ex_vs : H.op_ex)) return bad("finalize col exps");
         }
     return DMRG_OK;
 }
 
-int build_split_plan(const Plan& P, SplitHost& H, std::string* err) {
+int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err) {
     std::vector<SGemm>& gemms = H.gemms;
     std::vector<SSeg>& segs = H.segs;
     std::vector<SJob>& jobs = H.jobs;
@@ -735,8 +778,18 @@ int build_split_plan(const Plan& P, SplitHost& H, std::string* err) {
     auto seg = [](int space, int64_t off, int64_t ts, int64_t vs, int64_t ks, int kc, int nt) {
         SSeg s{};
         s.space = space; s.off = off; s.ts = ts; s.vs = vs; s.ks = ks; s.kc = kc; s.nt = nt;
+        s.vper = 1 << 30;   // one vector group unless stacked
         return s;
     };
+    // the same entries for nv stacked Davidson vectors: vector v*per + r of vector v
+    auto stacked = [](SSeg s, int per, int64_t vgs, int32_t ec_vgs) {
+        s.vper = per; s.vgs = vgs; s.ec_vgs = ec_vgs;
+        return s;
+    };
+    if (nv < 1 || nv > 64) {
+        *err = "nvec out of range";
+        return DMRG_ERR_INVALID_ARG;
+    }
     if (int64_t(P.groups.size()) > (int64_t(1) << 30)) {
         *err = "too many groups";
         return DMRG_ERR_INVALID_ARG;
@@ -751,20 +804,25 @@ int build_split_plan(const Plan& P, SplitHost& H, std::string* err) {
         const int n = int(G.terms.size());
         SGemm m{};
         int64_t lt, le, rt, re;
-        if (G.order == 0) {   // X_g = A_stack (n a x b) * x_q (b x c)
-            m.M = n * G.a; m.N = G.c;
+        // the nv Davidson vectors stack along N: column v*c + j is column j of vector v
+        if (G.order == 0) {   // X_g = A_stack (n a x b) * [x_q^(v)] (b x nv c)
+            m.M = n * G.a; m.N = nv * G.c;
             op_jobs.push_back(add_job(0, SPL_TM, m.M, G.b, {seg(SP_OPS, G.a_stack, 0, G.b, 1, G.b, 1)}, &lt, &le));
-            x_jobs.push_back(add_job(1, SPL_TN, m.N, G.b, {seg(SP_X, B.off, 0, 1, G.c, G.b, 1)}, &rt, &re));
-        } else {              // Z_g^T = B_stack (n d x c) * x_q^T (c x b)
-            m.M = n * G.d; m.N = G.b;
+            x_jobs.push_back(add_job(1, SPL_TN, m.N, G.b,
+                                     {stacked(seg(SP_X, B.off, 0, 1, G.c, G.b, 1), G.c, P.dim, 0)}, &rt, &re));
+        } else {              // Z_g^T = B_stack (n d x c) * [x_q^(v)T] (c x nv b)
+            m.M = n * G.d; m.N = nv * G.b;
             op_jobs.push_back(add_job(0, SPL_TM, m.M, G.c, {seg(SP_OPS, G.b_stack, 0, G.c, 1, G.c, 1)}, &lt, &le));
-            x_jobs.push_back(add_job(1, SPL_TN, m.N, G.c, {seg(SP_X, B.off, 0, G.c, 1, G.c, 1)}, &rt, &re));
+            x_jobs.push_back(add_job(1, SPL_TN, m.N, G.c,
+                                     {stacked(seg(SP_X, B.off, 0, G.c, 1, G.c, 1), G.b, P.dim, 0)}, &rt, &re));
         }
         m.l_tiles = lt; m.r_tiles = rt; m.l_buf = 0; m.r_buf = 1;
         m.kt = int32_t(cdiv(G.order == 0 ? G.b : G.c, SPL_TK));
-        m.d_off = G.scratch; m.ldd = m.N; m.kind = 0; m.sign = G.sign < 0 ? -1 : 1;
+        m.d_off = int64_t(nv) * G.scratch; m.ldd = m.N; m.kind = 0; m.sign = G.sign < 0 ? -1 : 1;
         m.fshift = fshift_for(G.order == 0 ? G.b : G.c);
-        m.er_off = le; m.ec_off = re; m.x2_period = G.order == 0 ? G.a : G.d; m.x2_exp = -1;
+        m.er_off = le; m.ec_off = re; m.x2_exp = -1;
+        m.x2_period = G.order == 0 ? G.a : G.d;
+        m.x2_colgroup = G.order == 0 ? G.c : G.b;
         s1_lexp[g] = le; s1_rexp[g] = re; s1_eoff[g] = 14 + m.fshift;
         const int32_t gi = int32_t(gemms.size());
         gemms.push_back(m);
@@ -784,15 +842,20 @@ int build_split_plan(const Plan& P, SplitHost& H, std::string* err) {
                 const Group& G = P.groups[g];
                 if (G.order != order) continue;
                 const int n = int(G.terms.size());
-                if (order == 0) {  // L = X_g rows (int64), R = B_t rows (operator)
-                    SSeg s = seg(SP_SCR, G.scratch, int64_t(G.a) * G.c, G.c, 1, G.c, n);
+                const int64_t sc = int64_t(nv) * G.scratch;
+                if (order == 0) {  // L = X_g rows (int64), vectors stacked along M; R = B_t rows
+                    // vector v*a + i, entry (t, k) = X_g[t a + i][v c + k]  (X_g is n a x nv c)
+                    SSeg s = stacked(seg(SP_SCR, sc, int64_t(G.a) * nv * G.c, int64_t(nv) * G.c, 1, G.c, n),
+                                     G.a, G.c, G.c);
                     s.is_i64 = 1; s.er_off = s1_lexp[g]; s.er_ts = G.a; s.ec_off = s1_rexp[g]; s.e_off = s1_eoff[g];
                     lseg.push_back(s);
                     rseg.push_back(seg(SP_OPS, G.b_stack, int64_t(G.d) * G.c, G.c, 1, G.c, n));
                     K += int64_t(G.c) * n;
-                } else {           // L = c_t A_t rows (operator), R = Z_g^T rows (int64)
+                } else {           // L = c_t A_t rows; R = Z_g^T rows (int64), vectors stacked along N
+                    // vector v*d + j, entry (t, k) = Z_g^T[t d + j][v b + k]  (Z_g^T is n d x nv b)
                     lseg.push_back(seg(SP_OPS, G.a_stack, int64_t(G.a) * G.b, G.b, 1, G.b, n));
-                    SSeg s = seg(SP_SCR, G.scratch, int64_t(G.d) * G.b, G.b, 1, G.b, n);
+                    SSeg s = stacked(seg(SP_SCR, sc, int64_t(G.d) * nv * G.b, int64_t(nv) * G.b, 1, G.b, n),
+                                     G.d, G.b, G.b);
                     s.is_i64 = 1; s.er_off = s1_lexp[g]; s.er_ts = G.d; s.ec_off = s1_rexp[g]; s.e_off = s1_eoff[g];
                     rseg.push_back(s);
                     K += int64_t(G.b) * n;
@@ -804,7 +867,9 @@ int build_split_plan(const Plan& P, SplitHost& H, std::string* err) {
                 return DMRG_ERR_INVALID_ARG;
             }
             SGemm m{};
-            m.M = O.rows; m.N = O.cols; m.kt = int32_t(cdiv(K, SPL_TK));
+            m.M = order == 0 ? nv * O.rows : O.rows;
+            m.N = order == 0 ? O.cols : nv * O.cols;
+            m.kt = int32_t(cdiv(K, SPL_TK));
             int64_t lt, le, rt, re;
             const int lbuf = order == 0 ? 1 : 0, rbuf = order == 0 ? 0 : 1;
             int32_t lj = add_job(lbuf, SPL_TM, m.M, K, lseg, &lt, &le);
@@ -816,7 +881,12 @@ int build_split_plan(const Plan& P, SplitHost& H, std::string* err) {
             m.l_tiles = lt; m.r_tiles = rt; m.l_buf = lbuf; m.r_buf = rbuf;
             m.d_off = s2; m.ldd = m.N; m.kind = 1; m.sign = 1;
             m.fshift = fshift_for(K);
-            parts.push_back({s2, le, re, lbuf, rbuf, 14 + m.fshift, 0});
+            SPart part{};
+            part.acc_off = s2; part.er_off = le; part.ec_off = re; part.er_buf = lbuf; part.ec_buf = rbuf;
+            part.e_off = 14 + m.fshift; part.ld = m.N;
+            part.rstack = order == 0 ? O.rows : 0;
+            part.cstack = order == 0 ? 0 : O.cols;
+            parts.push_back(part);
             blocks[o].np += 1;
             s2 += int64_t(m.M) * m.N;
             gemms.push_back(m);
@@ -882,8 +952,9 @@ int build_split_plan(const Plan& P, SplitHost& H, std::string* err) {
     H.op_ex = op_ex + 1;
     H.ap_sl_vs = cdiv(ap_sl, 64) * 64;
     H.ap_ex_vs = cdiv(ap_ex, 4) * 4 + 4;
-    H.s1_vs = P.scratch_len;
+    H.s1_vs = P.scratch_len * nv;
     H.s2_vs = s2;
+    H.nv = nv;
     return validate_split_plan(P, H, err);
 }
 
@@ -891,33 +962,22 @@ int Handle::init_split(const double*, const int64_t*, const int64_t*, const doub
     const Plan& P = plan;
     SplitState* S = new SplitState();
     split = S;
-    SplitHost H;
     std::string err;
-    int rc0 = build_split_plan(P, H, &err);
-    if (rc0 != DMRG_OK) return fail(rc0, err);
-    const std::vector<SGemm>& gemms = H.gemms;
-    const std::vector<SSeg>& segs = H.segs;
-    const std::vector<SJob>& jobs = H.jobs;
-    const std::vector<SWork>& w1 = H.w1;
-    const std::vector<SWork>& w2 = H.w2;
-    const std::vector<SBlock>& blocks = H.blocks;
-    const std::vector<SPart>& parts = H.parts;
-    const std::vector<SSlab>& slabs = H.slabs;
-    const std::vector<SItem>& items = H.items;
-    const std::vector<STile>& tiles = H.tiles;
-    const int64_t op_sl = H.op_sl, op_ex = H.op_ex;
-    S->it_op0 = H.it_op0; S->it_x0 = H.it_x0; S->it_mid0 = H.it_mid0; S->it_end = H.it_end;
-    S->tl_op0 = H.tl_op0; S->tl_x0 = H.tl_x0; S->tl_mid0 = H.tl_mid0; S->tl_end = H.tl_end;
-    S->n_work1 = int64_t(w1.size());
-    S->n_work2 = int64_t(w2.size());
-    S->n_blocks = int64_t(blocks.size());
-    S->ap_sl_vs = H.ap_sl_vs;
-    S->ap_ex_vs = H.ap_ex_vs;
-    S->s1_vs = H.s1_vs;
-    S->s2_vs = H.s2_vs;
-
-    // device buffers
-    const size_t nv = size_t(max_nvec);
+    // one plan per number of stacked vectors; operator slices are identical in all of them
+    std::vector<SplitHost> hosts(static_cast<size_t>(max_nvec));
+    int64_t ap_sl = 0, ap_ex = 0, s1 = 0, s2 = 0;
+    for (int nv = 1; nv <= max_nvec; ++nv) {
+        SplitHost& H = hosts[size_t(nv - 1)];
+        const int rc0 = build_split_plan(P, nv, H, &err);
+        if (rc0 != DMRG_OK) return fail(rc0, err);
+        if (H.op_sl != hosts[0].op_sl || H.op_ex != hosts[0].op_ex)
+            return fail(DMRG_ERR_BOUNDS, "operator slice layout differs between plans");
+        ap_sl = std::max(ap_sl, H.ap_sl_vs);
+        ap_ex = std::max(ap_ex, H.ap_ex_vs);
+        s1 = std::max(s1, H.s1_vs);
+        s2 = std::max(s2, H.s2_vs);
+    }
+    const int64_t op_sl = hosts[0].op_sl, op_ex = hosts[0].op_ex;
     auto al = [&](void** p, size_t bytes, const char* w) {
         *p = nullptr;
         if (bytes == 0) return DMRG_OK;
@@ -933,22 +993,42 @@ int Handle::init_split(const double*, const int64_t*, const int64_t*, const doub
     int rc;
     if ((rc = al((void**)&S->op_sl, sizeof(uint16_t) * op_sl, "operator slices")) ||
         (rc = al((void**)&S->op_ex, sizeof(int32_t) * op_ex, "operator exponents")) ||
-        (rc = al((void**)&S->ap_sl, sizeof(uint16_t) * S->ap_sl_vs * nv, "apply slices")) ||
-        (rc = al((void**)&S->ap_ex, sizeof(int32_t) * S->ap_ex_vs * nv, "apply exponents")) ||
-        (rc = al((void**)&S->s1, sizeof(int64_t) * S->s1_vs * nv, "stage-1 int64 results")) ||
-        (rc = al((void**)&S->s2, sizeof(int64_t) * S->s2_vs * nv, "stage-2 int64 sums")) ||
-        (rc = up((void**)&S->gemms, gemms.data(), sizeof(SGemm) * gemms.size(), "split gemms")) ||
-        (rc = up((void**)&S->work1, w1.data(), sizeof(SWork) * w1.size(), "split work")) ||
-        (rc = up((void**)&S->work2, w2.data(), sizeof(SWork) * w2.size(), "split work")) ||
-        (rc = up((void**)&S->segs, segs.data(), sizeof(SSeg) * segs.size(), "slice segments")) ||
-        (rc = up((void**)&S->jobs, jobs.data(), sizeof(SJob) * jobs.size(), "slice jobs")) ||
-        (rc = up((void**)&S->slabs, slabs.data(), sizeof(SSlab) * slabs.size(), "slice slabs")) ||
-        (rc = up((void**)&S->items, items.data(), sizeof(SItem) * items.size(), "slice items")) ||
-        (rc = up((void**)&S->tiles, tiles.data(), sizeof(STile) * tiles.size(), "slice tiles")) ||
-        (rc = up((void**)&S->blocks, blocks.data(), sizeof(SBlock) * blocks.size(), "output blocks")) ||
-        (rc = up((void**)&S->parts, parts.data(), sizeof(SPart) * parts.size(), "output parts")) ||
+        (rc = al((void**)&S->ap_sl, sizeof(uint16_t) * ap_sl, "apply slices")) ||
+        (rc = al((void**)&S->ap_ex, sizeof(int32_t) * ap_ex, "apply exponents")) ||
+        (rc = al((void**)&S->s1, sizeof(int64_t) * s1, "stage-1 int64 results")) ||
+        (rc = al((void**)&S->s2, sizeof(int64_t) * s2, "stage-2 int64 sums")) ||
         (rc = al((void**)&S->status, sizeof(int32_t), "status")))
         return rc;
+    S->plans.resize(size_t(max_nvec));
+    for (int nv = 1; nv <= max_nvec; ++nv) {
+        const SplitHost& H = hosts[size_t(nv - 1)];
+        SplitDevPlan& D = S->plans[size_t(nv - 1)];
+        if ((rc = up((void**)&D.gemms, H.gemms.data(), sizeof(SGemm) * H.gemms.size(), "split gemms")) ||
+            (rc = up((void**)&D.work1, H.w1.data(), sizeof(SWork) * H.w1.size(), "split work")) ||
+            (rc = up((void**)&D.work2, H.w2.data(), sizeof(SWork) * H.w2.size(), "split work")) ||
+            (rc = up((void**)&D.segs, H.segs.data(), sizeof(SSeg) * H.segs.size(), "slice segments")) ||
+            (rc = up((void**)&D.jobs, H.jobs.data(), sizeof(SJob) * H.jobs.size(), "slice jobs")) ||
+            (rc = up((void**)&D.slabs, H.slabs.data(), sizeof(SSlab) * H.slabs.size(), "slice slabs")) ||
+            (rc = up((void**)&D.items, H.items.data(), sizeof(SItem) * H.items.size(), "slice items")) ||
+            (rc = up((void**)&D.tiles, H.tiles.data(), sizeof(STile) * H.tiles.size(), "slice tiles")) ||
+            (rc = up((void**)&D.blocks, H.blocks.data(), sizeof(SBlock) * H.blocks.size(), "output blocks")) ||
+            (rc = up((void**)&D.parts, H.parts.data(), sizeof(SPart) * H.parts.size(), "output parts")))
+            return rc;
+        D.n_work1 = int64_t(H.w1.size());
+        D.n_work2 = int64_t(H.w2.size());
+        D.n_blocks = int64_t(H.blocks.size());
+        D.it_op0 = H.it_op0; D.it_x0 = H.it_x0; D.it_mid0 = H.it_mid0; D.it_end = H.it_end;
+        D.tl_op0 = H.tl_op0; D.tl_x0 = H.tl_x0; D.tl_mid0 = H.tl_mid0; D.tl_end = H.tl_end;
+        D.ap_ex_len = H.ap_ex_vs;
+        D.s2_len = H.s2_vs;
+        // algorithmic DRAM bytes of the two slice-GEMM launches: slice tiles read once
+        // (12 B per entry) plus the int64 results written (stage 1) or added (stage 2)
+        for (size_t gi = 0; gi < H.gemms.size(); ++gi) {
+            const SGemm& m = H.gemms[gi];
+            const double bytes = 12.0 * (double(m.M) + m.N) * m.kt * SPL_TK + 8.0 * double(m.M) * m.N;
+            (m.kind == 0 ? D.s1_bytes : D.s2_bytes) += bytes;
+        }
+    }
     cudaError_t e = cudaMemset(S->status, 0, sizeof(int32_t));
     if (e != cudaSuccess) return cuda_fail(e, "status");
     e = cudaFuncSetAttribute(k_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(UmmaSmem)));
@@ -960,17 +1040,18 @@ int Handle::init_split(const double*, const int64_t*, const int64_t*, const doub
     S->kid_fin = prof.kernel_id("split_finalize");
     // slice buffers start at zero (padding is never written again), exponents at "none"
     if (op_sl > 0 && (e = cudaMemset(S->op_sl, 0, sizeof(uint16_t) * op_sl)) != cudaSuccess) return cuda_fail(e, "zero slices");
-    if (S->ap_sl_vs > 0 && (e = cudaMemset(S->ap_sl, 0, sizeof(uint16_t) * S->ap_sl_vs * nv)) != cudaSuccess)
-        return cuda_fail(e, "zero slices");
+    if (ap_sl > 0 && (e = cudaMemset(S->ap_sl, 0, sizeof(uint16_t) * ap_sl)) != cudaSuccess) return cuda_fail(e, "zero slices");
     if ((e = cudaMemset(S->op_ex, 0xC0, sizeof(int32_t) * op_ex)) != cudaSuccess) return cuda_fail(e, "exponents");
-    // operator slices, once
-    if (S->it_x0 > S->it_op0) {
-        SliceArgs sa{S->items + S->it_op0, S->it_x0 - S->it_op0, S->slabs, S->jobs, S->segs, d_ops, nullptr, 0,
+    // operator slices, once (from the first plan; every plan has the same operator jobs)
+    const SplitDevPlan& D0 = S->plans[0];
+    if (D0.it_x0 > D0.it_op0) {
+        SliceArgs sa{D0.items + D0.it_op0, D0.it_x0 - D0.it_op0, D0.slabs, D0.jobs, D0.segs, d_ops, nullptr, 0,
                      nullptr, 0, S->op_sl, S->ap_sl, 0, S->op_ex, S->ap_ex, 0, 1};
-        TileArgs ta{S->tiles + S->tl_op0, S->tl_x0 - S->tl_op0, S->jobs, S->segs, d_ops, nullptr, 0, nullptr, 0,
+        TileArgs ta{D0.tiles + D0.tl_op0, D0.tl_x0 - D0.tl_op0, D0.jobs, D0.segs, d_ops, nullptr, 0, nullptr, 0,
                     S->op_sl, S->ap_sl, 0, S->op_ex, S->ap_ex, 0, 1};
-        k_slice_max<<<unsigned(std::min<int64_t>(S->it_x0 - S->it_op0, int64_t(n_sm) * 16)), 256>>>(sa);
-        k_slice_digits<<<unsigned(std::min<int64_t>(S->tl_x0 - S->tl_op0, int64_t(n_sm) * 16)), SPL_TILE_K>>>(ta);
+        k_slice_max<<<unsigned(std::min<int64_t>(D0.it_x0 - D0.it_op0, int64_t(n_sm) * 16)), 256>>>(sa);
+        k_slice_digits<<<unsigned(std::min<int64_t>(cdiv(D0.tl_x0 - D0.tl_op0, DIG_WARPS), int64_t(n_sm) * 16)),
+                         32 * DIG_WARPS>>>(ta);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return cuda_fail(e, "operator slicing");
@@ -978,47 +1059,52 @@ int Handle::init_split(const double*, const int64_t*, const int64_t*, const doub
     return DMRG_OK;
 }
 
+// One split H_eff*psi for nvec stacked vectors: slice x, stage-1 slice GEMM (int64 results,
+// stage-2 exponents raised), slice intermediates, stage-2 slice GEMM (int64 sums), finalize.
 int Handle::apply_split(const double* x, double* y, int32_t nvec, cudaStream_t st) {
     SplitState* S = split;
+    const SplitDevPlan& D = S->plans[size_t(nvec - 1)];
     Profiler::Pending pe;
     cudaError_t e;
     const int64_t slice_grid_cap = int64_t(n_sm) * 16;
     auto slice = [&](int64_t i0, int64_t i1, int64_t t0, int64_t t1, bool with_max, int kid) {
         if (t1 == t0) return cudaSuccess;
-        SliceArgs sa{S->items + i0, i1 - i0, S->slabs, S->jobs, S->segs, d_ops, x, plan.dim, S->s1, S->s1_vs,
-                     S->op_sl, S->ap_sl, S->ap_sl_vs, S->op_ex, S->ap_ex, S->ap_ex_vs, nvec};
-        TileArgs ta{S->tiles + t0, t1 - t0, S->jobs, S->segs, d_ops, x, plan.dim, S->s1, S->s1_vs, S->op_sl,
-                    S->ap_sl, S->ap_sl_vs, S->op_ex, S->ap_ex, S->ap_ex_vs, nvec};
+        SliceArgs sa{D.items + i0, i1 - i0, D.slabs, D.jobs, D.segs, d_ops, x, 0, S->s1, 0,
+                     S->op_sl, S->ap_sl, 0, S->op_ex, S->ap_ex, 0, 1};
+        TileArgs ta{D.tiles + t0, t1 - t0, D.jobs, D.segs, d_ops, x, 0, S->s1, 0, S->op_sl,
+                    S->ap_sl, 0, S->op_ex, S->ap_ex, 0, 1};
         prof.begin(kid, st, 0.0, 0.0, &pe);
         if (with_max && i1 > i0)
-            k_slice_max<<<unsigned(std::min<int64_t>((i1 - i0) * nvec, slice_grid_cap)), 256, 0, st>>>(sa);
-        k_slice_digits<<<unsigned(std::min<int64_t>((t1 - t0) * nvec, slice_grid_cap)), SPL_TILE_K, 0, st>>>(ta);
+            k_slice_max<<<unsigned(std::min<int64_t>(i1 - i0, slice_grid_cap)), 256, 0, st>>>(sa);
+        k_slice_digits<<<unsigned(std::min<int64_t>(cdiv(t1 - t0, DIG_WARPS), slice_grid_cap)), 32 * DIG_WARPS, 0,
+                         st>>>(ta);
         prof.end(pe, st);
         return cudaGetLastError();
     };
-    auto gemm = [&](const SWork* w, int64_t nw, int kid, double flops) {
+    auto gemm = [&](const SWork* w, int64_t nw, int kid, double flops, double bytes) {
         if (nw == 0) return cudaSuccess;
-        UmmaArgs ua{w, nw, S->gemms, S->op_sl, S->ap_sl, S->ap_sl_vs, S->s1, S->s1_vs, S->s2, S->s2_vs,
-                    S->op_ex, S->ap_ex, S->ap_ex_vs, nvec, S->status};
-        prof.begin(kid, st, flops * nvec, 0.0, &pe);
-        k_umma<<<unsigned(std::min<int64_t>(nw * nvec, n_sm)), UM_THREADS, sizeof(UmmaSmem), st>>>(ua);
+        UmmaArgs ua{w, nw, D.gemms, S->op_sl, S->ap_sl, 0, S->s1, 0, S->s2, 0, S->op_ex, S->ap_ex, 0, 1, S->status};
+        prof.begin(kid, st, flops, bytes, &pe);
+        k_umma<<<unsigned(std::min<int64_t>(nw, n_sm)), UM_THREADS, sizeof(UmmaSmem), st>>>(ua);
         prof.end(pe, st);
         return cudaGetLastError();
     };
-    if ((e = cudaMemsetAsync(S->ap_ex, 0xC0, sizeof(int32_t) * S->ap_ex_vs * nvec, st)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(S->ap_ex, 0xC0, sizeof(int32_t) * D.ap_ex_len, st)) != cudaSuccess)
         return cuda_fail(e, "reset exponents");
-    if ((e = slice(S->it_x0, S->it_mid0, S->tl_x0, S->tl_mid0, true, S->kid_x)) != cudaSuccess)
+    if ((e = slice(D.it_x0, D.it_mid0, D.tl_x0, D.tl_mid0, true, S->kid_x)) != cudaSuccess)
         return cuda_fail(e, "slice x");
-    if ((e = gemm(S->work1, S->n_work1, S->kid_s1, s1_flops)) != cudaSuccess) return cuda_fail(e, "stage-1 slice gemm");
-    if ((e = slice(S->it_mid0, S->it_end, S->tl_mid0, S->tl_end, false, S->kid_mid)) != cudaSuccess)
+    if ((e = gemm(D.work1, D.n_work1, S->kid_s1, s1_flops * nvec, D.s1_bytes)) != cudaSuccess)
+        return cuda_fail(e, "stage-1 slice gemm");
+    if ((e = slice(D.it_mid0, D.it_end, D.tl_mid0, D.tl_end, false, S->kid_mid)) != cudaSuccess)
         return cuda_fail(e, "slice intermediates");
-    if (S->s2_vs > 0 && (e = cudaMemsetAsync(S->s2, 0, sizeof(int64_t) * S->s2_vs * nvec, st)) != cudaSuccess)
+    if (D.s2_len > 0 && (e = cudaMemsetAsync(S->s2, 0, sizeof(int64_t) * D.s2_len, st)) != cudaSuccess)
         return cuda_fail(e, "zero stage-2 sums");
-    if ((e = gemm(S->work2, S->n_work2, S->kid_s2, s2_flops)) != cudaSuccess) return cuda_fail(e, "stage-2 slice gemm");
-    if (S->n_blocks > 0) {
+    if ((e = gemm(D.work2, D.n_work2, S->kid_s2, s2_flops * nvec, D.s2_bytes)) != cudaSuccess)
+        return cuda_fail(e, "stage-2 slice gemm");
+    if (D.n_blocks > 0) {
         prof.begin(S->kid_fin, st, 0.0, 0.0, &pe);
-        k_finalize<<<dim3(unsigned(S->n_blocks), unsigned(nvec)), 256, 0, st>>>(
-            S->blocks, S->parts, S->s2, S->s2_vs, S->op_ex, S->ap_ex, S->ap_ex_vs, y, plan.dim);
+        k_finalize<<<dim3(unsigned(D.n_blocks), unsigned(nvec)), 256, 0, st>>>(D.blocks, D.parts, S->s2, 0, S->op_ex,
+                                                                              S->ap_ex, 0, y, plan.dim);
         prof.end(pe, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "finalize");
     }

@@ -57,24 +57,28 @@ struct SGemm {
     int32_t kind;               // 0: store sign*F (stage 1), 1: atomic add (stage 2)
     int32_t sign;
     int32_t fshift;             // s: F = round(2^s * accumulated slice sums)
-    int32_t x2_period;          // stage 1: row r feeds vector r % x2_period of its stage-2 operand
-    // stage 1: the epilogue raises the exponents of the stage-2 vectors its rows feed,
-    //   ap_exp[x2_exp + r % x2_period] = max(..., msb(F)+1 + op_exp[er_off + r]
-    //                                         + ap_exp[ec_off + col] - (14 + s))
+    int32_t x2_period;          // stage 1: entry (r, col) feeds stage-2 vector
+    int32_t x2_colgroup;        //   (col / x2_colgroup) * x2_period + r % x2_period
+    int32_t pad;
+    // stage 1: the epilogue raises the exponents of the stage-2 vectors its entries feed,
+    //   ap_exp[x2_exp + vector] = max(..., msb(F)+1 + op_exp[er_off + r]
+    //                                 + ap_exp[ec_off + col] - (14 + s))
     int64_t x2_exp, er_off, ec_off;
 };
 
 struct SWork { int32_t gemm, mtile, ntile, k0, k1, pad; };
 
-// A contraction run of a sliced operand: nt sub-blocks of kc entries; entry k of
-// sub-block t of vector v is at off + t*ts + v*vs + k*ks in its source space.  For int64
-// sources (stage-1 results F) the entry's value is F * 2^e with
-//     e = op_exp[er_off + t*er_ts + v] + ap_exp[ec_off + k] - e_off.
+// A contraction run of a sliced operand: nt sub-blocks of kc entries.  Vector v of the
+// operand splits into (vg, vr) = (v / vper, v % vper) -- the stacked Davidson vector
+// and the row or column inside it -- and entry k of sub-block t is at
+//     off + t*ts + vg*vgs + vr*vs + k*ks
+// in its source space.  For int64 sources (stage-1 results F) the entry is F * 2^e with
+//     e = op_exp[er_off + t*er_ts + vr] + ap_exp[ec_off + vg*ec_vgs + k] - e_off.
 struct SSeg {
-    int64_t off, ts, vs, ks;
+    int64_t off, ts, vs, ks, vgs;
     int64_t er_off, ec_off;
     int32_t space, kc, nt, er_ts;
-    int32_t is_i64, e_off;
+    int32_t is_i64, e_off, vper, ec_vgs;
 };
 
 // Slice one operand: vectors [0, npad) (valid below nvalid) along K [0, kt*32) (valid
@@ -96,9 +100,15 @@ constexpr int SPL_ROWS_PER_ITEM = 64;
 struct STile { int32_t job, vg, k0, pad; };
 constexpr int SPL_TILE_K = 256;
 
-// Output block of the wave function and the stage-2 sums that land on it.
+// Output block of the wave function and the stage-2 sums that land on it.  Entry (i, j)
+// of Davidson vector v is F[(v*rstack + i)*ld + v*cstack + j] with row exponent
+// [er_off + v*rstack + i] and column exponent [ec_off + v*cstack + j] (vectors stack
+// along the rows of A-first sums and along the columns of B-first sums).
 struct SBlock { int64_t y_off; int32_t rows, cols, p0, np; };
-struct SPart { int64_t acc_off, er_off, ec_off; int32_t er_buf, ec_buf, e_off, pad; };
+struct SPart {
+    int64_t acc_off, er_off, ec_off;
+    int32_t er_buf, ec_buf, e_off, ld, rstack, cstack;
+};
 
 // Host-side split plan.
 struct SplitHost {
@@ -114,11 +124,12 @@ struct SplitHost {
     std::vector<STile> tiles;   // [operator tiles | x tiles | intermediate tiles] (digit pass)
     int64_t tl_op0 = 0, tl_x0 = 0, tl_mid0 = 0, tl_end = 0;
     int64_t op_sl = 0, op_ex = 0, ap_sl_vs = 0, ap_ex_vs = 0, s1_vs = 0, s2_vs = 0;
+    int nv = 1;   // Davidson vectors stacked in this plan
 };
 
 int64_t cdiv(int64_t a, int64_t b);
 int32_t fshift_for(int64_t K);
-int build_split_plan(const Plan& P, SplitHost& H, std::string* err);
+int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err);
 int validate_split_plan(const Plan& P, const SplitHost& H, std::string* err);
 
 }  // namespace dmrg

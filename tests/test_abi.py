@@ -97,10 +97,12 @@ def test_plan_only_handle_refuses_compute():
     assert e.value.code == -1
 
 
-@pytest.mark.parametrize("name,n_terms", [("tiny", None), ("mid", None), ("heavy", 120), ("precision", 24)])
-def test_split_plan_bounds_proof(name, n_terms):
+@pytest.mark.parametrize("name,n_terms,nvec", [("tiny", None, 1), ("tiny", None, 8), ("mid", None, 4),
+                                               ("heavy", 120, 8), ("precision", 24, 2)])
+def test_split_plan_bounds_proof(name, n_terms, nvec):
     # the split planner proves on the host that every copy, slice write, exponent
-    # access and output store of its kernels stays inside its buffer
+    # access and output store of its kernels stays inside its buffer, for every number
+    # of stacked vectors up to nvec
     p = S.generate(name, n_terms=n_terms)
-    h = lib.HEff.from_problem(p, precision="split", plan_only=True)
+    h = lib.HEff.from_problem(p, precision="split", plan_only=True, max_nvec=nvec)
     assert h.dim == p.dim and h.plan_dump().tobytes() == heff.plan(p).tobytes()

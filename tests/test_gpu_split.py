@@ -35,6 +35,28 @@ def test_mid_full_and_deterministic():
     assert np.array_equal(gpu_apply(h, x), y)
 
 
+@pytest.mark.parametrize("name,n_terms,nvec", [("mid", 300, 8), ("heavy", 120, 8), ("tiny", None, 5)])
+def test_stacked_vectors(name, n_terms, nvec):
+    # nvec vectors stacked inside every slice GEMM; every call size up to max_nvec
+    p = S.generate(name, n_terms=n_terms)
+    h = split_handle(p, nvec)
+    X = p.random_vectors(nvec)
+    ref = heff.apply(p, X)
+    for nv in sorted({1, 2, nvec}):
+        Y = gpu_apply(h, X[:nv])
+        for v in range(nv):
+            assert rel_fro(Y[v], ref[v]) <= TOL_SPLIT
+
+
+def test_davidson_split_block8(tiny_problem, tiny_dense):
+    import torch
+    w = np.linalg.eigvalsh(tiny_dense)
+    h = split_handle(tiny_problem, 8)
+    ev, info = h.davidson(torch.from_numpy(tiny_problem.random_vectors(8)).cuda(), k_eig=3, block=8, tol=1e-9)
+    assert info["converged"]
+    np.testing.assert_allclose(ev, w[:3], rtol=1e-10, atol=0)
+
+
 def test_heavy_tailed_reduced():
     p = S.generate("heavy", n_terms=240)
     x = p.random_vectors(1)
