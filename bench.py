@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--precision", default="split", help="split (Ozaki BF16 slices, default) or fp64")
     ap.add_argument("--nvec", type=int, default=1)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--terms", type=int, default=None, help="fewer terms than the workload (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-davidson", action="store_true")
@@ -79,7 +80,8 @@ def workload_config(p, args, precision):
     import dmrg_synth as S
     cfg = S.CONFIGS[args.config]
     return {
-        "workload": f"{args.config}: two-site H_eff, D={cfg['D']} per block over {len(p.left)} (n,2Sz) sectors, "
+        "workload": f"{args.config}{'' if args.terms is None else f' (first {args.terms} terms)'}: two-site H_eff, "
+                    f"D={cfg['D']} per block over {len(p.left)} (n,2Sz) sectors, "
                     f"T={p.n_terms} terms, |psi|={p.dim}, seed {args.seed}",
         "D": cfg["D"], "sectors": int(len(p.left)), "terms": int(p.n_terms), "psi_dim": int(p.dim),
         "operator_GB": round(p.op_data.size * 8 / 1e9, 3), "nvec": args.nvec, "precision": precision,
@@ -282,7 +284,7 @@ def run_ours(args):
     import paper_2407_07411_gb300 as lib
 
     precision = {"fp64": "fp64", "split": "split_bf16", "split_bf16": "split_bf16"}[args.precision]
-    p = S.generate(args.config, seed=args.seed)
+    p = S.generate(args.config, seed=args.seed, n_terms=args.terms)
     h = lib.HEff.from_problem(p, precision=precision, max_nvec=args.nvec)
     flops_vec = h.flops
     fp64_peak = lib.probe_fp64_peak() if precision == "fp64" else None

@@ -900,11 +900,13 @@ int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err) {
             tile_kt += cdiv(gemms[gi].M, SPL_TM) * cdiv(gemms[gi].N, SPL_TN) * int64_t(gemms[gi].kt);
         int chunk = SPL_S2_KCHUNK;
         while (chunk > SPL_DRAIN_KT && tile_kt / chunk < 4 * 152) chunk /= 2;
+        // K chunk outermost: CTAs that run at the same time share the L tile of an M row
+        // across its N tiles and the R tile of an N column across its M tiles (L2 reuse)
         for (size_t gi = P.groups.size(); gi < gemms.size(); ++gi) {
             const SGemm& m = gemms[gi];
-            for (int mt = 0; mt < cdiv(m.M, SPL_TM); ++mt)
-                for (int nt = 0; nt < cdiv(m.N, SPL_TN); ++nt)
-                    for (int k0 = 0; k0 < m.kt; k0 += chunk)
+            for (int k0 = 0; k0 < m.kt; k0 += chunk)
+                for (int mt = 0; mt < cdiv(m.M, SPL_TM); ++mt)
+                    for (int nt = 0; nt < cdiv(m.N, SPL_TN); ++nt)
                         w2.push_back({int32_t(gi), mt, nt, k0, std::min(m.kt, k0 + chunk), 0});
         }
     }
