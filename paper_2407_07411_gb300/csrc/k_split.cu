@@ -27,19 +27,37 @@ constexpr int UM_STAGES = 3;
 constexpr int UM_EPI_WARPS = 8;       // two per TMEM lane quarter, each drains 32 of the 64 columns
 constexpr int UM_THREADS = 64 + 32 * UM_EPI_WARPS;   // warp 0 producer, warp 1 MMA, the rest epilogue
 constexpr int UM_EPI_COLS = SPL_TN / (UM_EPI_WARPS / 4);
-constexpr int UM_TMEM_COLS = 512;     // 5 accumulators x 64 columns (power-of-two allocation)
-constexpr int UM_TBUF = 1;            // TMEM accumulator sets (drain alternates when 2)
+constexpr int UM_TMEM_COLS = 512;     // 8 accumulator slots x 64 columns
+// TMEM slots: accumulators 0 and 1 have one slot each, 2-4 two each (alternating drain
+// chunks), so the epilogue drains a chunk while the MMAs of the next one run; the
+// epilogue reads accumulators 0 and 1 first, the only ones the next chunk waits for.
+constexpr int UM_SLOTS = 8;
+constexpr int UM_SINGLE = 2;          // accumulators 0 .. UM_SINGLE-1 have one slot
+__host__ __device__ constexpr int um_slot(int c, int64_t chunk) {
+    return c < UM_SINGLE ? c : UM_SINGLE + 2 * (c - UM_SINGLE) + int(chunk & 1);
+}
+// completions of a slot's barriers before the one of this chunk
+__host__ __device__ constexpr uint32_t um_use(int c, int64_t chunk) {
+    return uint32_t(c < UM_SINGLE ? chunk : chunk >> 1);
+}
+static_assert(UM_SINGLE + 2 * (SPL_ACCS - UM_SINGLE) <= UM_SLOTS && UM_SLOTS * SPL_TN <= UM_TMEM_COLS, "TMEM slots");
 constexpr uint32_t UM_L_BYTES = SPL_S * SPL_LT * 2;   // 48 KB
 constexpr uint32_t UM_R_BYTES = SPL_S * SPL_RT * 2;   // 24 KB
 constexpr long long UM_WAIT_CYCLES = 4000000000ll;     // ~2 s at 2 GHz
 
+constexpr int UM_TR_LD = 5;           // row pitch (int64) of an epilogue warp's transpose patch
 struct UmmaSmem {
     uint16_t L[UM_STAGES][SPL_S * SPL_LT];
     uint16_t R[UM_STAGES][SPL_S * SPL_RT];
-    uint64_t full[UM_STAGES], empty[UM_STAGES], tfull[2], tempty[2], done;
+    long long tr[UM_EPI_WARPS][32 * UM_TR_LD];   // 32 rows x 4 columns per pass of the stage-1 store
+    uint64_t full[UM_STAGES], empty[UM_STAGES], tfull[UM_SLOTS], tempty[UM_SLOTS], done;
     uint32_t tmem_base;
     volatile int abort;
 };
+
+static_assert(sizeof(UmmaSmem) <= 232448, "slice GEMM shared memory exceeds the opt-in limit");
+static_assert(UM_EPI_COLS % 4 == 0, "the stage-1 store moves 4 columns per pass");
+static_assert(SPL_S2_KCHUNK / SPL_DRAIN_KT <= SPL_MAX_DRAINS, "stage-2 items span too many drains");
 
 // Device descriptors of the split plan for one number of stacked vectors.
 struct SplitDevPlan {
@@ -322,9 +340,12 @@ __device__ __forceinline__ uint32_t su32(const void* p) { return uint32_t(__cvta
 
 // Shared-memory matrix descriptor, K-major without swizzle: 8x8 core matrices of 128
 // contiguous bytes, LBO = 128 B between K-adjacent cores, SBO = 512 B between 8-row groups.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-    return uint64_t((addr >> 4) & 0x3FFF) | (uint64_t(128 >> 4) << 16) | (uint64_t(512 >> 4) << 32) | (1ull << 46);
-}
+// The low word holds the start address (bits 0-13, address / 16) and LBO / 16 (bits
+// 16-29); the high word SBO / 16 (bits 32-45) and the fixed version bit 46.  Every
+// operand of a stage sits below 256 KB of shared memory, so operand offsets are added to
+// the low word without a carry out of the address field.
+__device__ __forceinline__ uint32_t sdesc_lo(uint32_t addr) { return ((addr >> 4) & 0x3FFF) | ((128u >> 4) << 16); }
+constexpr uint32_t UM_DESC_HI = (512u >> 4) | (1u << (46 - 32));
 
 // Instruction descriptor of kind::f16: BF16 x BF16 -> FP32, both K-major, M=128, N=64.
 constexpr uint32_t UM_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(SPL_TN >> 3) << 17) |
@@ -382,10 +403,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  "l"(src), "r"(bytes), "r"(su32(b))
                  : "memory");
 }
-__device__ __forceinline__ void umma(uint32_t d, uint64_t da, uint64_t db, uint32_t accumulate) {
+__device__ __forceinline__ void umma(uint32_t d, uint32_t a_lo, uint32_t b_lo, uint32_t accumulate) {
     asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(da), "l"(db), "r"(UM_IDESC), "r"(accumulate));
+        "{\n.reg .pred p;\n.reg .b64 da, db;\nsetp.ne.b32 p, %3, 0;\nmov.b64 da, {%1, %4};\nmov.b64 db, {%2, %4};\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n}\n" ::"r"(d),
+        "r"(a_lo), "r"(b_lo), "r"(accumulate), "r"(UM_DESC_HI), "r"(UM_IDESC));
 }
 __device__ __forceinline__ void umma_commit(uint64_t* b) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
@@ -418,10 +440,43 @@ struct UmmaArgs {
     int* status;
 };
 
-// Slice pairs (i, j) with i + j <= 5 in issue order, grouped by level i + j; pair 0
-// feeds acc0, pairs 1-2 acc1, 3-5 acc2, 6-9 acc3, 10-20 acc4.
-__constant__ int8_t c_pair_i[SPL_PAIRS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
-__constant__ int8_t c_pair_j[SPL_PAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
+// The 42 MMAs of one K tile (two K=16 steps x 21 slice pairs), fully unrolled so that
+// each costs two 32-bit adds besides the MMA itself.  Order: K step, then level
+// l = i + j, then i (consecutive MMAs mostly feed different accumulators; a run into one
+// accumulator stalls on its own sum).  Level l feeds accumulator c = min(l, 4) in the
+// chunk's TMEM slot.  first: the tile opens drain chunk `chunk`, so the first pair of
+// every accumulator overwrites it, once the epilogue has emptied the slot (tempty).
+// last: the tile closes the chunk and hands its accumulators to the epilogue (tfull);
+// the next chunk waits only for accumulators 0 and 1 to be read.
+__device__ __forceinline__ bool umma_ktile(UmmaSmem& sm, uint32_t tmem, uint32_t la, uint32_t ra, bool first,
+                                           bool last, int64_t chunk, int* status) {
+    const uint32_t a0 = sdesc_lo(la), b0 = sdesc_lo(ra);
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+        for (int l = 0; l < SPL_S; ++l) {
+            const int c = l < SPL_ACCS - 1 ? l : SPL_ACCS - 1;
+            const int slot = um_slot(c, chunk);
+            if (first && ks == 0 && l == c) {   // previous use of the slot: chunk - 1 or chunk - 2
+                const uint32_t use = um_use(c, chunk);
+                if (use > 0) {
+                    if (!mbar_wait(sm, &sm.tempty[slot], (use - 1) & 1, status)) return false;
+                    tc_fence_after();
+                }
+            }
+#pragma unroll
+            for (int i = 0; i <= l; ++i) {
+                const int j = l - i;
+                const uint32_t accumulate = (first && ks == 0 && i == 0 && l == c) ? 0u : 1u;
+                umma(tmem + uint32_t(slot) * SPL_TN, a0 + uint32_t(i * (SPL_LT * 2) + ks * 256) / 16,
+                     b0 + uint32_t(j * (SPL_RT * 2) + ks * 256) / 16, accumulate);
+            }
+        }
+    if (last)
+#pragma unroll
+        for (int c = 0; c < SPL_ACCS; ++c) umma_commit(&sm.tfull[um_slot(c, chunk)]);
+    return true;
+}
 
 __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -437,9 +492,9 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
             mbar_init(&sm.full[s], 1);
             mbar_init(&sm.empty[s], 1);
         }
-        for (int b = 0; b < UM_TBUF; ++b) {
-            mbar_init(&sm.tfull[b], 1);
-            mbar_init(&sm.tempty[b], 32 * UM_EPI_WARPS);
+        for (int c = 0; c < UM_SLOTS; ++c) {
+            mbar_init(&sm.tfull[c], 1);
+            mbar_init(&sm.tempty[c], 32 * UM_EPI_WARPS);
         }
         mbar_init(&sm.done, 1);
         sm.abort = 0;
@@ -480,32 +535,16 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
         for (int64_t it = blockIdx.x; it < total && ok; it += gridDim.x) {
             const SWork W = a.work[it / a.nvec];
             for (int kc0 = W.k0; kc0 < W.k1 && ok; kc0 += SPL_DRAIN_KT, ++dchunk) {
-                const int b = int(dchunk % UM_TBUF);
-                const int64_t n = dchunk / UM_TBUF;
-                if (n > 0 && !(ok = mbar_wait(sm, &sm.tempty[b], uint32_t((n - 1) & 1), a.status))) break;
-                tc_fence_after();
-                const uint32_t acc = tmem + uint32_t(b) * (SPL_ACCS * SPL_TN);
                 const int kc1 = min(kc0 + SPL_DRAIN_KT, W.k1);
                 for (int kt = kc0; kt < kc1; ++kt, ++kidx) {
                     const int s = int(kidx % UM_STAGES);
                     if (!(ok = mbar_wait(sm, &sm.full[s], uint32_t((kidx / UM_STAGES) & 1), a.status))) break;
                     tc_fence_after();
-                    const uint32_t la = su32(sm.L[s]), ra = su32(sm.R[s]);
-#pragma unroll
-                    for (int ks = 0; ks < 2; ++ks) {
-#pragma unroll
-                        for (int p = 0; p < SPL_PAIRS; ++p) {
-                            const int i = c_pair_i[p], j = c_pair_j[p];
-                            const int which = p == 0 ? 0 : (p < 3 ? 1 : (p < 6 ? 2 : (p < 10 ? 3 : 4)));
-                            const bool first =
-                                kt == kc0 && ks == 0 && (p == 0 || p == 1 || p == 3 || p == 6 || p == 10);
-                            umma(acc + uint32_t(which) * SPL_TN, sdesc(la + i * (SPL_LT * 2) + ks * 256),
-                                 sdesc(ra + j * (SPL_RT * 2) + ks * 256), first ? 0u : 1u);
-                        }
-                    }
+                    if (!(ok = umma_ktile(sm, tmem, su32(sm.L[s]), su32(sm.R[s]), kt == kc0, kt == kc1 - 1, dchunk,
+                                          a.status)))
+                        break;
                     umma_commit(&sm.empty[s]);
                 }
-                if (ok) umma_commit(&sm.tfull[b]);
             }
         }
         umma_commit(&sm.done);   // completes when every MMA issued above has finished
@@ -522,77 +561,112 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
             const SWork W = a.work[it / a.nvec];
             const int v = int(it % a.nvec);
             const int fs = a.gemms[W.gemm].fshift;
-            const float scale_f = __int_as_float((127 + fs) << 23);   // 2^fs
-            long long acc[UM_EPI_COLS];
+            long long acc[UM_EPI_COLS];   // slice sums of the item in units of 2^-31
 #pragma unroll
             for (int j = 0; j < UM_EPI_COLS; ++j) acc[j] = 0;
-            for (int kc0 = W.k0; kc0 < W.k1; kc0 += SPL_DRAIN_KT, ++dchunk) {
-                const int b = int(dchunk % UM_TBUF);
-                if (!(ok = mbar_wait(sm, &sm.tfull[b], uint32_t((dchunk / UM_TBUF) & 1), a.status))) break;
-                tc_fence_after();
-                const uint32_t base = tmem + lane_addr + uint32_t(b) * (SPL_ACCS * SPL_TN) + col0;
+            for (int kc0 = W.k0; kc0 < W.k1 && ok; kc0 += SPL_DRAIN_KT, ++dchunk) {
+                // 32-bit conversions only (the 64-bit one is an FP64-rate operation): acc c
+                // holds the exact level sum in units of 2^(-8c) for c < 4 (|sum| <=
+                // (c+1) 2^22 in those units), acc 4 the rest, rounded to units of 2^-31
+                // (< 2^24 of them); each is added in units of 2^-31, the chunk's total
+                // staying below 2^53.01.  An accumulator is handed back to the MMA issuer
+                // as soon as it is in registers.
 #pragma unroll
-                for (int c0 = 0; c0 < UM_EPI_COLS; c0 += 8) {
-                    uint32_t r0[8], r1[8], r2[8], r3[8], r4[8];
-                    tmem_ld8(base + c0, r0);
-                    tmem_ld8(base + SPL_TN + c0, r1);
-                    tmem_ld8(base + 2 * SPL_TN + c0, r2);
-                    tmem_ld8(base + 3 * SPL_TN + c0, r3);
-                    tmem_ld8(base + 4 * SPL_TN + c0, r4);
+                for (int c = 0; c < SPL_ACCS; ++c) {
+                    // warp-uniform outcome: the TMEM loads below are .sync.aligned
+                    const int slot = um_slot(c, dchunk);
+                    ok = __all_sync(0xffffffffu, mbar_wait(sm, &sm.tfull[slot], um_use(c, dchunk) & 1, a.status));
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t base = tmem + lane_addr + uint32_t(slot) * SPL_TN + col0;
+                    uint32_t rv[UM_EPI_COLS];
+#pragma unroll
+                    for (int c0 = 0; c0 < UM_EPI_COLS; c0 += 8)
+                        tmem_ld8(base + c0, *reinterpret_cast<uint32_t(*)[8]>(rv + c0));
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    tc_fence_before();
+                    mbar_arrive(&sm.tempty[slot]);
+                    const float scale = c == 0 ? 1.0f : c == 1 ? 256.0f : c == 2 ? 65536.0f : c == 3 ? 16777216.0f : 2147483648.0f;
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const long long i0 = __float2int_rn(__uint_as_float(r0[j]));                 // exact
-                        const long long i1 = __float2int_rn(__uint_as_float(r1[j]) * 256.0f);        // exact
-                        const long long i2 = __float2int_rn(__uint_as_float(r2[j]) * 65536.0f);      // exact
-                        const long long i3 = __float2int_rn(__uint_as_float(r3[j]) * 16777216.0f);   // exact
-                        const long long i4 = __float2ll_rn(__uint_as_float(r4[j]) * scale_f);
-                        acc[c0 + j] += (i0 << fs) + (i1 << (fs - 8)) + (i2 << (fs - 16)) + (i3 << (fs - 24)) + i4;
+                    for (int j = 0; j < UM_EPI_COLS; ++j) {
+                        const int iv = __float2int_rn(__uint_as_float(rv[j]) * scale);
+                        if (c == 0)
+                            acc[j] += static_cast<long long>(iv) * (1ll << 31);
+                        else if (c < SPL_ACCS - 1)
+                            acc[j] += static_cast<long long>(iv) * (1 << (31 - 8 * c));
+                        else
+                            acc[j] += iv;
                     }
                 }
-                tc_fence_before();
-                mbar_arrive(&sm.tempty[b]);
             }
             if (!ok) break;
+            // F = round(2^fs * sum): exact for fs >= 31 (up to 32 drains of 2^53.01 stay
+            // below 2^58.01; the GEMM's shift keeps F below 2^62); for fs < 31 only the
+            // part below 2^-fs, i.e. of i4, is rounded
+#pragma unroll
+            for (int j = 0; j < UM_EPI_COLS; ++j)
+                acc[j] = fs >= 31 ? acc[j] * (1ll << (fs - 31)) : (acc[j] + (1ll << (30 - fs))) >> (31 - fs);
             const SGemm G = a.gemms[W.gemm];
             const int r = W.mtile * SPL_TM + row;
-            if (r < G.M) {
-                const int cbase = W.ntile * SPL_TN + col0;
-                if (G.kind == 0) {
-                    int64_t* D = a.s1 + int64_t(v) * a.s1_vs + G.d_off + int64_t(r) * G.ldd;
-                    const int32_t* cex = a.ap_ex + int64_t(v) * a.ap_ex_vs + G.ec_off;
-                    // stage-2 vector of entry (r, c): (c / colgroup) * period + r % period
-                    int32_t* x2 = a.ap_ex + int64_t(v) * a.ap_ex_vs + G.x2_exp + r % G.x2_period;
-                    const int eoff = a.op_ex[G.er_off + r] - (14 + G.fshift);
-                    int emax = INT_MIN, grp = cbase / G.x2_colgroup;
-                    int next = (grp + 1) * G.x2_colgroup;   // first column of the next group
+            const int cbase = W.ntile * SPL_TN + col0;
+            if (G.kind == 0) {
+                // exponents of the stage-2 vectors fed by this row: the column exponents
+                // come with one load per warp (lane l holds column cbase + l) and a
+                // broadcast per column, so no global load sits between the atomics
+                const bool rv = r < G.M;
+                const int rs = rv ? r : 0;
+                const int cl = cbase + lane;
+                const int cex_l = cl < G.N ? a.ap_ex[int64_t(v) * a.ap_ex_vs + G.ec_off + cl] : 0;
+                // stage-2 vector of entry (r, c): (c / colgroup) * period + r % period
+                int32_t* x2 = a.ap_ex + int64_t(v) * a.ap_ex_vs + G.x2_exp + rs % G.x2_period;
+                const int eoff = (rv ? a.op_ex[G.er_off + rs] : 0) - (14 + G.fshift);
+                int emax = INT_MIN, grp = cbase / G.x2_colgroup;
+                int next = (grp + 1) * G.x2_colgroup;   // first column of the next group
 #pragma unroll
-                    for (int j = 0; j < UM_EPI_COLS; ++j) {
-                        const int c = cbase + j;
-                        if (c < G.N) {
-                            if (c >= next) {
-                                if (emax != INT_MIN) atomicMax(x2 + grp * G.x2_period, emax + eoff);
-                                emax = INT_MIN;
-                                ++grp;
-                                next += G.x2_colgroup;
-                            }
-                            D[c] = G.sign > 0 ? acc[j] : -acc[j];
-                            if (acc[j] != 0) {
-                                const unsigned long long u = acc[j] < 0 ? static_cast<unsigned long long>(-acc[j])
-                                                                        : static_cast<unsigned long long>(acc[j]);
-                                emax = max(emax, (64 - __clzll(u)) + cex[c]);
-                            }
+                for (int j = 0; j < UM_EPI_COLS; ++j) {
+                    const int c = cbase + j;   // the same for every lane
+                    const int ce = __shfl_sync(0xffffffffu, cex_l, j);
+                    if (c < G.N) {
+                        if (c >= next) {
+                            if (rv && emax != INT_MIN) atomicMax(x2 + grp * G.x2_period, emax + eoff);
+                            emax = INT_MIN;
+                            ++grp;
+                            next += G.x2_colgroup;
+                        }
+                        if (acc[j] != 0) {
+                            const unsigned long long u = acc[j] < 0 ? static_cast<unsigned long long>(-acc[j])
+                                                                    : static_cast<unsigned long long>(acc[j]);
+                            emax = max(emax, (64 - __clzll(u)) + ce);
                         }
                     }
-                    if (emax != INT_MIN) atomicMax(x2 + grp * G.x2_period, emax + eoff);
-                } else {
-                    unsigned long long* D = reinterpret_cast<unsigned long long*>(a.s2 + int64_t(v) * a.s2_vs +
-                                                                                  G.d_off + int64_t(r) * G.ldd);
+                }
+                if (rv && emax != INT_MIN) atomicMax(x2 + grp * G.x2_period, emax + eoff);
+                // row-major store through the warp's shared-memory patch: each pass moves
+                // 4 columns of the warp's 32 rows, written as 8 rows x 32 contiguous bytes
+                // per instruction instead of 32 rows x 8 bytes
+                long long* tp = sm.tr[warp - 2];
+                int64_t* D = a.s1 + int64_t(v) * a.s1_vs + G.d_off;
+                const int rbase = W.mtile * SPL_TM + 32 * q;
 #pragma unroll
-                    for (int j = 0; j < UM_EPI_COLS; ++j) {
-                        const int c = cbase + j;
-                        if (c < G.N && acc[j] != 0) atomicAdd(D + c, static_cast<unsigned long long>(acc[j]));
+                for (int c4 = 0; c4 < UM_EPI_COLS; c4 += 4) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) tp[lane * UM_TR_LD + j] = G.sign > 0 ? acc[c4 + j] : -acc[c4 + j];
+                    __syncwarp();
+                    const int cc = lane & 3, c = cbase + c4 + cc;
+#pragma unroll
+                    for (int rep = 0; rep < 4; ++rep) {
+                        const int rr = 8 * rep + (lane >> 2), gr = rbase + rr;
+                        if (gr < G.M && c < G.N) D[int64_t(gr) * G.ldd + c] = tp[rr * UM_TR_LD + cc];
                     }
+                    __syncwarp();
+                }
+            } else if (r < G.M) {
+                unsigned long long* D = reinterpret_cast<unsigned long long*>(a.s2 + int64_t(v) * a.s2_vs +
+                                                                              G.d_off + int64_t(r) * G.ldd);
+#pragma unroll
+                for (int j = 0; j < UM_EPI_COLS; ++j) {
+                    const int c = cbase + j;
+                    if (c < G.N && acc[j] != 0) atomicAdd(D + c, static_cast<unsigned long long>(acc[j]));
                 }
             }
         }
@@ -696,6 +770,7 @@ int validate_split_plan(const Plan& P, const SplitHost& H, std::string* err) {
         for (const SWork& x : w) {
             const SGemm& G = H.gemms[x.gemm];
             if (x.k0 < 0 || x.k1 > G.kt || x.k0 >= x.k1) return false;
+            if (cdiv(x.k1 - x.k0, SPL_DRAIN_KT) > SPL_MAX_DRAINS) return false;   // epilogue sum bound
             const int64_t lsz = G.l_buf ? H.ap_sl_vs : H.op_sl, rsz = G.r_buf ? H.ap_sl_vs : H.op_sl;
             const int64_t lend = G.l_tiles + (int64_t(x.mtile) * G.kt + x.k1) * (SPL_S * SPL_LT);
             const int64_t rend = G.r_tiles + (int64_t(x.ntile) * G.kt + x.k1) * (SPL_S * SPL_RT);
@@ -818,6 +893,10 @@ int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err) {
         }
         m.l_tiles = lt; m.r_tiles = rt; m.l_buf = 0; m.r_buf = 1;
         m.kt = int32_t(cdiv(G.order == 0 ? G.b : G.c, SPL_TK));
+        if (m.kt > SPL_MAX_DRAINS * SPL_DRAIN_KT) {   // one stage-1 item spans the whole contraction
+            *err = "split path: a sector dimension above 8192";
+            return DMRG_ERR_INVALID_ARG;
+        }
         m.d_off = int64_t(nv) * G.scratch; m.ldd = m.N; m.kind = 0; m.sign = G.sign < 0 ? -1 : 1;
         m.fshift = fshift_for(G.order == 0 ? G.b : G.c);
         m.er_off = le; m.ec_off = re; m.x2_exp = -1;

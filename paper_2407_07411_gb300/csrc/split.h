@@ -16,10 +16,13 @@
 //     acc4 = the 11 pairs with i + j = 4, 5 (magnitude ~2^-32 of acc0)
 // The tensor cores add with truncation, so an inexact accumulator drifts by ~2^-23 of
 // its own magnitude per addition; keeping every level up to 3 exact confines that drift
-// to acc4, ~2^-47 of the result.  The accumulators are drained every 256 K into the
-// integer F = round(2^s (acc0 + ... + acc4)), with a
-// per-GEMM shift s = 47 - ceil(log2 K) that keeps |F| < 2^62 for K <= 2^23 while short
-// contractions keep a resolution far below 2^-46 of the result; then
+// to acc4, ~2^-47 of the result.  The accumulators are drained every 256 K with 32-bit
+// conversions only: acc0..acc3 exactly, acc4 rounded to a multiple of 2^-31, summed in
+// int64 in units of 2^-31 over the (at most 32) drains of a work item, and then
+//     F = round(2^s (acc0 + ... + acc4)),
+// with a per-GEMM shift s = 47 - ceil(log2 K) that keeps |F| < 2^62 for K <= 2^23 while
+// short contractions keep a resolution far below 2^-46 of the result (for s < 31 only
+// the acc4 part is rounded); then
 //     L*R = 2^(E_row + E_col - 14 - s) * F.
 // Stage-1 results are kept as int64 F (their exponents implied by the operand vectors),
 // sliced again for stage 2 with integer shifts only, and stage-2 results are summed as
@@ -45,6 +48,7 @@ constexpr int SPL_DRAIN_KT = 8;           // K tiles per exact drain (256 K)
 constexpr int SPL_ACCS = 5;               // TMEM accumulators (pair levels 0-3 exact, rest)
 constexpr int64_t SPL_MAX_K = int64_t(1) << 23;   // longest contraction (s >= 24)
 constexpr int SPL_S2_KCHUNK = 256;        // K tiles per stage-2 work item (8192 K)
+constexpr int SPL_MAX_DRAINS = 32;        // drains per work item (int64 sums of the epilogue)
 
 // One split GEMM: D (M x N) = L (M x K) * R (K x N) over kt K tiles.  L and R are
 // sliced tile arrays (buffer 0 = operator slices, 1 = per-apply slices); tile (mt, kt)
