@@ -179,6 +179,62 @@ int dmrg_heff_apply_noalloc(const int32_t* left, int32_t nl, const int32_t* righ
                             const double* op_data, int64_t op_len,
                             const double* x, double* y, void* stream);
 
+/*
+ * Schedule of the grouped GEMMs (batching step of the method; the paper's own
+ * scheduler assigns tasks to CPU and GPUs and has no counterpart of these fields).
+ * It fixes only how the planned GEMMs are cut into work items and launched: every
+ * schedule computes the same H_eff*psi (the split path bit for bit, the FP64 path up
+ * to the order of its split-K sums).  Stage-2 GEMMs fall into three shape classes by
+ * contraction length K: [0] K <= 2048, [1] K <= 16384, [2] longer.
+ *   fp64_kchunk[c]    K per FP64 stage-2 work item of class c: 0 (whole K, no split)
+ *                     or a positive multiple of 16.  Default 512.
+ *   fp64_ctas_per_sm  resident CTAs of the FP64 tile kernel per SM, 0..64; 0 (default)
+ *                     and values above the occupancy limit mean that limit.
+ *   split_kchunk[c]   K tiles (of 32) per split stage-2 work item of class c: 0
+ *                     (default: adaptive, the longest that leaves >= 4 items per SM)
+ *                     or a multiple of 8 up to 256.
+ *   per_gemm          0 (default): each stage is one persistent launch over all its
+ *                     GEMMs; 1: one launch per grouped GEMM (for comparison).
+ */
+typedef struct {
+    int32_t fp64_kchunk[3];
+    int32_t fp64_ctas_per_sm;
+    int32_t split_kchunk[3];
+    int32_t per_gemm;
+} dmrg_schedule;
+
+/* Current schedule of the handle. */
+int dmrg_heff_schedule_get(dmrg_heff_t h, dmrg_schedule* s);
+
+/* Replace the schedule: rebuilds and uploads the work lists (plan-only handles:
+ * builds and checks them on the host), synchronises the device first and drops the
+ * captured graphs.  DMRG_ERR_INVALID_ARG for a field out of range, leaving the
+ * schedule unchanged. */
+int dmrg_heff_schedule_set(dmrg_heff_t h, const dmrg_schedule* s);
+
+/* Outcome of dmrg_heff_autotune: applies timed, median ms per apply of the schedule
+ * the handle had on entry and of the one chosen. */
+typedef struct {
+    int32_t trials, nvec;
+    double default_ms, best_ms;
+    dmrg_schedule best;
+} dmrg_tune_report;
+
+/*
+ * Autotuner: times candidate schedules on this handle's plan with nvec vectors
+ * (deterministic internal test vectors; `reps` timed applies per candidate, 1..100,
+ * median) by coordinate descent over the stage-2 K extent of every shape class that
+ * has GEMMs (and, FP64, the CTAs per SM), and leaves the fastest schedule in place.
+ * Allocates two nvec x dim device vectors for the duration and synchronises the
+ * device.  Not for plan-only handles.
+ */
+int dmrg_heff_autotune(dmrg_heff_t h, int32_t nvec, int32_t reps, dmrg_tune_report* report);
+
+/* Number of grouped GEMMs of the plan for nvec vectors: counts[0] in stage 1 (one per
+ * term group), counts[1] in stage 2 (per output block and contraction order); with
+ * per_gemm set, an apply launches counts[0] + counts[1] GEMM kernels. */
+int dmrg_heff_gemm_count(dmrg_heff_t h, int32_t nvec, int64_t counts[2]);
+
 /* Release the handle and its device memory (NULL is ignored). */
 void dmrg_heff_destroy(dmrg_heff_t h);
 

@@ -31,7 +31,8 @@ SYMBOLS = ("dmrg_heff_create", "dmrg_heff_dim", "dmrg_heff_flops", "dmrg_heff_pl
            "dmrg_heff_apply", "dmrg_heff_apply_host", "dmrg_heff_diagonal", "dmrg_davidson",
            "dmrg_heff_destroy", "dmrg_strerror", "dmrg_last_error", "dmrg_heff_profile",
            "dmrg_heff_profile_read", "dmrg_probe_fp64_peak", "dmrg_heff_apply_noalloc",
-           "dmrg_selftest_wait_timeout")
+           "dmrg_selftest_wait_timeout", "dmrg_heff_schedule_get", "dmrg_heff_schedule_set",
+           "dmrg_heff_autotune", "dmrg_heff_gemm_count")
 
 
 class Opts(ctypes.Structure):
@@ -52,6 +53,31 @@ class KernelStat(ctypes.Structure):
                 ("flops_total", ctypes.c_double), ("bytes_total", ctypes.c_double)]
 
 
+class Schedule(ctypes.Structure):
+    _fields_ = [("fp64_kchunk", ctypes.c_int32 * 3), ("fp64_ctas_per_sm", ctypes.c_int32),
+                ("split_kchunk", ctypes.c_int32 * 3), ("per_gemm", ctypes.c_int32)]
+
+    def to_dict(self) -> dict:
+        return dict(fp64_kchunk=list(self.fp64_kchunk), fp64_ctas_per_sm=self.fp64_ctas_per_sm,
+                    split_kchunk=list(self.split_kchunk), per_gemm=self.per_gemm)
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "Schedule":
+        s = cls()
+        for i, v in enumerate(d["fp64_kchunk"]):
+            s.fp64_kchunk[i] = int(v)
+        for i, v in enumerate(d["split_kchunk"]):
+            s.split_kchunk[i] = int(v)
+        s.fp64_ctas_per_sm = int(d["fp64_ctas_per_sm"])
+        s.per_gemm = int(d["per_gemm"])
+        return s
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("trials", ctypes.c_int32), ("nvec", ctypes.c_int32), ("default_ms", ctypes.c_double),
+                ("best_ms", ctypes.c_double), ("best", Schedule)]
+
+
 _P = ctypes.c_void_p
 _i32, _i64, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 _lib.dmrg_heff_create.argtypes = [_P, _i32, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _i64, _P, _i64,
@@ -65,6 +91,10 @@ _lib.dmrg_heff_apply.argtypes = [_P, _P, _P, _i32, _P]
 _lib.dmrg_heff_apply_host.argtypes = [_P, _P, _P, _i32]
 _lib.dmrg_heff_diagonal.argtypes = [_P, _P, _P]
 _lib.dmrg_davidson.argtypes = [_P, _i32, _f64, _i32, _i32, _i32, _P, _P, ctypes.POINTER(DavidsonInfo)]
+_lib.dmrg_heff_schedule_get.argtypes = [_P, ctypes.POINTER(Schedule)]
+_lib.dmrg_heff_schedule_set.argtypes = [_P, ctypes.POINTER(Schedule)]
+_lib.dmrg_heff_autotune.argtypes = [_P, _i32, _i32, ctypes.POINTER(TuneReport)]
+_lib.dmrg_heff_gemm_count.argtypes = [_P, _i32, _P]
 _lib.dmrg_heff_destroy.argtypes = [_P]
 _lib.dmrg_heff_destroy.restype = None
 _lib.dmrg_strerror.argtypes = [ctypes.c_int]
@@ -80,7 +110,7 @@ _lib.dmrg_heff_apply_noalloc.argtypes = [_P, _i32, _P, _i32, _i32, _i32, _P, _P,
                                          _P, _P, _P]
 _lib.dmrg_heff_apply_noalloc.restype = ctypes.c_int
 
-ERR_NOT_CONVERGED = -6
+ERR_INVALID_ARG, ERR_NOT_CONVERGED = -1, -6
 
 
 class DmrgError(RuntimeError):
@@ -203,6 +233,32 @@ class HEff:
     def apply_host_ptr(self, x_ptr: int, y_ptr: int, nvec: int):
         """apply_host on raw host pointers (for pinned buffers)."""
         _check(_lib.dmrg_heff_apply_host(self._h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), nvec))
+
+    @property
+    def schedule(self) -> dict:
+        """Current work-list schedule (see dmrg_schedule in the C header)."""
+        s = Schedule()
+        _check(_lib.dmrg_heff_schedule_get(self._h, ctypes.byref(s)))
+        return s.to_dict()
+
+    @schedule.setter
+    def schedule(self, d: dict):
+        s = Schedule.from_dict(d)
+        _check(_lib.dmrg_heff_schedule_set(self._h, ctypes.byref(s)))
+
+    def autotune(self, nvec: int = 1, reps: int = 3) -> dict:
+        """Time candidate schedules on this handle and keep the fastest; returns the
+        report (trials, nvec, default_ms, best_ms, best)."""
+        r = TuneReport()
+        _check(_lib.dmrg_heff_autotune(self._h, nvec, reps, ctypes.byref(r)))
+        return dict(trials=r.trials, nvec=r.nvec, default_ms=r.default_ms, best_ms=r.best_ms,
+                    best=r.best.to_dict())
+
+    def gemm_count(self, nvec: int = 1) -> tuple:
+        """(stage-1, stage-2) grouped GEMMs of the plan for nvec vectors."""
+        c = (_i64 * 2)()
+        _check(_lib.dmrg_heff_gemm_count(self._h, nvec, c))
+        return int(c[0]), int(c[1])
 
     def profile(self, enable: bool = True):
         """Start (reset) or stop per-kernel CUDA-event timing of this handle."""

@@ -5,6 +5,7 @@
 #include <string>
 #include <vector>
 
+#include "../../include/dmrg_heff.h"
 #include "kernels.h"
 #include "plan.h"
 
@@ -80,6 +81,15 @@ struct Handle : dmrg_heff {
     Seg* d_segs = nullptr;
     Reduce* d_red = nullptr;
     int32_t* d_counters = nullptr;
+    // current schedule and the capacities of the device work lists it fills
+    Schedule sched;
+    size_t cap_tiles1 = 0, cap_tiles2 = 0, cap_red = 0, cap_part = 0, cap_counters = 0;
+    int upload_fp64_work();
+    int set_schedule(const Schedule& s);
+    int split_set_schedule(const Schedule& s);   // k_split.cu
+    void drop_graphs();
+    int autotune(int32_t nvec, int32_t reps, dmrg_tune_report* rep);   // autotune.cu
+    const struct SplitHost* split_plan_host(int nv) const;             // k_split.cu
     double* d_xstage = nullptr;
     double* d_ystage = nullptr;
     DiagJob* d_diag_jobs = nullptr;

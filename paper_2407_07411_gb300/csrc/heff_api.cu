@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -47,6 +48,70 @@ static int dalloc(void** p, size_t bytes, const char* what) {
     return DMRG_OK;
 }
 
+// Copies the FP64 work lists of the current schedule to the device, growing a buffer
+// only when the list outgrew it.
+int Handle::upload_fp64_work() {
+    auto put = [&](auto& vec, auto** dptr, size_t* cap, const char* what) {
+        using T = typename std::remove_reference_t<decltype(vec)>::value_type;
+        if (vec.size() > *cap) {
+            if (*dptr) cudaFree(*dptr);
+            *dptr = nullptr;
+            *cap = 0;
+            int rc = dalloc(reinterpret_cast<void**>(dptr), sizeof(T) * vec.size(), what);
+            if (rc != DMRG_OK) return rc;
+            *cap = vec.size();
+        }
+        if (vec.empty()) return int(DMRG_OK);
+        cudaError_t e = cudaMemcpy(*dptr, vec.data(), sizeof(T) * vec.size(), cudaMemcpyHostToDevice);
+        return e == cudaSuccess ? int(DMRG_OK) : cuda_fail(e, what);
+    };
+    int rc;
+    if ((rc = put(plan.tiles1, &d_tiles1, &cap_tiles1, "tiles")) != DMRG_OK) return rc;
+    if ((rc = put(plan.tiles2, &d_tiles2, &cap_tiles2, "tiles")) != DMRG_OK) return rc;
+    if ((rc = put(plan.reduces, &d_red, &cap_red, "reduce jobs")) != DMRG_OK) return rc;
+    const size_t part = size_t(plan.n_slots) * FP64_BM * FP64_BN * size_t(max_nvec);
+    if (precision == DMRG_PREC_FP64 && part > cap_part) {
+        if (d_part) cudaFree(d_part);
+        d_part = nullptr;
+        cap_part = 0;
+        if ((rc = dalloc(reinterpret_cast<void**>(&d_part), sizeof(double) * part, "partials")) != DMRG_OK) return rc;
+        cap_part = part;
+    }
+    const size_t counters = 2 + plan.ranges1.size() + plan.ranges2.size();
+    if (counters > cap_counters) {
+        if (d_counters) cudaFree(d_counters);
+        d_counters = nullptr;
+        cap_counters = 0;
+        if ((rc = dalloc(reinterpret_cast<void**>(&d_counters), sizeof(int32_t) * counters, "counters")) != DMRG_OK)
+            return rc;
+        cap_counters = counters;
+    }
+    return DMRG_OK;
+}
+
+void Handle::drop_graphs() {
+    for (GraphEntry& g : graphs) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+}
+
+// Rebuilds the work lists for schedule s (results of every schedule agree: the FP64
+// path up to the order of its split-K sums, the split path bit for bit).
+int Handle::set_schedule(const Schedule& s) {
+    std::string err;
+    int rc = check_schedule(s, &err);
+    if (rc != DMRG_OK) return fail(rc, err);
+    if (!plan_only) {
+        cudaError_t e = cudaDeviceSynchronize();   // no apply may still read the old lists
+        if (e != cudaSuccess) return cuda_fail(e, "synchronize before rescheduling");
+    }
+    if ((rc = build_fp64_work(plan, s, &err)) != DMRG_OK) return fail(rc, err);
+    sched = s;
+    if (precision == DMRG_PREC_SPLIT_BF16 && (rc = split_set_schedule(s)) != DMRG_OK) return rc;
+    if (plan_only) return DMRG_OK;
+    drop_graphs();
+    return upload_fp64_work();
+}
+
 Spaces Handle::spaces(const double* x, double* y) const {
     Spaces s;
     s.ops = d_ops; s.x = x; s.scr = d_scr; s.y = y; s.part = d_part;
@@ -58,26 +123,43 @@ Spaces Handle::spaces(const double* x, double* y) const {
 int Handle::apply_fp64(const double* x, double* y, int32_t nvec, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(y, 0, sizeof(double) * plan.dim * nvec, st);
     if (e != cudaSuccess) return cuda_fail(e, "zero y");
-    e = cudaMemsetAsync(d_counters, 0, sizeof(int32_t) * 2, st);
+    const size_t n_counters = 2 + plan.ranges1.size() + plan.ranges2.size();
+    e = cudaMemsetAsync(d_counters, 0, sizeof(int32_t) * n_counters, st);
     if (e != cudaSuccess) return cuda_fail(e, "zero counters");
     const Spaces sp = spaces(x, y);
+    const int ctas = sched.fp64_ctas_per_sm > 0 ? std::min(sched.fp64_ctas_per_sm, tiles_per_sm) : tiles_per_sm;
     auto grid_for = [&](size_t n) {
         int64_t items = int64_t(n) * nvec;
-        int64_t g = int64_t(n_sm) * tiles_per_sm;
+        int64_t g = int64_t(n_sm) * ctas;
         return int32_t(items < g ? items : g);
+    };
+    // one stage: a single persistent launch over its tile list (queue counter 0 for
+    // stage 1, 1 for stage 2), or (per_gemm) one launch per GEMM over that GEMM's
+    // contiguous tile range (counters 2 .. 2 + #stage-1 GEMMs + #stage-2 GEMMs)
+    auto stage = [&](const Tile* d_t, const std::vector<Tile>& tl, const std::vector<std::pair<int32_t, int32_t>>& rg,
+                     int32_t* counters) {
+        if (!sched.per_gemm)
+            return launch_fp64_tiles(d_t, int32_t(tl.size()), d_gemms, d_segs, sp, nvec, counters,
+                                     grid_for(tl.size()), st);
+        for (size_t r = 0; r < rg.size(); ++r) {
+            const int32_t n = rg[r].second - rg[r].first;
+            cudaError_t le = launch_fp64_tiles(d_t + rg[r].first, n, d_gemms, d_segs, sp, nvec,
+                                               counters + r, grid_for(size_t(n)), st);
+            if (le != cudaSuccess) return le;
+        }
+        return cudaSuccess;
     };
     Profiler::Pending pe;
     if (!plan.tiles1.empty()) {
         prof.begin(kid_s1, st, s1_flops * nvec, s1_bytes * nvec, &pe);
-        e = launch_fp64_tiles(d_tiles1, int32_t(plan.tiles1.size()), d_gemms, d_segs, sp, nvec,
-                              d_counters, grid_for(plan.tiles1.size()), st);
+        e = stage(d_tiles1, plan.tiles1, plan.ranges1, sched.per_gemm ? d_counters + 2 : d_counters);
         prof.end(pe, st);
         if (e != cudaSuccess) return cuda_fail(e, "stage-1 tiles");
     }
     if (!plan.tiles2.empty()) {
         prof.begin(kid_s2, st, s2_flops * nvec, s2_bytes * nvec, &pe);
-        e = launch_fp64_tiles(d_tiles2, int32_t(plan.tiles2.size()), d_gemms, d_segs, sp, nvec,
-                              d_counters + 1, grid_for(plan.tiles2.size()), st);
+        e = stage(d_tiles2, plan.tiles2, plan.ranges2, sched.per_gemm ? d_counters + 2 + plan.ranges1.size()
+                                                                      : d_counters + 1);
         prof.end(pe, st);
         if (e != cudaSuccess) return cuda_fail(e, "stage-2 tiles");
     }
@@ -257,24 +339,16 @@ int dmrg_heff_create(const int32_t* left, int32_t nl, const int32_t* right, int3
         if ((rc = dmrg::upload(staging, &h->d_ops, "operators")) != DMRG_OK) return bail(rc);
     }
     const size_t nv = size_t(o.max_nvec);
-    if ((rc = dmrg::upload(P.tiles1, &h->d_tiles1, "tiles")) != DMRG_OK) return bail(rc);
-    if ((rc = dmrg::upload(P.tiles2, &h->d_tiles2, "tiles")) != DMRG_OK) return bail(rc);
     if ((rc = dmrg::upload(P.gemms, &h->d_gemms, "gemms")) != DMRG_OK) return bail(rc);
     if ((rc = dmrg::upload(P.segs, &h->d_segs, "segments")) != DMRG_OK) return bail(rc);
-    if ((rc = dmrg::upload(P.reduces, &h->d_red, "reduce jobs")) != DMRG_OK) return bail(rc);
+    if ((rc = h->upload_fp64_work()) != DMRG_OK) return bail(rc);
     if (o.precision == DMRG_PREC_FP64) {
         if ((rc = dmrg::dalloc(reinterpret_cast<void**>(&h->d_scr), sizeof(double) * P.scratch_len * nv,
                                "stage-1 scratch")) != DMRG_OK)
             return bail(rc);
-        if ((rc = dmrg::dalloc(reinterpret_cast<void**>(&h->d_part),
-                               sizeof(double) * P.n_slots * dmrg::FP64_BM * dmrg::FP64_BN * nv,
-                               "partials")) != DMRG_OK)
-            return bail(rc);
     } else {
         if ((rc = h->init_split(coef, a_off, b_off, op_data)) != DMRG_OK) return bail(rc);
     }
-    if ((rc = dmrg::dalloc(reinterpret_cast<void**>(&h->d_counters), 64, "counters")) != DMRG_OK)
-        return bail(rc);
     if ((rc = h->init_diag()) != DMRG_OK) return bail(rc);
     *out = h;
     return DMRG_OK;

@@ -72,6 +72,7 @@ struct SplitDevPlan {
     SBlock* blocks = nullptr;
     SPart* parts = nullptr;
     int64_t n_work1 = 0, n_work2 = 0, n_blocks = 0;
+    std::vector<std::pair<int32_t, int32_t>> r1, r2;   // per-GEMM work ranges (per_gemm)
     int64_t it_op0 = 0, it_x0 = 0, it_mid0 = 0, it_end = 0;      // item ranges
     int64_t tl_op0 = 0, tl_x0 = 0, tl_mid0 = 0, tl_end = 0;      // tile ranges
     int64_t ap_ex_len = 0, s2_len = 0;
@@ -92,6 +93,8 @@ struct SplitState {
     int64_t* s2 = nullptr;
     int32_t* status = nullptr;
     std::vector<SplitDevPlan> plans;   // plans[nv - 1]
+    std::vector<SplitHost> hosts;      // their host copies (work lists rebuilt per schedule)
+    std::vector<size_t> cap_w1, cap_w2;
     int kid_x = -1, kid_s1 = -1, kid_mid = -1, kid_s2 = -1, kid_fin = -1;
     ~SplitState() {
         for (SplitDevPlan& d : plans) d.release();
@@ -815,13 +818,64 @@ int validate_split_plan(const Plan& P, const SplitHost& H, std::string* err) {
     return DMRG_OK;
 }
 
-int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err) {
+void build_split_work(SplitHost& H, const Schedule& S) {
+    std::vector<SWork>& w1 = H.w1;
+    std::vector<SWork>& w2 = H.w2;
+    w1.clear(); w2.clear(); H.r1.clear(); H.r2.clear();
+    // stage 1: every output tile over the whole contraction (at most 8192 K)
+    for (size_t gi = 0; gi < H.gemms.size(); ++gi) {
+        const SGemm& m = H.gemms[gi];
+        if (m.kind != 0) continue;
+        for (int mt = 0; mt < cdiv(m.M, SPL_TM); ++mt)
+            for (int nt = 0; nt < cdiv(m.N, SPL_TN); ++nt) w1.push_back({int32_t(gi), mt, nt, 0, m.kt, 0});
+    }
+    // stage 2: output tiles x K chunks.  A shape class with no scheduled chunk takes the
+    // adaptive one: the longest multiple of the drain length up to SPL_S2_KCHUNK K tiles
+    // that leaves >= 4 items per SM.
+    int64_t tile_kt = 0;
+    for (const SGemm& m : H.gemms)
+        if (m.kind == 1) tile_kt += cdiv(m.M, SPL_TM) * cdiv(m.N, SPL_TN) * int64_t(m.kt);
+    int adaptive = SPL_S2_KCHUNK;
+    while (adaptive > SPL_DRAIN_KT && tile_kt / adaptive < 4 * 152) adaptive /= 2;
+    // K chunk outermost: CTAs that run at the same time share the L tile of an M row
+    // across its N tiles and the R tile of an N column across its M tiles (L2 reuse)
+    for (size_t gi = 0; gi < H.gemms.size(); ++gi) {
+        const SGemm& m = H.gemms[gi];
+        if (m.kind != 1) continue;
+        const int sc = S.split_kchunk[kclass(int64_t(m.kt) * SPL_TK)];
+        const int chunk = sc > 0 ? sc : adaptive;
+        for (int k0 = 0; k0 < m.kt; k0 += chunk)
+            for (int mt = 0; mt < cdiv(m.M, SPL_TM); ++mt)
+                for (int nt = 0; nt < cdiv(m.N, SPL_TN); ++nt)
+                    w2.push_back({int32_t(gi), mt, nt, k0, std::min(m.kt, k0 + chunk), 0});
+    }
+    // longest items first; one launch per GEMM keeps each GEMM's items contiguous
+    auto by_cost = [](const SWork& x, const SWork& y) { return (x.k1 - x.k0) > (y.k1 - y.k0); };
+    auto by_gemm = [](const SWork& x, const SWork& y) {
+        return x.gemm != y.gemm ? x.gemm < y.gemm : (x.k1 - x.k0) > (y.k1 - y.k0);
+    };
+    for (int st = 0; st < 2; ++st) {
+        std::vector<SWork>& w = st == 0 ? w1 : w2;
+        if (!S.per_gemm) {
+            std::stable_sort(w.begin(), w.end(), by_cost);
+            continue;
+        }
+        std::stable_sort(w.begin(), w.end(), by_gemm);
+        auto& R = st == 0 ? H.r1 : H.r2;
+        for (int32_t i = 0; i < int32_t(w.size());) {
+            int32_t j = i;
+            while (j < int32_t(w.size()) && w[j].gemm == w[i].gemm) ++j;
+            R.push_back({i, j});
+            i = j;
+        }
+    }
+}
+
+int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err, const Schedule& S) {
     std::vector<SGemm>& gemms = H.gemms;
     std::vector<SSeg>& segs = H.segs;
     std::vector<SJob>& jobs = H.jobs;
     std::vector<int32_t> op_jobs, x_jobs, mid_jobs;
-    std::vector<SWork>& w1 = H.w1;
-    std::vector<SWork>& w2 = H.w2;
     std::vector<SBlock>& blocks = H.blocks;
     blocks.assign(P.blocks.size(), SBlock{});
     std::vector<SPart>& parts = H.parts;
@@ -903,10 +957,7 @@ int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err) {
         m.x2_period = G.order == 0 ? G.a : G.d;
         m.x2_colgroup = G.order == 0 ? G.c : G.b;
         s1_lexp[g] = le; s1_rexp[g] = re; s1_eoff[g] = 14 + m.fshift;
-        const int32_t gi = int32_t(gemms.size());
         gemms.push_back(m);
-        for (int mt = 0; mt < cdiv(m.M, SPL_TM); ++mt)
-            for (int nt = 0; nt < cdiv(m.N, SPL_TN); ++nt) w1.push_back({gi, mt, nt, 0, m.kt, 0});
     }
     // stage 2: per output block, one GEMM over its A-first groups and one over its B-first groups
     std::vector<std::vector<int32_t>> by_out(P.blocks.size());
@@ -971,27 +1022,7 @@ int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err) {
             gemms.push_back(m);
         }
     }
-    // stage-2 work: output tiles x K chunks; the chunk (a multiple of the drain length,
-    // at most SPL_S2_KCHUNK K tiles) shrinks until there are >= 4 items per SM
-    {
-        int64_t tile_kt = 0;
-        for (size_t gi = P.groups.size(); gi < gemms.size(); ++gi)
-            tile_kt += cdiv(gemms[gi].M, SPL_TM) * cdiv(gemms[gi].N, SPL_TN) * int64_t(gemms[gi].kt);
-        int chunk = SPL_S2_KCHUNK;
-        while (chunk > SPL_DRAIN_KT && tile_kt / chunk < 4 * 152) chunk /= 2;
-        // K chunk outermost: CTAs that run at the same time share the L tile of an M row
-        // across its N tiles and the R tile of an N column across its M tiles (L2 reuse)
-        for (size_t gi = P.groups.size(); gi < gemms.size(); ++gi) {
-            const SGemm& m = gemms[gi];
-            for (int k0 = 0; k0 < m.kt; k0 += chunk)
-                for (int mt = 0; mt < cdiv(m.M, SPL_TM); ++mt)
-                    for (int nt = 0; nt < cdiv(m.N, SPL_TN); ++nt)
-                        w2.push_back({int32_t(gi), mt, nt, k0, std::min(m.kt, k0 + chunk), 0});
-        }
-    }
-    auto by_cost = [](const SWork& x, const SWork& y) { return (x.k1 - x.k0) > (y.k1 - y.k0); };
-    std::stable_sort(w1.begin(), w1.end(), by_cost);
-    std::stable_sort(w2.begin(), w2.end(), by_cost);
+    build_split_work(H, S);
     std::vector<SSlab>& slabs = H.slabs;
     std::vector<SItem>& items = H.items;
     auto add_items = [&](const std::vector<int32_t>& js) {
@@ -1097,6 +1128,8 @@ int Handle::init_split(const double*, const int64_t*, const int64_t*, const doub
             return rc;
         D.n_work1 = int64_t(H.w1.size());
         D.n_work2 = int64_t(H.w2.size());
+        D.r1 = H.r1;
+        D.r2 = H.r2;
         D.n_blocks = int64_t(H.blocks.size());
         D.it_op0 = H.it_op0; D.it_x0 = H.it_x0; D.it_mid0 = H.it_mid0; D.it_end = H.it_end;
         D.tl_op0 = H.tl_op0; D.tl_x0 = H.tl_x0; D.tl_mid0 = H.tl_mid0; D.tl_end = H.tl_end;
@@ -1110,6 +1143,11 @@ int Handle::init_split(const double*, const int64_t*, const int64_t*, const doub
             (m.kind == 0 ? D.s1_bytes : D.s2_bytes) += bytes;
         }
     }
+    for (const SplitHost& H : hosts) {
+        S->cap_w1.push_back(H.w1.size());
+        S->cap_w2.push_back(H.w2.size());
+    }
+    S->hosts = std::move(hosts);
     cudaError_t e = cudaMemset(S->status, 0, sizeof(int32_t));
     if (e != cudaSuccess) return cuda_fail(e, "status");
     e = cudaFuncSetAttribute(k_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(UmmaSmem)));
@@ -1162,25 +1200,37 @@ int Handle::apply_split(const double* x, double* y, int32_t nvec, cudaStream_t s
         prof.end(pe, st);
         return cudaGetLastError();
     };
-    auto gemm = [&](const SWork* w, int64_t nw, int kid, double flops, double bytes) {
+    // one stage: a single persistent launch over its work list, or (per_gemm) one launch
+    // per GEMM over that GEMM's contiguous range
+    auto gemm = [&](const SWork* w, int64_t nw, const std::vector<std::pair<int32_t, int32_t>>& rg, int kid,
+                    double flops, double bytes) {
         if (nw == 0) return cudaSuccess;
-        UmmaArgs ua{w, nw, D.gemms, S->op_sl, S->ap_sl, 0, S->s1, 0, S->s2, 0, S->op_ex, S->ap_ex, 0, 1, S->status};
+        auto launch = [&](const SWork* w0, int64_t n) {
+            UmmaArgs ua{w0, n, D.gemms, S->op_sl, S->ap_sl, 0, S->s1, 0, S->s2, 0, S->op_ex, S->ap_ex, 0, 1, S->status};
+            k_umma<<<unsigned(std::min<int64_t>(n, n_sm)), UM_THREADS, sizeof(UmmaSmem), st>>>(ua);
+            return cudaGetLastError();
+        };
         prof.begin(kid, st, flops, bytes, &pe);
-        k_umma<<<unsigned(std::min<int64_t>(nw, n_sm)), UM_THREADS, sizeof(UmmaSmem), st>>>(ua);
+        cudaError_t le = cudaSuccess;
+        if (!sched.per_gemm)
+            le = launch(w, nw);
+        else
+            for (size_t r = 0; r < rg.size() && le == cudaSuccess; ++r)
+                le = launch(w + rg[r].first, rg[r].second - rg[r].first);
         prof.end(pe, st);
-        return cudaGetLastError();
+        return le;
     };
     if ((e = cudaMemsetAsync(S->ap_ex, 0xC0, sizeof(int32_t) * D.ap_ex_len, st)) != cudaSuccess)
         return cuda_fail(e, "reset exponents");
     if ((e = slice(D.it_x0, D.it_mid0, D.tl_x0, D.tl_mid0, true, S->kid_x)) != cudaSuccess)
         return cuda_fail(e, "slice x");
-    if ((e = gemm(D.work1, D.n_work1, S->kid_s1, s1_flops * nvec, D.s1_bytes)) != cudaSuccess)
+    if ((e = gemm(D.work1, D.n_work1, D.r1, S->kid_s1, s1_flops * nvec, D.s1_bytes)) != cudaSuccess)
         return cuda_fail(e, "stage-1 slice gemm");
     if ((e = slice(D.it_mid0, D.it_end, D.tl_mid0, D.tl_end, false, S->kid_mid)) != cudaSuccess)
         return cuda_fail(e, "slice intermediates");
     if (D.s2_len > 0 && (e = cudaMemsetAsync(S->s2, 0, sizeof(int64_t) * D.s2_len, st)) != cudaSuccess)
         return cuda_fail(e, "zero stage-2 sums");
-    if ((e = gemm(D.work2, D.n_work2, S->kid_s2, s2_flops * nvec, D.s2_bytes)) != cudaSuccess)
+    if ((e = gemm(D.work2, D.n_work2, D.r2, S->kid_s2, s2_flops * nvec, D.s2_bytes)) != cudaSuccess)
         return cuda_fail(e, "stage-2 slice gemm");
     if (D.n_blocks > 0) {
         prof.begin(S->kid_fin, st, 0.0, 0.0, &pe);
@@ -1226,6 +1276,53 @@ extern "C" int dmrg_selftest_wait_timeout(int64_t wait_cycles) {
 }
 
 namespace dmrg {
+
+// New work lists for schedule s in every stacked-vector plan, validated like the
+// originals, then uploaded (plan-only handles: built and validated on the host).
+int Handle::split_set_schedule(const Schedule& s) {
+    std::string err;
+    if (!split) {
+        for (int nv = 1; nv <= max_nvec; ++nv) {
+            SplitHost H;
+            const int rc = build_split_plan(plan, nv, H, &err, s);
+            if (rc != DMRG_OK) return fail(rc, err);
+        }
+        return DMRG_OK;
+    }
+    SplitState* S = split;
+    for (int nv = 1; nv <= max_nvec; ++nv) {
+        SplitHost& H = S->hosts[size_t(nv - 1)];
+        SplitDevPlan& D = S->plans[size_t(nv - 1)];
+        build_split_work(H, s);
+        int rc = validate_split_plan(plan, H, &err);
+        if (rc != DMRG_OK) return fail(rc, err);
+        auto put = [&](const std::vector<SWork>& w, SWork** d, size_t* cap) {
+            if (w.size() > *cap) {
+                if (*d) cudaFree(*d);
+                *d = nullptr;
+                *cap = 0;
+                cudaError_t e = cudaMalloc(reinterpret_cast<void**>(d), sizeof(SWork) * w.size());
+                if (e != cudaSuccess) return cuda_fail(e, "split work");
+                *cap = w.size();
+            }
+            if (w.empty()) return int(DMRG_OK);
+            cudaError_t e = cudaMemcpy(*d, w.data(), sizeof(SWork) * w.size(), cudaMemcpyHostToDevice);
+            return e == cudaSuccess ? int(DMRG_OK) : cuda_fail(e, "split work");
+        };
+        if ((rc = put(H.w1, &D.work1, &S->cap_w1[size_t(nv - 1)])) != DMRG_OK) return rc;
+        if ((rc = put(H.w2, &D.work2, &S->cap_w2[size_t(nv - 1)])) != DMRG_OK) return rc;
+        D.n_work1 = int64_t(H.w1.size());
+        D.n_work2 = int64_t(H.w2.size());
+        D.r1 = H.r1;
+        D.r2 = H.r2;
+    }
+    return DMRG_OK;
+}
+
+const SplitHost* Handle::split_plan_host(int nv) const {
+    if (!split || nv < 1 || nv > int(split->hosts.size())) return nullptr;
+    return &split->hosts[size_t(nv - 1)];
+}
 
 void Handle::release_split() {
     delete split;

@@ -238,15 +238,43 @@ int build_plan(const int32_t* left, int32_t nl, const int32_t* right, int32_t nr
         s2gemm.push_back(int32_t(P.gemms.size()));
         P.gemms.push_back(m);
     }
-    for (int32_t gi : s1gemm) {
+    P.s1gemms = s1gemm;
+    P.s2gemms = s2gemm;
+    return build_fp64_work(P, Schedule{}, err);
+}
+
+int check_schedule(const Schedule& S, std::string* err) {
+    for (int c = 0; c < N_KCLASS; ++c) {
+        if (S.fp64_kchunk[c] < 0 || S.fp64_kchunk[c] % FP64_BK || S.fp64_kchunk[c] > (1 << 24)) {
+            *err = "schedule: FP64 K chunk must be 0 or a positive multiple of 16";
+            return DMRG_ERR_INVALID_ARG;
+        }
+        if (S.split_kchunk[c] < 0 || S.split_kchunk[c] % 8 || S.split_kchunk[c] > 256) {
+            *err = "schedule: split K chunk must be 0 or a multiple of 8 K tiles up to 256";
+            return DMRG_ERR_INVALID_ARG;
+        }
+    }
+    if (S.fp64_ctas_per_sm < 0 || S.fp64_ctas_per_sm > 64 || (S.per_gemm != 0 && S.per_gemm != 1)) {
+        *err = "schedule: CTAs per SM in [0, 64], per_gemm 0 or 1";
+        return DMRG_ERR_INVALID_ARG;
+    }
+    return DMRG_OK;
+}
+
+int build_fp64_work(Plan& P, const Schedule& S, std::string* err) {
+    int rc = check_schedule(S, err);
+    if (rc != DMRG_OK) return rc;
+    P.tiles1.clear(); P.tiles2.clear(); P.reduces.clear(); P.ranges1.clear(); P.ranges2.clear();
+    for (int32_t gi : P.s1gemms) {
         const Gemm& m = P.gemms[gi];
         for (int32_t m0 = 0; m0 < m.M; m0 += FP64_BM)
             for (int32_t n0 = 0; n0 < m.N; n0 += FP64_BN) P.tiles1.push_back({0, m.K, gi, m0, n0, -1});
     }
     int64_t slot = 0;
-    for (int32_t gi : s2gemm) {
+    for (int32_t gi : P.s2gemms) {
         const Gemm& m = P.gemms[gi];
-        const int64_t ns = (m.K + FP64_KCHUNK - 1) / FP64_KCHUNK;
+        const int64_t kc = S.fp64_kchunk[kclass(m.K)] > 0 ? S.fp64_kchunk[kclass(m.K)] : m.K;
+        const int64_t ns = kc > 0 ? (m.K + kc - 1) / kc : 1;
         for (int32_t m0 = 0; m0 < m.M; m0 += FP64_BM)
             for (int32_t n0 = 0; n0 < m.N; n0 += FP64_BN) {
                 if (ns <= 1) {
@@ -255,20 +283,36 @@ int build_plan(const int32_t* left, int32_t nl, const int32_t* right, int32_t nr
                 }
                 P.reduces.push_back({gi, m0, n0, int32_t(slot), int32_t(ns), 0});
                 for (int64_t s = 0; s < ns; ++s)
-                    P.tiles2.push_back({s * FP64_KCHUNK, std::min(m.K, (s + 1) * FP64_KCHUNK), gi, m0,
-                                        n0, int32_t(slot + s)});
+                    P.tiles2.push_back({s * kc, std::min(m.K, (s + 1) * kc), gi, m0, n0, int32_t(slot + s)});
                 slot += ns;
+                if (slot > (int64_t(1) << 31) / (FP64_BM * FP64_BN)) {
+                    *err = "too many partial tiles";
+                    return DMRG_ERR_INVALID_ARG;
+                }
             }
     }
     P.n_slots = slot;
-    if (slot > (int64_t(1) << 31) / (FP64_BM * FP64_BN)) {
-        *err = "too many partial tiles";
-        return DMRG_ERR_INVALID_ARG;
-    }
-    // Largest K range first (the kernels take tiles in this order).
+    // Largest K range first (the kernels take tiles in this order); one launch per GEMM
+    // takes each GEMM's tiles as one contiguous range instead.
     auto by_cost = [](const Tile& x, const Tile& y) { return (x.k1 - x.k0) > (y.k1 - y.k0); };
-    std::stable_sort(P.tiles1.begin(), P.tiles1.end(), by_cost);
-    std::stable_sort(P.tiles2.begin(), P.tiles2.end(), by_cost);
+    auto by_gemm = [](const Tile& x, const Tile& y) {
+        return x.gemm != y.gemm ? x.gemm < y.gemm : (x.k1 - x.k0) > (y.k1 - y.k0);
+    };
+    for (int st = 0; st < 2; ++st) {
+        std::vector<Tile>& T = st == 0 ? P.tiles1 : P.tiles2;
+        if (!S.per_gemm) {
+            std::stable_sort(T.begin(), T.end(), by_cost);
+            continue;
+        }
+        std::stable_sort(T.begin(), T.end(), by_gemm);
+        auto& R = st == 0 ? P.ranges1 : P.ranges2;
+        for (int32_t i = 0; i < int32_t(T.size());) {
+            int32_t j = i;
+            while (j < int32_t(T.size()) && T[j].gemm == T[i].gemm) ++j;
+            R.push_back({i, j});
+            i = j;
+        }
+    }
     return DMRG_OK;
 }
 

@@ -53,6 +53,18 @@ struct Reduce {
 
 struct PsiBlock { int32_t iL, iR, rows, cols; int64_t off; };
 
+// How the planned GEMMs are cut into work items and launched (what is computed does
+// not depend on it).  Stage-2 GEMMs fall into shape classes by contraction length:
+// K <= 2048, K <= 16384, longer.
+constexpr int N_KCLASS = 3;
+inline int kclass(int64_t K) { return K <= 2048 ? 0 : (K <= 16384 ? 1 : 2); }
+struct Schedule {
+    int32_t fp64_kchunk[N_KCLASS] = {512, 512, 512};   // K per FP64 stage-2 item (0: whole K)
+    int32_t fp64_ctas_per_sm = 0;                      // 0: the occupancy limit
+    int32_t split_kchunk[N_KCLASS] = {0, 0, 0};        // K tiles per split stage-2 item (0: adaptive)
+    int32_t per_gemm = 0;                              // 1: one launch per grouped GEMM
+};
+
 struct Group {
     int32_t dn, d2sz, parity;
     int32_t in_block, out_block;
@@ -77,16 +89,17 @@ struct Plan {
     // FP64 grouped-GEMM work lists
     std::vector<Seg> segs;
     std::vector<Gemm> gemms;
+    std::vector<int32_t> s1gemms, s2gemms;   // GEMM indices of the two stages
     std::vector<Tile> tiles1, tiles2;
     std::vector<Reduce> reduces;
     int64_t n_slots = 0;                // partial slots per vector
+    // per-GEMM launch ranges [first, last) into tiles1 / tiles2 (per_gemm schedules)
+    std::vector<std::pair<int32_t, int32_t>> ranges1, ranges2;
     int64_t diag_terms = 0;
 };
 
-// Tile shape of the FP64 kernels.
+// Tile shape of the FP64 kernels (the K extent of stage-2 items is scheduled).
 constexpr int FP64_BM = 32, FP64_BN = 32, FP64_BK = 16;
-// Stage-2 K range per work item (multiple of FP64_BK).
-constexpr int64_t FP64_KCHUNK = 512;
 
 // Validates the inputs and builds the plan; returns 0 or a DMRG_ERR_* code with
 // a message in *err.
@@ -94,6 +107,11 @@ int build_plan(const int32_t* left, int32_t nl, const int32_t* right, int32_t nr
                int32_t tn, int32_t t2sz, const double* coef, const int32_t* delta,
                const int32_t* parity, const int64_t* a_off, const int64_t* b_off,
                int64_t T, int64_t op_len, Plan& P, std::string* err);
+
+// (Re)builds the FP64 tile lists of P for schedule S; returns 0 or DMRG_ERR_INVALID_ARG.
+int build_fp64_work(Plan& P, const Schedule& S, std::string* err);
+// Checks the ranges of a schedule (not its fit to a plan).
+int check_schedule(const Schedule& S, std::string* err);
 
 // Fills the device operator layout (host staging buffer of P.ops_len doubles).
 void fill_ops(const Plan& P, const double* coef, const int64_t* a_off, const int64_t* b_off,

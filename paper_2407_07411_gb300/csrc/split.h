@@ -120,6 +120,7 @@ struct SplitHost {
     std::vector<SSeg> segs;
     std::vector<SJob> jobs;
     std::vector<SWork> w1, w2;
+    std::vector<std::pair<int32_t, int32_t>> r1, r2;   // per-GEMM ranges of w1 / w2 (per_gemm)
     std::vector<SBlock> blocks;
     std::vector<SPart> parts;
     std::vector<SSlab> slabs;
@@ -133,7 +134,9 @@ struct SplitHost {
 
 int64_t cdiv(int64_t a, int64_t b);
 int32_t fshift_for(int64_t K);
-int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err);
+int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err, const Schedule& S = Schedule{});
+// (Re)builds the work lists w1, w2 (and their per-GEMM ranges) of H from its GEMMs.
+void build_split_work(SplitHost& H, const Schedule& S);
 int validate_split_plan(const Plan& P, const SplitHost& H, std::string* err);
 
 }  // namespace dmrg
