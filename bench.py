@@ -34,8 +34,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 NCU_TRAFFIC = {
     # k_fp64_tiles, mid workload: (280.8 + 358.1) / 2 MB per launch (profiles/fp64_tiles_mid.md)
     "7ea6b95187a63352e09b039a09918be5e89d2a14561ebf2f4d93d0eae118ec22": 319.5e6,
-    # k_umma, mid workload: (495.3 + 1417.1) / 2 MB per launch (profiles/split_umma_mid.md)
-    "c67c0afcc471dfd948533386ab0c1ea267f83204aecd40649b7d86b3ad7a42e8": 956.2e6,
+    # k_umma, mid workload: (489.1 + 1369.5) / 2 MB per launch (profiles/split_umma_mid.md)
+    "a83b765028285a201b8e5c47d6045e7590cff99a854292959ef11bfe8c8b9548": 929.3e6,
 }
 
 
@@ -168,8 +168,8 @@ def roofline(stats, precision, fp64_peak, timed_long):
     if name.startswith("fp64"):
         peak, src, src_name = fp64_peak, "measured live: DMMA m16n8k16 probe (dmrg_probe_fp64_peak)", "k_fp64.cu"
     else:
-        # split path: each FP64-equivalent multiply-add costs 15 BF16 slice-pair
-        # multiply-adds, so the FP64-equivalent ceiling is the BF16 peak / 15
+        # split path: each FP64-equivalent multiply-add costs SPLIT_PAIRS BF16 slice-pair
+        # multiply-adds, so the FP64-equivalent ceiling is the BF16 peak / SPLIT_PAIRS
         pk = peaks()
         key = "bf16_tflops_sustained" if timed_long else "bf16_tflops"
         bf16 = pk.get(key, 1700.0 if timed_long else 1900.0)
