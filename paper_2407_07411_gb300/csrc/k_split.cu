@@ -14,6 +14,7 @@
 // the handle's status word, drains its own copies and MMAs and releases TMEM.
 #include <algorithm>
 #include <climits>
+#include <cstddef>
 #include <cstdint>
 #include <vector>
 
@@ -490,6 +491,14 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
                      "r"(UM_TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    // zero the operand stages once: rows that are never copied then hold valid digits
+    {
+        uint4* z = reinterpret_cast<uint4*>(&sm.L[0][0]);
+        constexpr int n16 = int((sizeof(sm.L) + sizeof(sm.R)) / 16);
+        static_assert(offsetof(UmmaSmem, R) == sizeof(UmmaSmem::L), "stages are contiguous");
+        for (int i = threadIdx.x; i < n16; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
     if (threadIdx.x == 0) {
         for (int s = 0; s < UM_STAGES; ++s) {
             mbar_init(&sm.full[s], 1);
@@ -519,13 +528,30 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
             const SGemm G = a.gemms[W.gemm];
             const uint16_t* Lb = (G.l_buf ? a.ap_sl + int64_t(v) * a.ap_sl_vs : a.op_sl) + G.l_tiles;
             const uint16_t* Rb = (G.r_buf ? a.ap_sl + int64_t(v) * a.ap_sl_vs : a.op_sl) + G.r_tiles;
+            // only the 8-row groups that hold rows of the GEMM are copied: the first lg (rg)
+            // 512-byte groups of every slice; the rest of the stage keeps digits of an
+            // earlier tile (or the zeros of set-up), whose products land in accumulator
+            // rows / columns that the epilogue never reads
+            const int lg = (min(SPL_TM, G.M - W.mtile * SPL_TM) + 7) >> 3;
+            const int rg = (min(SPL_TN, G.N - W.ntile * SPL_TN) + 7) >> 3;
+            const uint32_t lbytes = uint32_t(lg) * 512u, rbytes = uint32_t(rg) * 512u;
             for (int kt = W.k0; kt < W.k1; ++kt, ++kidx) {
                 const int s = int(kidx % UM_STAGES);
                 const int64_t n = kidx / UM_STAGES;
                 if (n > 0 && !(ok = mbar_wait(sm, &sm.empty[s], uint32_t((n - 1) & 1), a.status))) break;
-                mbar_expect_tx(&sm.full[s], UM_L_BYTES + UM_R_BYTES);
-                bulk_g2s(sm.L[s], Lb + (int64_t(W.mtile) * G.kt + kt) * (SPL_S * SPL_LT), UM_L_BYTES, &sm.full[s]);
-                bulk_g2s(sm.R[s], Rb + (int64_t(W.ntile) * G.kt + kt) * (SPL_S * SPL_RT), UM_R_BYTES, &sm.full[s]);
+                mbar_expect_tx(&sm.full[s], uint32_t(SPL_S) * (lbytes + rbytes));
+                const uint16_t* lt = Lb + (int64_t(W.mtile) * G.kt + kt) * (SPL_S * SPL_LT);
+                const uint16_t* rt = Rb + (int64_t(W.ntile) * G.kt + kt) * (SPL_S * SPL_RT);
+                if (lbytes == UM_L_BYTES / SPL_S) {
+                    bulk_g2s(sm.L[s], lt, UM_L_BYTES, &sm.full[s]);
+                } else {
+                    for (int q = 0; q < SPL_S; ++q) bulk_g2s(sm.L[s] + q * SPL_LT, lt + q * SPL_LT, lbytes, &sm.full[s]);
+                }
+                if (rbytes == UM_R_BYTES / SPL_S) {
+                    bulk_g2s(sm.R[s], rt, UM_R_BYTES, &sm.full[s]);
+                } else {
+                    for (int q = 0; q < SPL_S; ++q) bulk_g2s(sm.R[s] + q * SPL_RT, rt + q * SPL_RT, rbytes, &sm.full[s]);
+                }
             }
         }
         // every issued stage must land before the CTA may exit
