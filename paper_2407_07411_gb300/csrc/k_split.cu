@@ -122,18 +122,19 @@ __device__ __forceinline__ int exp_i64(long long F, int eF) {
     return (64 - __clzll(u)) + eF;          // |F 2^eF| < 2^(msb+1+eF)
 }
 
-// Balanced base-256 digits of the non-negative integer R <= 2^47, most significant
-// first, with the sign applied.
+// Balanced base-256 digits (each in [-127, 128]) of the non-negative integer R <= 2^47,
+// most significant first, with the sign applied.  The digit set is a complete residue
+// system mod 256, so the representation is unique; digit k is byte (5 - k) of
+// R + 0x7F7F7F7F7F7F minus 127 (the added 127s produce exactly the carries), and
+// R <= 2^47 needs no seventh digit.
 __device__ __forceinline__ void balanced_digits(unsigned long long R, bool neg, int (&d)[SPL_S]) {
+    const unsigned long long Rb = R + 0x7F7F7F7F7F7Full;
+    const uint32_t lo = uint32_t(Rb), hi = uint32_t(Rb >> 32);
 #pragma unroll
-    for (int k = SPL_S - 1; k >= 0; --k) {
-        int t = int(R & 255ull);
-        R >>= 8;
-        if (t > 128) {
-            t -= 256;
-            R += 1;
-        }
-        d[k] = neg ? -t : t;
+    for (int k = 0; k < SPL_S; ++k) {
+        const int byte = SPL_S - 1 - k;
+        const int b = int(((byte < 4 ? lo >> (8 * byte) : hi >> (8 * (byte - 4)))) & 255u);
+        d[k] = neg ? 127 - b : b - 127;
     }
 }
 
@@ -160,8 +161,13 @@ __device__ __forceinline__ void digits_i64(long long F, int eF, int E, int (&d)[
     balanced_digits(R, F < 0, d);
 }
 
+// BF16 bit pattern of d 2^(-8k) for a digit |d| <= 128 (exact: 8 significant bits).
+// float(d) is formed as (2^23 + (d + 128)) - (2^23 + 128): both lie in [2^23, 2^24)
+// where FP32 holds every integer, so the difference is exact, with full-rate FP32
+// operations instead of an int->float conversion.
 __device__ __forceinline__ uint16_t digit_bf16(int d, int k) {
-    const float f = float(d) * __int_as_float((127 - 8 * k) << 23);   // d * 2^(-8k), exact
+    const float x = __uint_as_float(0x4B000000u + uint32_t(d + 128));   // 2^23 + d + 128
+    const float f = (x - 8388736.0f) * __int_as_float((127 - 8 * k) << 23);   // d * 2^(-8k)
     return uint16_t(__float_as_uint(f) >> 16);
 }
 
@@ -276,13 +282,10 @@ __global__ void __launch_bounds__(32 * DIG_WARPS) k_slice_digits(TileArgs a) {
 #pragma unroll
                 for (int q = 0; q < SPL_S; ++q) d[vv][q] = 0;
             if (K < J.K) {
-                int kb = 0, sg = J.seg0;
-                for (; sg < J.seg0 + J.nseg - 1; ++sg) {
-                    const int ext = a.segs[sg].kc * a.segs[sg].nt;
-                    if (K < kb + ext) break;
-                    kb += ext;
-                }
+                int sg = T.seg;   // holds the tile's first K; later runs follow in order
+                while (sg < J.seg0 + J.nseg - 1 && K >= a.segs[sg + 1].kbase) ++sg;
                 const SSeg g = a.segs[sg];
+                const int kb = g.kbase;
                 const int t = (K - kb) / g.kc, k = (K - kb) - t * g.kc;
                 const int64_t base = g.off + t * g.ts + k * g.ks;
                 int vg = (8 * T.vg) / g.vper, vr = 8 * T.vg - vg * g.vper;
@@ -779,6 +782,7 @@ int validate_split_plan(const Plan& P, const SplitHost& H, std::string* err) {
         int64_t K = 0;
         for (int s = J.seg0; s < J.seg0 + J.nseg; ++s) {
             const SSeg& g = H.segs[s];
+            if (g.kbase != K) return bad("segment K base");
             K += int64_t(g.kc) * g.nt;
             if (J.nvalid == 0 || g.kc <= 0 || g.nt <= 0) continue;
             if (g.vper < 1) return bad("vector grouping");
@@ -794,6 +798,13 @@ int validate_split_plan(const Plan& P, const SplitHost& H, std::string* err) {
             }
         }
         if (K != J.K) return bad("job K");
+    }
+    for (const STile& T : H.tiles) {   // the digit pass starts its segment search at T.seg
+        if (T.job < 0 || T.job >= int32_t(H.jobs.size())) return bad("tile job");
+        const SJob& J = H.jobs[size_t(T.job)];
+        if (T.seg < J.seg0 || T.seg >= J.seg0 + J.nseg || T.k0 < 0 || T.k0 >= J.K || 8 * T.vg >= J.nvalid ||
+            H.segs[size_t(T.seg)].kbase > T.k0)
+            return bad("tile segment");
     }
     auto check_work = [&](const std::vector<SWork>& w) {
         for (const SWork& x : w) {
@@ -918,7 +929,12 @@ int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err, cons
         J.kt = int32_t(cdiv(K, SPL_TK));
         J.seg0 = int32_t(segs.size());
         J.nseg = int32_t(js.size());
-        segs.insert(segs.end(), js.begin(), js.end());
+        int32_t kb = 0;
+        for (SSeg g : js) {
+            g.kbase = kb;
+            kb += g.kc * g.nt;
+            segs.push_back(g);
+        }
         int64_t& sl = out_buf ? ap_sl : op_sl;
         int64_t& ex = out_buf ? ap_ex : op_ex;
         J.out_tiles = sl;
@@ -1076,8 +1092,14 @@ int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err, cons
     std::vector<STile>& tiles = H.tiles;
     auto add_tiles = [&](const std::vector<int32_t>& js) {
         for (int32_t j : js)
-            for (int vg = 0; 8 * vg < jobs[j].nvalid; ++vg)
-                for (int k0 = 0; k0 < jobs[j].K; k0 += SPL_TILE_K) tiles.push_back({j, vg, k0, 0});
+            for (int vg = 0; 8 * vg < jobs[j].nvalid; ++vg) {
+                int32_t sg = jobs[j].seg0;
+                for (int k0 = 0; k0 < jobs[j].K; k0 += SPL_TILE_K) {
+                    while (sg < jobs[j].seg0 + jobs[j].nseg - 1 && k0 >= segs[sg].kbase + segs[sg].kc * segs[sg].nt)
+                        ++sg;
+                    tiles.push_back({j, vg, k0, sg});
+                }
+            }
     };
     H.tl_op0 = 0;
     add_tiles(op_jobs);

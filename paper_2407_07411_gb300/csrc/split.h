@@ -83,6 +83,7 @@ struct SSeg {
     int64_t er_off, ec_off;
     int32_t space, kc, nt, er_ts;
     int32_t is_i64, e_off, vper, ec_vgs;
+    int32_t kbase, pad;   // first K index of the run inside its job
 };
 
 // Slice one operand: vectors [0, npad) (valid below nvalid) along K [0, kt*32) (valid
@@ -100,8 +101,9 @@ struct SSlab { int64_t rows; int32_t job, seg, kbase, pad; };
 // A run of up to SPL_ROWS_PER_ITEM rows of one slab, the unit of work of the slicer.
 struct SItem { int64_t r0; int32_t slab, nrows; };
 constexpr int SPL_ROWS_PER_ITEM = 64;
-// Output tile of the digit pass: vectors [8 vg, 8 vg + 8) x K [k0, k0 + SPL_TILE_K) of one job.
-struct STile { int32_t job, vg, k0, pad; };
+// Output tile of the digit pass: vectors [8 vg, 8 vg + 8) x K [k0, k0 + SPL_TILE_K) of one
+// job; seg is the job's segment that holds K index k0.
+struct STile { int32_t job, vg, k0, seg; };
 constexpr int SPL_TILE_K = 256;
 
 // Output block of the wave function and the stage-2 sums that land on it.  Entry (i, j)
