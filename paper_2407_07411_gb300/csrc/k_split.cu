@@ -429,21 +429,18 @@ __device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&r)[8]) {
                  : "r"(addr));
 }
 
+// Work list of one slice-GEMM launch (the Davidson vectors of an apply are stacked
+// inside its GEMMs).
 struct UmmaArgs {
     const SWork* work;
     int64_t n_work;
     const SGemm* gemms;
     const uint16_t* op_sl;
     const uint16_t* ap_sl;
-    int64_t ap_sl_vs;
     int64_t* s1;
-    int64_t s1_vs;
     int64_t* s2;
-    int64_t s2_vs;
     const int32_t* op_ex;
     int32_t* ap_ex;
-    int64_t ap_ex_vs;
-    int nvec;
     int* status;
 };
 
@@ -519,18 +516,30 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = sm.tmem_base;
-    const int64_t total = a.n_work * a.nvec;
+    const int64_t total = a.n_work;
+    const int64_t step = gridDim.x;
 
     if (warp == 0 && lane == 0) {
         // ---- producer
         int64_t kidx = 0;
         bool ok = true;
-        for (int64_t it = blockIdx.x; it < total && ok; it += gridDim.x) {
-            const SWork W = a.work[it / a.nvec];
-            const int v = int(it % a.nvec);
-            const SGemm G = a.gemms[W.gemm];
-            const uint16_t* Lb = (G.l_buf ? a.ap_sl + int64_t(v) * a.ap_sl_vs : a.op_sl) + G.l_tiles;
-            const uint16_t* Rb = (G.r_buf ? a.ap_sl + int64_t(v) * a.ap_sl_vs : a.op_sl) + G.r_tiles;
+        // descriptors are loaded ahead (the work item two items ahead, its GEMM one
+        // item ahead), so no dependent global load sits at an item boundary
+        SWork W1{}, W2{};
+        SGemm G1{};
+        if (blockIdx.x < total) {
+            W1 = a.work[blockIdx.x];
+            G1 = a.gemms[W1.gemm];
+        }
+        if (blockIdx.x + step < total) W2 = a.work[blockIdx.x + step];
+        for (int64_t it = blockIdx.x; it < total && ok; it += step) {
+            const SWork W = W1;
+            const SGemm G = G1;
+            W1 = W2;
+            if (it + step < total) G1 = a.gemms[W1.gemm];
+            if (it + 2 * step < total) W2 = a.work[it + 2 * step];
+            const uint16_t* Lb = (G.l_buf ? a.ap_sl : a.op_sl) + G.l_tiles;
+            const uint16_t* Rb = (G.r_buf ? a.ap_sl : a.op_sl) + G.r_tiles;
             // only the 8-row groups that hold rows of the GEMM are copied: the first lg (rg)
             // 512-byte groups of every slice; the rest of the stage keeps digits of an
             // earlier tile (or the zeros of set-up), whose products land in accumulator
@@ -564,8 +573,11 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
         // ---- MMA issuer
         int64_t kidx = 0, dchunk = 0;
         bool ok = true;
-        for (int64_t it = blockIdx.x; it < total && ok; it += gridDim.x) {
-            const SWork W = a.work[it / a.nvec];
+        SWork Wn{};
+        if (blockIdx.x < total) Wn = a.work[blockIdx.x];
+        for (int64_t it = blockIdx.x; it < total && ok; it += step) {
+            const SWork W = Wn;
+            if (it + step < total) Wn = a.work[it + step];
             for (int kc0 = W.k0; kc0 < W.k1 && ok; kc0 += SPL_DRAIN_KT, ++dchunk) {
                 const int kc1 = min(kc0 + SPL_DRAIN_KT, W.k1);
                 for (int kt = kc0; kt < kc1; ++kt, ++kidx) {
@@ -589,10 +601,20 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
         const uint32_t lane_addr = uint32_t(32 * q) << 16;
         int64_t dchunk = 0;
         bool ok = true;
-        for (int64_t it = blockIdx.x; it < total && ok; it += gridDim.x) {
-            const SWork W = a.work[it / a.nvec];
-            const int v = int(it % a.nvec);
-            const int fs = a.gemms[W.gemm].fshift;
+        SWork W1{}, W2{};
+        SGemm G1{};
+        if (blockIdx.x < total) {
+            W1 = a.work[blockIdx.x];
+            G1 = a.gemms[W1.gemm];
+        }
+        if (blockIdx.x + step < total) W2 = a.work[blockIdx.x + step];
+        for (int64_t it = blockIdx.x; it < total && ok; it += step) {
+            const SWork W = W1;
+            const SGemm G = G1;
+            W1 = W2;
+            if (it + step < total) G1 = a.gemms[W1.gemm];
+            if (it + 2 * step < total) W2 = a.work[it + 2 * step];
+            const int fs = G.fshift;
             long long acc[UM_EPI_COLS];   // slice sums of the item in units of 2^-31
 #pragma unroll
             for (int j = 0; j < UM_EPI_COLS; ++j) acc[j] = 0;
@@ -638,7 +660,6 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
 #pragma unroll
             for (int j = 0; j < UM_EPI_COLS; ++j)
                 acc[j] = fs >= 31 ? acc[j] * (1ll << (fs - 31)) : (acc[j] + (1ll << (30 - fs))) >> (31 - fs);
-            const SGemm G = a.gemms[W.gemm];
             const int r = W.mtile * SPL_TM + row;
             const int cbase = W.ntile * SPL_TN + col0;
             if (G.kind == 0) {
@@ -648,9 +669,9 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
                 const bool rv = r < G.M;
                 const int rs = rv ? r : 0;
                 const int cl = cbase + lane;
-                const int cex_l = cl < G.N ? a.ap_ex[int64_t(v) * a.ap_ex_vs + G.ec_off + cl] : 0;
+                const int cex_l = cl < G.N ? a.ap_ex[G.ec_off + cl] : 0;
                 // stage-2 vector of entry (r, c): (c / colgroup) * period + r % period
-                int32_t* x2 = a.ap_ex + int64_t(v) * a.ap_ex_vs + G.x2_exp + rs % G.x2_period;
+                int32_t* x2 = a.ap_ex + G.x2_exp + rs % G.x2_period;
                 const int eoff = (rv ? a.op_ex[G.er_off + rs] : 0) - (14 + G.fshift);
                 int emax = INT_MIN, grp = cbase / G.x2_colgroup;
                 int next = (grp + 1) * G.x2_colgroup;   // first column of the next group
@@ -677,7 +698,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
                 // 4 columns of the warp's 32 rows, written as 8 rows x 32 contiguous bytes
                 // per instruction instead of 32 rows x 8 bytes
                 long long* tp = sm.tr[warp - 2];
-                int64_t* D = a.s1 + int64_t(v) * a.s1_vs + G.d_off;
+                int64_t* D = a.s1 + G.d_off;
                 const int rbase = W.mtile * SPL_TM + 32 * q;
 #pragma unroll
                 for (int c4 = 0; c4 < UM_EPI_COLS; c4 += 4) {
@@ -693,7 +714,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
                     __syncwarp();
                 }
             } else if (r < G.M) {
-                unsigned long long* D = reinterpret_cast<unsigned long long*>(a.s2 + int64_t(v) * a.s2_vs +
+                unsigned long long* D = reinterpret_cast<unsigned long long*>(a.s2 +
                                                                               G.d_off + int64_t(r) * G.ldd);
 #pragma unroll
                 for (int j = 0; j < UM_EPI_COLS; ++j) {
@@ -1254,7 +1275,7 @@ int Handle::apply_split(const double* x, double* y, int32_t nvec, cudaStream_t s
                     double flops, double bytes) {
         if (nw == 0) return cudaSuccess;
         auto launch = [&](const SWork* w0, int64_t n) {
-            UmmaArgs ua{w0, n, D.gemms, S->op_sl, S->ap_sl, 0, S->s1, 0, S->s2, 0, S->op_ex, S->ap_ex, 0, 1, S->status};
+            UmmaArgs ua{w0, n, D.gemms, S->op_sl, S->ap_sl, S->s1, S->s2, S->op_ex, S->ap_ex, S->status};
             k_umma<<<unsigned(std::min<int64_t>(n, n_sm)), UM_THREADS, sizeof(UmmaSmem), st>>>(ua);
             return cudaGetLastError();
         };
