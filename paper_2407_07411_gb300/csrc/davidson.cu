@@ -147,8 +147,13 @@ __global__ void k_diag_set(double* __restrict__ S, int lds, int mmax, const doub
 // Cyclic Jacobi eigensolver of the symmetric m x m matrix S (row stride lds) in one CTA:
 // round-robin (circle-method) ordering, the m/2 disjoint rotations of a round applied
 // together.  theta ascending, U[i*ldu + j] = component i of eigenvector j.
+// Warm start: on entry U[0:mp, 0:mp] (mp < m, or mp = 0 for none) holds the eigenvectors
+// of S[0:mp, 0:mp] from the previous call (the Davidson basis only grew since), so the
+// sweeps start from B^T S B, B = diag(U[0:mp, 0:mp], I), with the rotations accumulated
+// onto B: only the new rows and columns need to be annihilated.
 __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ S, int m, int lds,
-                                                double* __restrict__ theta, double* __restrict__ U, int ldu) {
+                                                double* __restrict__ theta, double* __restrict__ U, int ldu,
+                                                int mp) {
     extern __shared__ double sm[];
     const int M = (m + 1) & ~1;          // even size; a padded index stays decoupled
     const int ld = MAX_BASIS + 1;
@@ -158,10 +163,40 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ S, in
     __shared__ int pp[MAX_BASIS / 2], qq[MAX_BASIS / 2];
     __shared__ int order[MAX_BASIS];
     const int tid = threadIdx.x, nt = blockDim.x;
+    // Z = B;  A = S B (into A), then A = B^T A
     for (int e = tid; e < M * M; e += nt) {
         const int i = e / M, j = e % M;
-        A[i * ld + j] = (i < m && j < m) ? S[i * lds + j] : 0.0;
-        Z[i * ld + j] = i == j ? 1.0 : 0.0;
+        Z[i * ld + j] = (i < mp && j < mp) ? U[i * ldu + j] : (i == j ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    for (int e = tid; e < M * M; e += nt) {
+        const int i = e / M, j = e % M;
+        double v = 0.0;
+        if (i < m && j < m) {
+            if (j < mp)
+                for (int k = 0; k < mp; ++k) v += S[i * lds + k] * Z[k * ld + j];
+            else
+                v = S[i * lds + j];
+        }
+        A[i * ld + j] = v;
+    }
+    __syncthreads();
+    double bt[(MAX_BASIS * MAX_BASIS + 255) / 256];   // this thread's entries of B^T A (256 threads)
+    int nb = 0;
+    for (int e = tid; e < M * M; e += nt) {
+        const int i = e / M, j = e % M;
+        double v = A[i * ld + j];
+        if (i < mp) {
+            v = 0.0;
+            for (int k = 0; k < mp; ++k) v += Z[k * ld + i] * A[k * ld + j];
+        }
+        bt[nb++] = v;
+    }
+    __syncthreads();
+    nb = 0;
+    for (int e = tid; e < M * M; e += nt) {
+        const int i = e / M, j = e % M;
+        A[i * ld + j] = bt[nb++];
     }
     __syncthreads();
     const int half = M / 2;
@@ -384,11 +419,13 @@ extern "C" int dmrg_davidson(dmrg_heff_t hh, int32_t k_eig, double tol, int32_t 
 
     std::vector<double> th(mmax), rn(mmax);
     int it = 0, kb = 0;
+    int m_prev = 0;   // rows of U that diagonalise S[0:m_prev, 0:m_prev] (warm start)
     bool converged = false;
     while (it < max_iter) {
         ++it;
-        k_jacobi<<<1, 256, jac_smem, st>>>(s->S, m, mmax, s->theta, s->U, mmax);
+        k_jacobi<<<1, 256, jac_smem, st>>>(s->S, m, mmax, s->theta, s->U, mmax, m_prev < m ? m_prev : 0);
         if ((rc = run.check(cudaGetLastError(), "jacobi"))) return rc;
+        m_prev = m;
         kb = m < kbmax ? m : kbmax;
         if ((rc = run.lincomb(s->U, mmax, 0, kb, m, s->V, s->X, 0))) return rc;
         if ((rc = run.lincomb(s->U, mmax, 0, kb, m, s->W, s->R, 0))) return rc;
@@ -428,6 +465,7 @@ extern "C" int dmrg_davidson(dmrg_heff_t hh, int32_t k_eig, double tol, int32_t 
                 return rc;
             k_diag_set<<<blocks_for(mmax * mmax), 256, 0, st>>>(s->S, mmax, mmax, s->theta, r);
             m = r;
+            m_prev = 0;   // the rotated basis: S[0:r, 0:r] is diagonal
             ++restarts;
         }
         const int m_old = m;
