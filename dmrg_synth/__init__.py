@@ -231,29 +231,30 @@ def assemble(left, right, target, terms, seed=0, name="custom") -> Problem:
                    dim=wavefunction_dim(left, right, target), seed=seed, name=name)
 
 
-def _random_blocks(table, shift, g, symmetric):
-    """Dense N(0,1)/sqrt(d_in) blocks [q+shift <- q] for every q with q+shift present."""
+def _shift_pairs(table, shift):
+    """(q, p) for every sector q whose shifted sector p = q + shift exists, q ascending."""
     idx = _index(table)
-    out = {}
-    for q, (n, s, dq) in enumerate(table):
+    out = []
+    for q, (n, s, _) in enumerate(table):
         p = idx.get((int(n) + shift[0], int(s) + shift[1]))
-        if p is None:
-            continue
-        m = g.standard_normal((int(table[p][2]), int(dq))) / np.sqrt(float(dq))
-        if symmetric:
-            m = 0.5 * (m + m.T)
-        out[q] = m
+        if p is not None:
+            out.append((q, p))
     return out
 
 
 def generate(name: str, seed: int = 0, n_terms: int | None = None) -> Problem:
-    """Build the named workload with the given seed (optionally fewer terms)."""
+    """Build the named workload with the given seed (optionally fewer terms).
+
+    The operator data is laid out first (per term its A blocks, then its B blocks, each
+    in ascending input sector) and every block is drawn straight into that one array,
+    so the peak host memory is the operator data itself.  Term t's blocks come from
+    its own Philox stream in layout order (A then B); an adjoint partner's blocks are
+    the transposes of the forward term's."""
     cfg = dict(CONFIGS[name])
     if n_terms is not None:
         cfg["T"] = int(n_terms)
     table = sector_table(cfg, seed)
     left = right = table
-    idx = _index(table)
     T = cfg["T"]
     g = philox(seed, STREAM_TERMS)
     kinds = []
@@ -265,20 +266,41 @@ def generate(name: str, seed: int = 0, n_terms: int | None = None) -> Problem:
         else:
             kinds.append(("fwd", d, c))
             kinds.append(("adj", (-d[0], -d[1]), c if d[0] % 2 == 0 else -c))
-    terms = []
-    for t, (kind, d, c) in enumerate(kinds):
-        par = 1 if d[0] % 2 else 0
-        if kind == "adj":
-            _, _, _, fa, fb = terms[t - 1]
+    dims = [int(x) for x in table[:, 2]]
+    a_off = -np.ones((T, len(left)), np.int64)
+    b_off = -np.ones((T, len(right)), np.int64)
+    pairs = {}
+    pos = 0
+    for t, (_, d, _) in enumerate(kinds):
+        for off, shift in ((a_off, d), (b_off, (-d[0], -d[1]))):
+            if shift not in pairs:
+                pairs[shift] = _shift_pairs(table, shift)
+            for q, p in pairs[shift]:
+                off[t, q] = pos
+                pos += dims[p] * dims[q]
+    op = np.empty(pos, np.float64)
+
+    def block(off, t, q, p):
+        return op[off[t, q]:off[t, q] + dims[p] * dims[q]].reshape(dims[p], dims[q])
+
+    for t, (kind, d, _) in enumerate(kinds):
+        if kind == "adj":   # A'[q <- p] = A[p <- q]^T of the forward partner, B likewise
             dn, ds = -d[0], -d[1]      # the partner's (forward) shift
-            ab, bb = {}, {}
-            for q, m in fa.items():     # A[q+dF <- q]^T is A'[q <- q+dF]
-                ab[idx[(int(left[q][0]) + dn, int(left[q][1]) + ds)]] = np.ascontiguousarray(m.T)
-            for q, m in fb.items():     # B[q-dF <- q]^T is B'[q <- q-dF]
-                bb[idx[(int(right[q][0]) - dn, int(right[q][1]) - ds)]] = np.ascontiguousarray(m.T)
-        else:
-            gt = philox(seed, 1 + t)
-            ab = _random_blocks(left, d, gt, kind == "self")
-            bb = _random_blocks(right, (-d[0], -d[1]), gt, kind == "self")
-        terms.append((c, d, par, ab, bb))
-    return assemble(left, right, cfg["target"], terms, seed=seed, name=name)
+            for off, shift in ((a_off, (dn, ds)), (b_off, (-dn, -ds))):
+                for q, p in pairs[shift]:
+                    block(off, t, p, q)[...] = block(off, t - 1, q, p).T
+            continue
+        gt = philox(seed, 1 + t)
+        for off, shift in ((a_off, d), (b_off, (-d[0], -d[1]))):
+            for q, p in pairs[shift]:
+                m = gt.standard_normal((dims[p], dims[q])) / np.sqrt(float(dims[q]))
+                if kind == "self":
+                    m = 0.5 * (m + m.T)
+                block(off, t, q, p)[...] = m
+    return Problem(left=np.asarray(left, np.int32).reshape(-1, 3), right=np.asarray(right, np.int32).reshape(-1, 3),
+                   target=(int(cfg["target"][0]), int(cfg["target"][1])),
+                   coef=np.array([k[2] for k in kinds], np.float64),
+                   delta=np.array([k[1] for k in kinds], np.int32).reshape(T, 2),
+                   parity=np.array([1 if k[1][0] % 2 else 0 for k in kinds], np.int32),
+                   a_off=a_off, b_off=b_off, op_data=op,
+                   dim=wavefunction_dim(left, right, cfg["target"]), seed=seed, name=name)

@@ -187,7 +187,7 @@ int dmrg_heff_apply_noalloc(const int32_t* left, int32_t nl, const int32_t* righ
  * to the order of its split-K sums).  Stage-2 GEMMs fall into three shape classes by
  * contraction length K: [0] K <= 2048, [1] K <= 16384, [2] longer.
  *   fp64_kchunk[c]    K per FP64 stage-2 work item of class c: 0 (whole K, no split)
- *                     or a positive multiple of 16.  Default 512.
+ *                     or a positive multiple of 16.  Default 512, 512, 2048.
  *   fp64_ctas_per_sm  resident CTAs of the FP64 tile kernel per SM, 0..64; 0 (default)
  *                     and values above the occupancy limit mean that limit.
  *   split_kchunk[c]   K tiles (of 32) per split stage-2 work item of class c: 0

@@ -3,6 +3,7 @@
 // k_*.cu; this file only validates, allocates, uploads and launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -332,11 +333,36 @@ int dmrg_heff_create(const int32_t* left, int32_t nl, const int32_t* right, int3
         delete h;
         return code;
     };
-    // Operators in the grouped device layout.
+    // Operators in the grouped device layout, streamed through a bounded host buffer (the
+    // host never holds a second copy of the operator data).
     if (P.ops_len > 0) {
-        std::vector<double> staging(size_t(P.ops_len));
-        dmrg::fill_ops(P, coef, a_off, b_off, op_data, staging.data());
-        if ((rc = dmrg::upload(staging, &h->d_ops, "operators")) != DMRG_OK) return bail(rc);
+        if ((rc = dmrg::dalloc(reinterpret_cast<void**>(&h->d_ops), sizeof(double) * size_t(P.ops_len),
+                               "operators")) != DMRG_OK)
+            return bail(rc);
+        const size_t cap = size_t(std::min<int64_t>(P.ops_len, int64_t(1) << 25));   // 256 MB
+        std::vector<double> stage(cap);
+        size_t fill = 0;
+        int64_t dst = 0;
+        cudaError_t ce = cudaSuccess;
+        auto flush = [&]() {
+            if (fill > 0 && ce == cudaSuccess)
+                ce = cudaMemcpy(h->d_ops + dst, stage.data(), sizeof(double) * fill, cudaMemcpyHostToDevice);
+            dst += int64_t(fill);
+            fill = 0;
+        };
+        dmrg::stream_ops(P, coef, a_off, b_off, op_data, [&](const double* src, int64_t n, double scale) {
+            while (n > 0) {
+                const int64_t k = std::min<int64_t>(n, int64_t(cap - fill));
+                for (int64_t e = 0; e < k; ++e) stage[fill + size_t(e)] = scale * src[e];
+                fill += size_t(k);
+                src += k;
+                n -= k;
+                if (fill == cap) flush();
+            }
+        });
+        flush();
+        if (ce != cudaSuccess) return bail(dmrg::cuda_fail(ce, "operators"));
+        if (dst != P.ops_len) return bail(dmrg::fail(DMRG_ERR_BOUNDS, "operator layout size"));
     }
     const size_t nv = size_t(o.max_nvec);
     if ((rc = dmrg::upload(P.gemms, &h->d_gemms, "gemms")) != DMRG_OK) return bail(rc);

@@ -4,8 +4,10 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <climits>
 #include <array>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <tuple>
 
@@ -285,7 +287,7 @@ int build_fp64_work(Plan& P, const Schedule& S, std::string* err) {
                 for (int64_t s = 0; s < ns; ++s)
                     P.tiles2.push_back({s * kc, std::min(m.K, (s + 1) * kc), gi, m0, n0, int32_t(slot + s)});
                 slot += ns;
-                if (slot > (int64_t(1) << 31) / (FP64_BM * FP64_BN)) {
+                if (slot > INT32_MAX) {   // slot indices are int32 (offsets are formed in int64)
                     *err = "too many partial tiles";
                     return DMRG_ERR_INVALID_ARG;
                 }
@@ -316,19 +318,13 @@ int build_fp64_work(Plan& P, const Schedule& S, std::string* err) {
     return DMRG_OK;
 }
 
-void fill_ops(const Plan& P, const double* coef, const int64_t* a_off, const int64_t* b_off,
-              const double* op_data, double* ops) {
+void stream_ops(const Plan& P, const double* coef, const int64_t* a_off, const int64_t* b_off,
+                const double* op_data, const std::function<void(const double*, int64_t, double)>& sink) {
     for (const Group& G : P.groups) {
         const PsiBlock& B = P.blocks[G.in_block];
         const int64_t na = int64_t(G.a) * G.b, nb = int64_t(G.d) * G.c;
-        for (size_t j = 0; j < G.terms.size(); ++j) {
-            const int64_t t = G.terms[j];
-            const double* A = op_data + a_off[t * P.nl + B.iL];
-            const double* Bm = op_data + b_off[t * P.nr + B.iR];
-            double* Ad = ops + G.a_stack + int64_t(j) * na;
-            for (int64_t e = 0; e < na; ++e) Ad[e] = coef[t] * A[e];
-            std::memcpy(ops + G.b_stack + int64_t(j) * nb, Bm, sizeof(double) * nb);
-        }
+        for (int32_t t : G.terms) sink(op_data + a_off[int64_t(t) * P.nl + B.iL], na, coef[t]);
+        for (int32_t t : G.terms) sink(op_data + b_off[int64_t(t) * P.nr + B.iR], nb, 1.0);
     }
 }
 

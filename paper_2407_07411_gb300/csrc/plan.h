@@ -12,6 +12,7 @@
 // (all groups that land on it), reduced in a fixed order without atomics.
 #pragma once
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -59,7 +60,7 @@ struct PsiBlock { int32_t iL, iR, rows, cols; int64_t off; };
 constexpr int N_KCLASS = 3;
 inline int kclass(int64_t K) { return K <= 2048 ? 0 : (K <= 16384 ? 1 : 2); }
 struct Schedule {
-    int32_t fp64_kchunk[N_KCLASS] = {512, 512, 512};   // K per FP64 stage-2 item (0: whole K)
+    int32_t fp64_kchunk[N_KCLASS] = {512, 512, 2048};  // K per FP64 stage-2 item (0: whole K)
     int32_t fp64_ctas_per_sm = 0;                      // 0: the occupancy limit
     int32_t split_kchunk[N_KCLASS] = {0, 0, 0};        // K tiles per split stage-2 item (0: adaptive)
     int32_t per_gemm = 0;                              // 1: one launch per grouped GEMM
@@ -113,8 +114,9 @@ int build_fp64_work(Plan& P, const Schedule& S, std::string* err);
 // Checks the ranges of a schedule (not its fit to a plan).
 int check_schedule(const Schedule& S, std::string* err);
 
-// Fills the device operator layout (host staging buffer of P.ops_len doubles).
-void fill_ops(const Plan& P, const double* coef, const int64_t* a_off, const int64_t* b_off,
-              const double* op_data, double* ops);
+// Visits the device operator layout in memory order: per group its stacked c_t A_t
+// blocks, then its B_t blocks; sink(src, n, scale) receives n doubles to be scaled.
+void stream_ops(const Plan& P, const double* coef, const int64_t* a_off, const int64_t* b_off,
+                const double* op_data, const std::function<void(const double*, int64_t, double)>& sink);
 
 }  // namespace dmrg

@@ -1,6 +1,6 @@
-"""Writes tests/golden/synth_digests.json: structure digests of the seeded
-workloads, their oracle plan flop totals and the oracle ground-state energy of
-the mid workload.  Calls only dmrg_synth and
+"""Writes tests/golden/synth_digests.json: structure and full byte digests of the
+seeded workloads, their oracle plan flop totals and the oracle ground-state energy
+of the mid workload.  Calls only dmrg_synth and
 oracle; run from the repository root:  python tests/golden/make_golden.py"""
 import json
 import os
@@ -16,7 +16,7 @@ out = {}
 for name in ("tiny", "mid"):
     p = S.generate(name, seed=0)
     plan = heff.plan(p)
-    out[name] = dict(structure_sha256=p.structure_digest(), dim=p.dim, n_terms=p.n_terms,
+    out[name] = dict(structure_sha256=p.structure_digest(), sha256=p.digest(), dim=p.dim, n_terms=p.n_terms,
                      op_len=int(p.op_data.size), plan_items=int(len(plan)),
                      plan_flops=int(plan[:, 4].sum()))
     if name == "mid":

@@ -12,7 +12,7 @@ from tests.gpu_util import gpu_apply, rel_fro
 
 pytestmark = pytest.mark.gpu
 lib = pytest.importorskip("paper_2407_07411_gb300")
-DEFAULT = dict(fp64_kchunk=[512, 512, 512], fp64_ctas_per_sm=0, split_kchunk=[0, 0, 0], per_gemm=0)
+DEFAULT = dict(fp64_kchunk=[512, 512, 2048], fp64_ctas_per_sm=0, split_kchunk=[0, 0, 0], per_gemm=0)
 
 
 @pytest.mark.parametrize("name,n_terms", [("mid", 200), ("heavy", 80)])

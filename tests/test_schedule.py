@@ -9,7 +9,7 @@ from oracle import heff
 
 lib = pytest.importorskip("paper_2407_07411_gb300")
 
-DEFAULT = dict(fp64_kchunk=[512, 512, 512], fp64_ctas_per_sm=0, split_kchunk=[0, 0, 0], per_gemm=0)
+DEFAULT = dict(fp64_kchunk=[512, 512, 2048], fp64_ctas_per_sm=0, split_kchunk=[0, 0, 0], per_gemm=0)
 
 
 def test_default_schedule():

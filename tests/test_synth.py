@@ -46,6 +46,7 @@ def test_deterministic_and_pinned():
         p1, p2 = S.generate(name), S.generate(name)
         assert p1.digest() == p2.digest()
         assert p1.structure_digest() == g[name]["structure_sha256"]
+        assert p1.digest() == g[name]["sha256"]   # every value byte
         assert p1.dim == g[name]["dim"] and p1.op_data.size == g[name]["op_len"]
     assert S.generate("tiny", seed=1).digest() != S.generate("tiny", seed=0).digest()
 
