@@ -615,6 +615,16 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
             if (it + step < total) G1 = a.gemms[W1.gemm];
             if (it + 2 * step < total) W2 = a.work[it + 2 * step];
             const int fs = G.fshift;
+            const int r = W.mtile * SPL_TM + row;
+            const int cbase = W.ntile * SPL_TN + col0;
+            // stage 1: the exponents its epilogue needs, loaded before the drain (both
+            // arrays are read-only while stage 1 runs): column cbase + lane, this row
+            const bool rv = r < G.M;
+            int cex_l = 0, erow = 0;
+            if (G.kind == 0) {
+                if (cbase + lane < G.N) cex_l = a.ap_ex[G.ec_off + cbase + lane];
+                if (rv) erow = a.op_ex[G.er_off + r];
+            }
             long long acc[UM_EPI_COLS];   // slice sums of the item in units of 2^-31
 #pragma unroll
             for (int j = 0; j < UM_EPI_COLS; ++j) acc[j] = 0;
@@ -659,20 +669,16 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
             // part below 2^-fs, i.e. of i4, is rounded
 #pragma unroll
             for (int j = 0; j < UM_EPI_COLS; ++j)
-                acc[j] = fs >= 31 ? acc[j] * (1ll << (fs - 31)) : (acc[j] + (1ll << (30 - fs))) >> (31 - fs);
-            const int r = W.mtile * SPL_TM + row;
-            const int cbase = W.ntile * SPL_TN + col0;
+                acc[j] = fs >= 31 ? static_cast<long long>(static_cast<unsigned long long>(acc[j]) << (fs - 31))
+                                  : (acc[j] + (1ll << (30 - fs))) >> (31 - fs);
             if (G.kind == 0) {
                 // exponents of the stage-2 vectors fed by this row: the column exponents
                 // come with one load per warp (lane l holds column cbase + l) and a
                 // broadcast per column, so no global load sits between the atomics
-                const bool rv = r < G.M;
                 const int rs = rv ? r : 0;
-                const int cl = cbase + lane;
-                const int cex_l = cl < G.N ? a.ap_ex[G.ec_off + cl] : 0;
                 // stage-2 vector of entry (r, c): (c / colgroup) * period + r % period
                 int32_t* x2 = a.ap_ex + G.x2_exp + rs % G.x2_period;
-                const int eoff = (rv ? a.op_ex[G.er_off + rs] : 0) - (14 + G.fshift);
+                const int eoff = erow - (14 + G.fshift);
                 int emax = INT_MIN, grp = cbase / G.x2_colgroup;
                 int next = (grp + 1) * G.x2_colgroup;   // first column of the next group
 #pragma unroll
