@@ -34,8 +34,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 NCU_TRAFFIC = {
     # k_fp64_tiles, mid workload: (280.8 + 358.1) / 2 MB per launch (profiles/fp64_tiles_mid.md)
     "7ea6b95187a63352e09b039a09918be5e89d2a14561ebf2f4d93d0eae118ec22": 319.5e6,
-    # k_umma, mid workload: (489.1 + 1369.5) / 2 MB per launch (profiles/split_umma_mid.md)
-    "a83b765028285a201b8e5c47d6045e7590cff99a854292959ef11bfe8c8b9548": 929.3e6,
+    # k_umma, mid workload: (470.6 + 541.3) / 2 MB per launch (profiles/split_umma_mid.md)
+    "884c5da3f3d9f49499165eb3536a5de9f6bc7b8df84efef25531f89f7e5c92fe": 505.9e6,
 }
 
 
