@@ -5,10 +5,12 @@
 //             canonical K-major layout, plus the vectors' exponents (integer ops only
 //             for int64 sources).  The nvec vectors of an apply are stacked inside
 //             every GEMM (along N in stage 1, along M or N in stage 2).
-//   k_umma    warp-specialised slice GEMM: one producer thread streams 72 KB stages
-//             with cp.async.bulk, one thread issues the 42 tcgen05.mma of each K tile
-//             into five TMEM accumulators, eight epilogue warps drain the
-//             exact FP32 sums into int64 every 256 K and store / atomically add.
+//   k_umma    warp-specialised slice GEMM: one producer thread streams up to 72 KB
+//             stages with cp.async.bulk (the row groups that hold GEMM rows), one
+//             thread issues the 42 tcgen05.mma of each K tile into five accumulators
+//             (8 TMEM slots: accumulators 2-4 alternate between two), eight epilogue
+//             warps drain the exact FP32 sums into int64 every 256 K and store /
+//             atomically add.
 //   k_finalize  stage-2 int64 sums -> FP64 wave-function blocks.
 // Every mbarrier wait is bounded; on timeout the CTA records DMRG_ERR_DEVICE_TIMEOUT in
 // the handle's status word, drains its own copies and MMAs and releases TMEM.
