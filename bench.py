@@ -208,7 +208,9 @@ def davidson_time_to_e(lib, p, args):
             # large workloads: the reference solve (same start vector) is the FP64 run
             ev, info = ref_ev, ref_info
         else:
-            h.davidson(torch.from_numpy(x0).cuda(), tol=1e-9, max_iter=5)      # warm-up
+            # warm-up: long enough to pass every basis size (the apply of each block of
+            # new vectors is captured once as a CUDA graph)
+            h.davidson(torch.from_numpy(x0).cuda(), tol=1e-9, max_iter=50)
             ev, info = h.davidson(torch.from_numpy(x0).cuda(), tol=1e-9, max_iter=800)
         th, tm = info["theta"], info["time"]
         hit = np.nonzero(np.abs(th - e_ref) <= 1e-10 * abs(e_ref))[0]

@@ -121,9 +121,12 @@ __global__ void k_precond(double* __restrict__ out, const double* __restrict__ r
     out[n] = r[n] / den;
 }
 
-__global__ void k_scale(double* __restrict__ dst, const double* __restrict__ src, double s, int64_t dim) {
+// dst = src / ||src|| with the squared norm read from device memory (zero stays zero)
+__global__ void k_normalise(double* __restrict__ dst, const double* __restrict__ src, const double* __restrict__ sq,
+                            int64_t dim) {
     const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (n < dim) dst[n] = s * src[n];
+    const double q = *sq;
+    if (n < dim) dst[n] = q > 0.0 ? src[n] / sqrt(q) : 0.0;
 }
 
 // S[i][m0+j] = S[m0+j][i] = (G1[i][j] + G2[i][j]) / 2 for i < m, j < nb (G ld = nb)
@@ -293,11 +296,6 @@ struct Run {
         k_chunk_reduce<<<blocks_for(np * nq), 256, 0, st>>>(s->partial, s->n_chunks, np * nq, out);
         return check(cudaGetLastError(), "dot kernels");
     }
-    int sqnorm(const double* v, double* host) {
-        int rc = dots(v, 1, v, 1, s->small);
-        if (rc) return rc;
-        return check(cudaMemcpy(host, s->small, sizeof(double), cudaMemcpyDeviceToHost), "read norm");
-    }
     int lincomb(const double* coef, int ldc, int col0, int nj, int m, const double* V, double* out, int sub) {
         for (int j0 = 0; j0 < nj; j0 += MAXQ) {
             const int n = nj - j0 < MAXQ ? nj - j0 : MAXQ;
@@ -306,14 +304,14 @@ struct Run {
         }
         return check(cudaGetLastError(), "lincomb");
     }
-    // CGS2 of v against V[0:m]; appends it as V[m] when kept.
+    // CGS2 of v against V[0:m]; appends it as V[m] when kept.  Both norms stay on the
+    // device (the normalisation reads the second); one read-back decides whether the
+    // vector is kept (norm after CGS2 >= 1e-10 of the norm before).
     int cgs2_append(double* v, int* m, bool* kept) {
         *kept = false;
-        double n0 = 0, n1 = 0;
-        int rc = sqnorm(v, &n0);
+        double* nrm = s->small;   // [0] = |v|^2 before, [1] = after
+        int rc = dots(v, 1, v, 1, nrm);
         if (rc) return rc;
-        n0 = std::sqrt(n0);
-        if (!(n0 > 0.0)) return DMRG_OK;
         for (int pass = 0; pass < 2; ++pass) {
             if (*m == 0) break;
             double* d = s->small + 64;
@@ -324,11 +322,13 @@ struct Run {
             k_lincomb<<<blocks_for(dim), 256, 0, st>>>(d, 1, 0, 1, *m, s->V, dim, dim, v, dim, 1);
             if ((rc = check(cudaGetLastError(), "cgs update"))) return rc;
         }
-        if ((rc = sqnorm(v, &n1))) return rc;
-        n1 = std::sqrt(n1);
-        if (n1 < 1e-10 * n0) return DMRG_OK;
-        k_scale<<<blocks_for(dim), 256, 0, st>>>(s->V + int64_t(*m) * dim, v, 1.0 / n1, dim);
+        if ((rc = dots(v, 1, v, 1, nrm + 1))) return rc;
+        k_normalise<<<blocks_for(dim), 256, 0, st>>>(s->V + int64_t(*m) * dim, v, nrm + 1, dim);
         if ((rc = check(cudaGetLastError(), "normalise"))) return rc;
+        double n2[2];
+        if ((rc = check(cudaMemcpy(n2, nrm, sizeof(n2), cudaMemcpyDeviceToHost), "read norms"))) return rc;
+        const double n0 = std::sqrt(n2[0]), n1 = std::sqrt(n2[1]);
+        if (!(n0 > 0.0) || n1 < 1e-10 * n0) return DMRG_OK;   // V[m] is left to be overwritten
         *m += 1;
         *kept = true;
         return DMRG_OK;
@@ -417,7 +417,7 @@ extern "C" int dmrg_davidson(dmrg_heff_t hh, int32_t k_eig, double tol, int32_t 
     int matvecs = m, restarts = 0;
     if ((rc = run.s_update(0, m))) return rc;
 
-    std::vector<double> th(mmax), rn(mmax);
+    std::vector<double> th(mmax), rn(mmax), rb(size_t(2 * MAX_BASIS));
     int it = 0, kb = 0;
     int m_prev = 0;   // rows of U that diagonalise S[0:m_prev, 0:m_prev] (warm start)
     bool converged = false;
@@ -432,11 +432,17 @@ extern "C" int dmrg_davidson(dmrg_heff_t hh, int32_t k_eig, double tol, int32_t 
         k_residual<<<blocks_for(dim), 256, 0, st>>>(s->R, s->X, s->theta, kb, dim);
         for (int j = 0; j < kb; ++j)
             if ((rc = run.dots(s->R + j * dim, 1, s->R + j * dim, 1, s->small + 2048 + j))) return rc;
-        if ((rc = run.check(cudaMemcpy(rn.data(), s->small + 2048, sizeof(double) * kb, cudaMemcpyDeviceToHost),
-                            "read residuals")))
+        // Ritz values next to the residual norms: one read-back per step
+        if ((rc = run.check(cudaMemcpyAsync(s->small + 2048 + MAX_BASIS, s->theta, sizeof(double) * m,
+                                            cudaMemcpyDeviceToDevice, st),
+                            "stage theta")))
             return rc;
-        if ((rc = run.check(cudaMemcpy(th.data(), s->theta, sizeof(double) * m, cudaMemcpyDeviceToHost), "read theta")))
+        if ((rc = run.check(cudaMemcpy(rb.data(), s->small + 2048, sizeof(double) * (MAX_BASIS + m),
+                                       cudaMemcpyDeviceToHost),
+                            "read residuals and theta")))
             return rc;
+        for (int j = 0; j < kb; ++j) rn[j] = rb[size_t(j)];
+        for (int j = 0; j < m; ++j) th[j] = rb[size_t(MAX_BASIS + j)];
         for (int j = 0; j < kb; ++j) rn[j] = std::sqrt(rn[j]);
         if (info && info->hist_theta && it <= info->hist_cap) info->hist_theta[it - 1] = th[0];
         if (info && info->hist_time && it <= info->hist_cap)
