@@ -10,6 +10,7 @@
 //   unconverged pairs, thick restart to k_eig + b Ritz vectors when the basis is full,
 //   CGS2 (two classical Gram-Schmidt passes, drop below 1e-10 of the input norm).
 #include <chrono>
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -18,7 +19,10 @@
 
 namespace dmrg {
 
-constexpr int DOT_CHUNK = 8192;  // elements of one dot-product partial
+// Dot products are cut into chunks of at least DOT_MIN_CHUNK elements, about two per SM
+// (FP64 arithmetic is scarce on this GPU, so every SM takes a share); partials are
+// summed in chunk order.
+constexpr int DOT_MIN_CHUNK = 1024;
 constexpr int DOT_NT = 256;
 constexpr int MAXQ = 8;          // Q vectors per multi-dot launch
 constexpr int MAX_BASIS = 64;    // m_max limit of the Jacobi kernel
@@ -26,7 +30,7 @@ constexpr int MAX_BASIS = 64;    // m_max limit of the Jacobi kernel
 struct DavidsonState {
     double *V = nullptr, *W = nullptr, *X = nullptr, *R = nullptr, *C = nullptr, *T = nullptr;
     double *diag = nullptr, *S = nullptr, *U = nullptr, *theta = nullptr, *small = nullptr, *partial = nullptr;
-    int64_t n_chunks = 0;
+    int64_t n_chunks = 0, chunk = 0;   // dot-product partials: count and length
     int mmax = 0, kbmax = 0, block = 0, k_eig = 0;   // sizes the buffers were allocated for
     bool diag_ready = false;
     ~DavidsonState() {
@@ -41,11 +45,11 @@ namespace {
 // partial[(c*np + i)*nq + j] = sum over chunk c of P_i . Q_j   (fixed-order tree)
 __global__ void __launch_bounds__(DOT_NT) k_multidot(const double* __restrict__ P, int64_t ldp, int np,
                                                      const double* __restrict__ Q, int64_t ldq, int nq,
-                                                     int64_t dim, double* __restrict__ partial) {
+                                                     int64_t dim, int64_t chunk, double* __restrict__ partial) {
     __shared__ double red[DOT_NT];
     const int c = blockIdx.x, i = blockIdx.y;
-    const int64_t n0 = int64_t(c) * DOT_CHUNK;
-    const int64_t n1 = min(dim, n0 + DOT_CHUNK);
+    const int64_t n0 = int64_t(c) * chunk;
+    const int64_t n1 = min(dim, n0 + chunk);
     double acc[MAXQ];
 #pragma unroll
     for (int j = 0; j < MAXQ; ++j) acc[j] = 0.0;
@@ -164,6 +168,7 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ S, in
     double* Z = sm + MAX_BASIS * ld;     // eigenvectors, M x ld
     __shared__ double cs[MAX_BASIS / 2], sn[MAX_BASIS / 2];
     __shared__ int pp[MAX_BASIS / 2], qq[MAX_BASIS / 2];
+    __shared__ int s_nr;   // rotations of the current round (compacted into pp, qq, cs, sn)
     __shared__ int order[MAX_BASIS];
     const int tid = threadIdx.x, nt = blockDim.x;
     // Z = B;  A = S B (into A), then A = B^T A
@@ -208,25 +213,35 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ S, in
         if (tid == 0) s_rot = 0;
         __syncthreads();
         for (int r = 0; r < M - 1; ++r) {
+            if (tid == 0) s_nr = 0;
+            __syncthreads();
             if (tid < half) {
                 const int k = tid;
                 const int a = k == 0 ? 0 : ((k - 1 + r) % (M - 1)) + 1;
                 const int b = ((M - 2 - k + r) % (M - 1)) + 1;
                 const int p = min(a, b), q = max(a, b);
                 const double apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
-                double c = 1.0, s = 0.0;
                 // rotate only while the off-diagonal entry is above rounding level
-                if (fabs(apq) > 1e-18 * sqrt(fabs(app * aqq)) + 1e-300) {
+                // (|apq| > 1e-18 sqrt|app aqq|, compared in squares)
+                if (apq * apq > 1e-36 * fabs(app * aqq) + 1e-300) {
                     const double tau = (aqq - app) / (2.0 * apq);
                     const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                    c = 1.0 / sqrt(1.0 + t * t);
-                    s = t * c;
+                    const double c = 1.0 / sqrt(1.0 + t * t);
+                    const int slot = atomicAdd(&s_nr, 1);
+                    pp[slot] = p; qq[slot] = q; cs[slot] = c; sn[slot] = t * c;
                     s_rot = 1;
                 }
-                pp[k] = p; qq[k] = q; cs[k] = c; sn[k] = s;
             }
             __syncthreads();
-            for (int e = tid; e < half * M; e += nt) {       // A <- A J
+            // the disjoint rotations of this round, in any order; every thread reads the
+            // same count (no write to s_nr before the next barrier), and that barrier -- the
+            // first of the update loops, or the one below -- comes before the next reset
+            const int nr = s_nr;
+            if (nr == 0) {
+                __syncthreads();
+                continue;
+            }
+            for (int e = tid; e < nr * M; e += nt) {       // A <- A J
                 const int k = e / M, row = e % M;
                 const int p = pp[k], q = qq[k];
                 const double c = cs[k], s = sn[k];
@@ -235,7 +250,7 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ S, in
                 A[row * ld + q] = s * x + c * y;
             }
             __syncthreads();
-            for (int e = tid; e < half * M; e += nt) {       // A <- J^T A, Z <- Z J
+            for (int e = tid; e < nr * M; e += nt) {       // A <- J^T A, Z <- Z J
                 const int k = e / M, col = e % M;
                 const int p = pp[k], q = qq[k];
                 const double c = cs[k], s = sn[k];
@@ -291,7 +306,7 @@ struct Run {
     // out[i*nq + j] = P_i . Q_j  (np <= MAX_BASIS, nq <= MAXQ); result in s->small
     int dots(const double* P, int np, const double* Q, int nq, double* out) {
         if (np == 0 || nq == 0) return DMRG_OK;
-        k_multidot<<<dim3(unsigned(s->n_chunks), unsigned(np)), DOT_NT, 0, st>>>(P, dim, np, Q, dim, nq, dim,
+        k_multidot<<<dim3(unsigned(s->n_chunks), unsigned(np)), DOT_NT, 0, st>>>(P, dim, np, Q, dim, nq, dim, s->chunk,
                                                                              s->partial);
         k_chunk_reduce<<<blocks_for(np * nq), 256, 0, st>>>(s->partial, s->n_chunks, np * nq, out);
         return check(cudaGetLastError(), "dot kernels");
@@ -381,7 +396,10 @@ extern "C" int dmrg_davidson(dmrg_heff_t hh, int32_t k_eig, double tol, int32_t 
     if (!h->dav) {
         h->dav = new DavidsonState();
         DavidsonState* s = h->dav;
-        s->n_chunks = (dim + DOT_CHUNK - 1) / DOT_CHUNK;
+        const int64_t want = 2 * int64_t(h->n_sm);
+        s->chunk = std::max<int64_t>(DOT_MIN_CHUNK, (dim + want - 1) / want);
+        s->chunk = (s->chunk + DOT_NT - 1) / DOT_NT * DOT_NT;
+        s->n_chunks = (dim + s->chunk - 1) / s->chunk;
         s->mmax = mmax; s->kbmax = kbmax; s->block = block; s->k_eig = k_eig;
         auto al = [&](double** p, int64_t n, const char* w) {
             cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(double) * (n > 0 ? n : 1));
