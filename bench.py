@@ -221,6 +221,20 @@ def davidson_time_to_e(lib, p, args):
         h.close()
     if out["split"]["time_to_E_s"] and out["fp64"]["time_to_E_s"]:
         out["fp64_over_split"] = round(out["fp64"]["time_to_E_s"] / out["split"]["time_to_E_s"], 3)
+    # the same criterion for restarted Lanczos (small workloads only)
+    if args.config in ("tiny", "mid"):
+        lz = {}
+        for prec in ("split", "fp64"):
+            h = lib.HEff.from_problem(p, precision="split_bf16" if prec == "split" else "fp64")
+            h.lanczos(torch.from_numpy(x0[0]).cuda(), tol=1e-9, max_iter=200)    # warm-up
+            ev, info = h.lanczos(torch.from_numpy(x0[0]).cuda(), tol=1e-9, max_iter=3000)
+            hit = np.nonzero(np.abs(info["theta"] - e_ref) <= 1e-10 * abs(e_ref))[0]
+            lz[prec] = {"time_to_E_s": round(float(info["time"][hit[0]]), 5) if hit.size else None,
+                        "iters_to_E": int(hit[0]) + 1 if hit.size else None, "E": ev,
+                        "rel_err_E": abs(ev - e_ref) / abs(e_ref), "iters": info["iters"],
+                        "converged": info["converged"], "seconds": round(info["seconds"], 5)}
+            h.close()
+        out["lanczos"] = lz
     return out
 
 

@@ -150,6 +150,22 @@ int dmrg_heff_diagonal(dmrg_heff_t h, double* diag, void* stream);
 int dmrg_davidson(dmrg_heff_t h, int32_t k_eig, double tol, int32_t max_iter, int32_t block,
                   int32_t n_iter, double* x_inout, double* evals, dmrg_davidson_info* info);
 
+/* Lowest eigenpair by restarted Lanczos (paper: Numerical procedure, the Lanczos
+ * alternative to Davidson named after Eq. 2): per step one H_eff product, the
+ * three-term recurrence, full FP64 reorthogonalisation against the basis (two
+ * Gram-Schmidt passes) and Rayleigh-Ritz on the tridiagonal matrix by cyclic Jacobi
+ * on the device; explicit restart from the Ritz vector when the basis holds m_max
+ * vectors.  Converged when the residual estimate beta_j |s_j| <= tol, or when the
+ * Krylov space becomes invariant.
+ *   max_iter : steps allowed (each one product);  m_max : 2 .. 63
+ *   x_inout  : device, dim doubles: the start vector (any norm); on return the unit
+ *              Ritz vector
+ *   eval     : host, 1 double; info: host, may be NULL (resid_max is the explicit
+ *              residual ||H x - theta x|| of the returned vector).
+ * Returns DMRG_ERR_NOT_CONVERGED (results still written) when tol was not met. */
+int dmrg_lanczos(dmrg_heff_t h, double tol, int32_t max_iter, int32_t m_max, double* x_inout, double* eval,
+                 dmrg_davidson_info* info);
+
 /* Size of the fixed device array used by dmrg_heff_apply_noalloc (32 MiB per GPU). */
 #define DMRG_NOALLOC_SCRATCH_BYTES (32 * 1024 * 1024)
 

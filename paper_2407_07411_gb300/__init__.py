@@ -32,7 +32,7 @@ SYMBOLS = ("dmrg_heff_create", "dmrg_heff_dim", "dmrg_heff_flops", "dmrg_heff_pl
            "dmrg_heff_destroy", "dmrg_strerror", "dmrg_last_error", "dmrg_heff_profile",
            "dmrg_heff_profile_read", "dmrg_probe_fp64_peak", "dmrg_heff_apply_noalloc",
            "dmrg_selftest_wait_timeout", "dmrg_heff_schedule_get", "dmrg_heff_schedule_set",
-           "dmrg_heff_autotune", "dmrg_heff_gemm_count")
+           "dmrg_heff_autotune", "dmrg_heff_gemm_count", "dmrg_lanczos")
 
 
 class Opts(ctypes.Structure):
@@ -95,6 +95,7 @@ _lib.dmrg_heff_schedule_get.argtypes = [_P, ctypes.POINTER(Schedule)]
 _lib.dmrg_heff_schedule_set.argtypes = [_P, ctypes.POINTER(Schedule)]
 _lib.dmrg_heff_autotune.argtypes = [_P, _i32, _i32, ctypes.POINTER(TuneReport)]
 _lib.dmrg_heff_gemm_count.argtypes = [_P, _i32, _P]
+_lib.dmrg_lanczos.argtypes = [_P, _f64, _i32, _i32, _P, _P, ctypes.POINTER(DavidsonInfo)]
 _lib.dmrg_heff_destroy.argtypes = [_P]
 _lib.dmrg_heff_destroy.restype = None
 _lib.dmrg_strerror.argtypes = [ctypes.c_int]
@@ -299,6 +300,26 @@ class HEff:
         return ev[:k_eig], dict(iters=n, matvecs=info.matvecs, converged=bool(info.converged),
                                 restarts=info.restarts, resid_max=info.resid_max, seconds=info.seconds,
                                 theta=th[:n].copy(), time=tm[:n].copy())
+
+    def lanczos(self, x0, tol: float = 1e-8, max_iter: int = 300, m_max: int = 63):
+        """Lowest eigenpair by restarted Lanczos.  x0: CUDA float64 tensor of dim values
+        (the start vector), overwritten with the unit Ritz vector.
+        Returns (eval, info dict) as davidson does; info['resid_max'] is the explicit
+        residual of the returned vector."""
+        ev = np.zeros(1, np.float64)
+        cap = max(max_iter, 1)
+        th = np.full(cap, np.nan)
+        tm = np.full(cap, np.nan)
+        info = DavidsonInfo()
+        info.hist_theta, info.hist_time, info.hist_cap = th.ctypes.data, tm.ctypes.data, cap
+        rc = _lib.dmrg_lanczos(self._h, tol, max_iter, m_max, _dev_ptr(x0, self.dim, "x0"), _ptr(ev),
+                               ctypes.byref(info))
+        if rc not in (0, ERR_NOT_CONVERGED):
+            raise DmrgError(rc)
+        n = info.iters
+        return float(ev[0]), dict(iters=n, matvecs=info.matvecs, converged=bool(info.converged),
+                                  restarts=info.restarts, resid_max=info.resid_max, seconds=info.seconds,
+                                  theta=th[:n].copy(), time=tm[:n].copy())
 
 
 def probe_fp64_peak() -> float:

@@ -133,6 +133,34 @@ __global__ void k_normalise(double* __restrict__ dst, const double* __restrict__
     if (n < dim) dst[n] = q > 0.0 ? src[n] / sqrt(q) : 0.0;
 }
 
+// Lanczos three-term step: w -= alpha_j q_j + beta_{j-1} q_{j-1} (beta from its square;
+// q_prev null for j = 0)
+__global__ void k_lanczos_step(double* __restrict__ w, const double* __restrict__ q, const double* __restrict__ q_prev,
+                               const double* __restrict__ alpha_j, const double* __restrict__ beta2_prev, int64_t dim) {
+    const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (n >= dim) return;
+    double v = w[n] - *alpha_j * q[n];
+    if (q_prev) v -= sqrt(*beta2_prev) * q_prev[n];
+    w[n] = v;
+}
+
+// T (n x n, row stride lds): diagonal alpha, off-diagonal sqrt(beta2)
+__global__ void k_tridiag(double* __restrict__ T, int lds, const double* __restrict__ alpha,
+                          const double* __restrict__ beta2, int n) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * n) return;
+    const int i = e / n, k = e % n;
+    T[i * lds + k] = i == k ? alpha[i] : (i == k + 1 || k == i + 1 ? sqrt(beta2[i < k ? i : k]) : 0.0);
+}
+
+// out = (theta[0], U[last][0], beta2[j]) for the one read-back of a Lanczos step
+__global__ void k_lanczos_probe(double* __restrict__ out, const double* __restrict__ theta, const double* __restrict__ U,
+                                int ldu, int last, const double* __restrict__ beta2_j) {
+    out[0] = theta[0];
+    out[1] = U[last * ldu];
+    out[2] = *beta2_j;
+}
+
 // S[i][m0+j] = S[m0+j][i] = (G1[i][j] + G2[i][j]) / 2 for i < m, j < nb (G ld = nb)
 __global__ void k_sym_update(double* __restrict__ S, int lds, const double* __restrict__ G1,
                              const double* __restrict__ G2, int m, int m0, int nb) {
@@ -368,6 +396,45 @@ struct Run {
 }  // namespace
 }  // namespace dmrg
 
+namespace dmrg {
+namespace {
+
+// The solver buffers of a handle, kept between calls of the same shape.
+int ensure_state(Handle* h, int mmax, int kbmax, int block, int k_eig) {
+    if (h->dav && (h->dav->mmax != mmax || h->dav->kbmax != kbmax || h->dav->block != block ||
+                   h->dav->k_eig != k_eig))
+        h->release_davidson();
+    if (h->dav) return DMRG_OK;
+    const int64_t dim = h->plan.dim;
+    h->dav = new DavidsonState();
+    DavidsonState* s = h->dav;
+    const int64_t want = 2 * int64_t(h->n_sm);
+    s->chunk = std::max<int64_t>(DOT_MIN_CHUNK, (dim + want - 1) / want);
+    s->chunk = (s->chunk + DOT_NT - 1) / DOT_NT * DOT_NT;
+    s->n_chunks = (dim + s->chunk - 1) / s->chunk;
+    s->mmax = mmax; s->kbmax = kbmax; s->block = block; s->k_eig = k_eig;
+    auto al = [&](double** p, int64_t n, const char* w) {
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(double) * (n > 0 ? n : 1));
+        return e == cudaSuccess ? DMRG_OK : cuda_fail(e, w);
+    };
+    int rc;
+    if ((rc = al(&s->V, int64_t(mmax) * dim, "V")) || (rc = al(&s->W, int64_t(mmax) * dim, "W")) ||
+        (rc = al(&s->X, int64_t(kbmax) * dim, "X")) || (rc = al(&s->R, int64_t(kbmax) * dim, "R")) ||
+        (rc = al(&s->C, int64_t(block) * dim, "C")) || (rc = al(&s->T, int64_t(k_eig + block) * dim, "T")) ||
+        (rc = al(&s->diag, dim, "diag")) || (rc = al(&s->S, mmax * mmax, "S")) ||
+        (rc = al(&s->U, mmax * mmax, "U")) || (rc = al(&s->theta, mmax, "theta")) ||
+        (rc = al(&s->small, 4096, "small")) || (rc = al(&s->partial, s->n_chunks * MAX_BASIS * MAXQ, "partials"))) {
+        h->release_davidson();
+        return rc;
+    }
+    cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(sizeof(double) * 2 * MAX_BASIS * (MAX_BASIS + 1)));
+    return DMRG_OK;
+}
+
+}  // namespace
+}  // namespace dmrg
+
 using dmrg::Handle;
 
 extern "C" int dmrg_davidson(dmrg_heff_t hh, int32_t k_eig, double tol, int32_t max_iter, int32_t block,
@@ -387,35 +454,10 @@ extern "C" int dmrg_davidson(dmrg_heff_t hh, int32_t k_eig, double tol, int32_t 
     if (!x_inout || !evals) return fail(DMRG_ERR_INVALID_ARG, "null x_inout or evals");
 
     const int kbmax = k_eig > block ? k_eig : block;
-    if (h->dav && (h->dav->mmax != mmax || h->dav->kbmax != kbmax || h->dav->block != block ||
-                   h->dav->k_eig != k_eig))
-        h->release_davidson();   // buffers are kept between calls of the same shape
     int rc;
+    if ((rc = ensure_state(h, mmax, kbmax, block, k_eig))) return rc;
     const size_t jac_smem = sizeof(double) * 2 * MAX_BASIS * (MAX_BASIS + 1);
     cudaStream_t st = nullptr;
-    if (!h->dav) {
-        h->dav = new DavidsonState();
-        DavidsonState* s = h->dav;
-        const int64_t want = 2 * int64_t(h->n_sm);
-        s->chunk = std::max<int64_t>(DOT_MIN_CHUNK, (dim + want - 1) / want);
-        s->chunk = (s->chunk + DOT_NT - 1) / DOT_NT * DOT_NT;
-        s->n_chunks = (dim + s->chunk - 1) / s->chunk;
-        s->mmax = mmax; s->kbmax = kbmax; s->block = block; s->k_eig = k_eig;
-        auto al = [&](double** p, int64_t n, const char* w) {
-            cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(double) * (n > 0 ? n : 1));
-            return e == cudaSuccess ? DMRG_OK : cuda_fail(e, w);
-        };
-        if ((rc = al(&s->V, int64_t(mmax) * dim, "V")) || (rc = al(&s->W, int64_t(mmax) * dim, "W")) ||
-            (rc = al(&s->X, int64_t(kbmax) * dim, "X")) || (rc = al(&s->R, int64_t(kbmax) * dim, "R")) ||
-            (rc = al(&s->C, int64_t(block) * dim, "C")) || (rc = al(&s->T, int64_t(k_eig + block) * dim, "T")) ||
-            (rc = al(&s->diag, dim, "diag")) || (rc = al(&s->S, mmax * mmax, "S")) ||
-            (rc = al(&s->U, mmax * mmax, "U")) || (rc = al(&s->theta, mmax, "theta")) ||
-            (rc = al(&s->small, 4096, "small")) || (rc = al(&s->partial, s->n_chunks * MAX_BASIS * MAXQ, "partials"))) {
-            h->release_davidson();
-            return rc;
-        }
-        cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, int(jac_smem));
-    }
     DavidsonState* s = h->dav;
     Run run{h, s, dim, mmax};
     if (!s->diag_ready) {
@@ -518,4 +560,107 @@ extern "C" int dmrg_davidson(dmrg_heff_t hh, int32_t k_eig, double tol, int32_t 
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     }
     return converged || n_iter > 0 ? DMRG_OK : DMRG_ERR_NOT_CONVERGED;
+}
+
+// Lowest eigenpair by restarted Lanczos with full reorthogonalisation (the steps are
+// listed with the oracle's variant): per step one apply, alpha_j, the three-term step,
+// two Gram-Schmidt passes against the basis, beta_j, and Rayleigh-Ritz on the growing
+// tridiagonal T with the warm-started Jacobi kernel; one read-back per step.
+extern "C" int dmrg_lanczos(dmrg_heff_t hh, double tol, int32_t max_iter, int32_t m_max, double* x_inout,
+                            double* eval, dmrg_davidson_info* info) {
+    using namespace dmrg;
+    const auto t_start = std::chrono::steady_clock::now();
+    if (!hh) return fail(DMRG_ERR_INVALID_ARG, "null handle");
+    Handle* h = static_cast<Handle*>(hh);
+    if (h->plan_only) return fail(DMRG_ERR_INVALID_ARG, "plan-only handle");
+    const int64_t dim = h->plan.dim;
+    if (max_iter < 1 || m_max < 2 || m_max > MAX_BASIS - 1 || !(tol >= 0.0))
+        return fail(DMRG_ERR_INVALID_ARG, "max_iter >= 1, 2 <= m_max <= 63, tol >= 0");
+    if (dim < 2) return fail(DMRG_ERR_INVALID_ARG, "problem smaller than 2");
+    if (!x_inout || !eval) return fail(DMRG_ERR_INVALID_ARG, "null x_inout or eval");
+    const int mmax = m_max + 1;   // the basis holds q_0 .. q_{m_max}
+    int rc;
+    if ((rc = ensure_state(h, mmax, 1, 1, 1))) return rc;
+    DavidsonState* s = h->dav;
+    cudaStream_t st = nullptr;
+    Run run{h, s, dim, mmax};
+    double* alpha = s->small + 3000;   // alpha_j (device)
+    double* beta2 = s->small + 3100;   // beta_j^2 (device)
+    double* probe = s->small + 3200;
+    const size_t jac_smem = sizeof(double) * 2 * MAX_BASIS * (MAX_BASIS + 1);
+    // q_0 = x0 / ||x0||
+    if ((rc = run.check(cudaMemcpy(s->R, x_inout, sizeof(double) * dim, cudaMemcpyDeviceToDevice), "x0"))) return rc;
+    int m = 0;
+    bool kept = false;
+    if ((rc = run.cgs2_append(s->R, &m, &kept))) return rc;
+    if (!kept) return fail(DMRG_ERR_INVALID_ARG, "start vector is numerically zero");
+    int it = 0, matvecs = 0, restarts = 0, m_prev = 0, n = 0;
+    double theta = 0.0;
+    bool converged = false, restart = false;
+    while (it < max_iter) {
+        if (restart) {   // T has m_max rows: restart from the Ritz vector y = sum_i s_i q_i
+            if ((rc = run.lincomb(s->U, mmax, 0, 1, n, s->V, s->C, 0))) return rc;
+            m = 0;
+            if ((rc = run.cgs2_append(s->C, &m, &kept))) return rc;
+            if (!kept) return fail(DMRG_ERR_INVALID_ARG, "Ritz vector is numerically zero");
+            m_prev = 0;
+            ++restarts;
+            restart = false;
+        }
+        ++it;
+        const int j = m - 1;   // the newest basis vector q_j
+        const double* qj = s->V + int64_t(j) * dim;
+        if ((rc = h->apply(qj, s->R, 1, st))) return rc;
+        ++matvecs;
+        if ((rc = run.dots(qj, 1, s->R, 1, alpha + j))) return rc;
+        k_lanczos_step<<<blocks_for(dim), 256, 0, st>>>(s->R, qj, j > 0 ? qj - dim : nullptr, alpha + j,
+                                                        beta2 + (j > 0 ? j - 1 : 0), dim);
+        if ((rc = run.check(cudaGetLastError(), "lanczos step"))) return rc;
+        // full reorthogonalisation; q_{j+1} appended when w did not vanish
+        if ((rc = run.cgs2_append(s->R, &m, &kept))) return rc;
+        if ((rc = run.check(cudaMemcpyAsync(beta2 + j, s->small + 1, sizeof(double), cudaMemcpyDeviceToDevice, st),
+                            "beta")))
+            return rc;
+        n = j + 1;   // T_j is n x n
+        k_tridiag<<<blocks_for(n * n), 256, 0, st>>>(s->S, mmax, alpha, beta2, n);
+        k_jacobi<<<1, 256, jac_smem, st>>>(s->S, n, mmax, s->theta, s->U, mmax, m_prev < n ? m_prev : 0);
+        m_prev = n;
+        k_lanczos_probe<<<1, 1, 0, st>>>(probe, s->theta, s->U, mmax, n - 1, beta2 + j);
+        if ((rc = run.check(cudaGetLastError(), "lanczos ritz"))) return rc;
+        double pr[3];
+        if ((rc = run.check(cudaMemcpy(pr, probe, sizeof(pr), cudaMemcpyDeviceToHost), "read ritz"))) return rc;
+        theta = pr[0];
+        if (info && info->hist_theta && it <= info->hist_cap) info->hist_theta[it - 1] = theta;
+        if (info && info->hist_time && it <= info->hist_cap)
+            info->hist_time[it - 1] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+        if (std::sqrt(pr[2]) * std::fabs(pr[1]) <= tol || !kept) {   // converged, or invariant Krylov space
+            converged = true;
+            break;
+        }
+        restart = n == m_max;
+    }
+    // Ritz vector of the last T (n x n), normalised, and its explicit residual
+    if ((rc = run.lincomb(s->U, mmax, 0, 1, n, s->V, s->C, 0))) return rc;
+    int m1 = 0;
+    if ((rc = run.cgs2_append(s->C, &m1, &kept))) return rc;   // V[0] = y / ||y||
+    if (!kept) return fail(DMRG_ERR_INVALID_ARG, "Ritz vector is numerically zero");
+    if ((rc = h->apply(s->V, s->R, 1, st))) return rc;
+    ++matvecs;
+    if ((rc = run.check(cudaMemcpy(x_inout, s->V, sizeof(double) * dim, cudaMemcpyDeviceToDevice), "x out"))) return rc;
+    k_lanczos_step<<<blocks_for(dim), 256, 0, st>>>(s->R, s->V, nullptr, s->theta, nullptr, dim);   // H y - theta y
+    double r2 = 0.0;
+    if ((rc = run.dots(s->R, 1, s->R, 1, s->small + 3300))) return rc;
+    if ((rc = run.check(cudaMemcpy(&r2, s->small + 3300, sizeof(double), cudaMemcpyDeviceToHost), "residual"))) return rc;
+    if ((rc = run.check(cudaDeviceSynchronize(), "lanczos"))) return rc;
+    if ((rc = h->check_status())) return rc;
+    *eval = theta;
+    if (info) {
+        info->iters = it;
+        info->matvecs = matvecs;
+        info->converged = converged ? 1 : 0;
+        info->restarts = restarts;
+        info->resid_max = std::sqrt(r2);
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    }
+    return converged ? DMRG_OK : DMRG_ERR_NOT_CONVERGED;
 }
