@@ -251,6 +251,25 @@ int dmrg_heff_autotune(dmrg_heff_t h, int32_t nvec, int32_t reps, dmrg_tune_repo
  * per_gemm set, an apply launches counts[0] + counts[1] GEMM kernels. */
 int dmrg_heff_gemm_count(dmrg_heff_t h, int32_t nvec, int64_t counts[2]);
 
+/*
+ * Operator renormalisation (paper: the renormalisation of the block operators in the
+ * new, truncated basis that follows each local update, Numerical procedure):
+ *     O'[p <- q] = U_p^T O[p <- q] U_q   for every listed block,
+ * with per-sector bases U_q (d_q x d'_q, normally orthonormal columns).  No handle.
+ *   nsec, dims, dims_new : sector count, old dims d_q, new dims d'_q (1 <= d'_q <= d_q)
+ *   U        : device, the bases row-major one after another in sector order
+ *              (sum_q d_q d'_q doubles)
+ *   blocks   : host, n_blocks rows (q, p, offset): input sector, output sector and the
+ *              offset of the row-major d_p x d_q block in op
+ *   op       : device, op_len doubles;  out: device, out_len doubles >= sum d'_p d'_q
+ *   out_off  : host, n_blocks offsets of the d'_p x d'_q results in out (block order)
+ * Runs on `stream` and returns when the results are written (it allocates and frees
+ * its scratch).  DMRG_ERR_INVALID_ARG for out-of-range sectors, dims or offsets,
+ * checked on the host before any device work. */
+int dmrg_renormalise(int32_t nsec, const int32_t* dims, const int32_t* dims_new, const double* U,
+                     const int64_t* blocks, int64_t n_blocks, const double* op, int64_t op_len, double* out,
+                     int64_t out_len, int64_t* out_off, void* stream);
+
 /* Release the handle and its device memory (NULL is ignored). */
 void dmrg_heff_destroy(dmrg_heff_t h);
 

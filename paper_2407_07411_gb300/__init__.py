@@ -32,7 +32,7 @@ SYMBOLS = ("dmrg_heff_create", "dmrg_heff_dim", "dmrg_heff_flops", "dmrg_heff_pl
            "dmrg_heff_destroy", "dmrg_strerror", "dmrg_last_error", "dmrg_heff_profile",
            "dmrg_heff_profile_read", "dmrg_probe_fp64_peak", "dmrg_heff_apply_noalloc",
            "dmrg_selftest_wait_timeout", "dmrg_heff_schedule_get", "dmrg_heff_schedule_set",
-           "dmrg_heff_autotune", "dmrg_heff_gemm_count", "dmrg_lanczos")
+           "dmrg_heff_autotune", "dmrg_heff_gemm_count", "dmrg_lanczos", "dmrg_renormalise")
 
 
 class Opts(ctypes.Structure):
@@ -96,6 +96,7 @@ _lib.dmrg_heff_schedule_set.argtypes = [_P, ctypes.POINTER(Schedule)]
 _lib.dmrg_heff_autotune.argtypes = [_P, _i32, _i32, ctypes.POINTER(TuneReport)]
 _lib.dmrg_heff_gemm_count.argtypes = [_P, _i32, _P]
 _lib.dmrg_lanczos.argtypes = [_P, _f64, _i32, _i32, _P, _P, ctypes.POINTER(DavidsonInfo)]
+_lib.dmrg_renormalise.argtypes = [_i32, _P, _P, _P, _P, _i64, _P, _i64, _P, _i64, _P, _P]
 _lib.dmrg_heff_destroy.argtypes = [_P]
 _lib.dmrg_heff_destroy.restype = None
 _lib.dmrg_strerror.argtypes = [ctypes.c_int]
@@ -320,6 +321,21 @@ class HEff:
         return float(ev[0]), dict(iters=n, matvecs=info.matvecs, converged=bool(info.converged),
                                   restarts=info.restarts, resid_max=info.resid_max, seconds=info.seconds,
                                   theta=th[:n].copy(), time=tm[:n].copy())
+
+
+def renormalise(dims, dims_new, U, blocks, op, out, stream=None) -> np.ndarray:
+    """O'[p<-q] = U_p^T O[p<-q] U_q for each row (q, p, offset) of blocks.  dims and
+    dims_new: per-sector old and new dims; U, op, out: contiguous CUDA float64 tensors;
+    returns the offsets of the results in out."""
+    dims = np.ascontiguousarray(dims, np.int32)
+    dims_new = np.ascontiguousarray(dims_new, np.int32)
+    blocks = np.ascontiguousarray(np.asarray(blocks, np.int64).reshape(-1, 3))
+    out_off = np.zeros(max(len(blocks), 1), np.int64)
+    nu = int((dims.astype(np.int64) * dims_new).sum())
+    _check(_lib.dmrg_renormalise(len(dims), _ptr(dims), _ptr(dims_new), _dev_ptr(U, nu, "U"), _ptr(blocks),
+                                 len(blocks), _dev_ptr(op, 0, "op"), int(op.numel()), _dev_ptr(out, 0, "out"),
+                                 int(out.numel()), _ptr(out_off), _stream_ptr(stream)))
+    return out_off[:len(blocks)]
 
 
 def probe_fp64_peak() -> float:
