@@ -270,6 +270,31 @@ int dmrg_renormalise(int32_t nsec, const int32_t* dims, const int32_t* dims_new,
                      const int64_t* blocks, int64_t n_blocks, const double* op, int64_t op_len, double* out,
                      int64_t out_len, int64_t* out_off, void* stream);
 
+/* Layout of the wave function: n_blocks rows (left sector, right sector, rows, cols,
+ * offset) in storage order; with buf NULL only *n_blocks is set, otherwise buf holds
+ * *n_blocks * 5 values. */
+int dmrg_heff_psi_blocks(dmrg_heff_t h, int64_t* buf, int64_t* n_blocks);
+
+/*
+ * Two-site decomposition and truncation (paper: the matrix factorisation of the two-site
+ * wave function after each local update, Numerical procedure): per wave-function block
+ * psi_b (rows = dim of its left sector, cols = dim of its right sector) the singular
+ * values and left singular vectors (one-sided Jacobi in FP64 on the device, one CTA
+ * per block, blocks up to 8192 columns), then the D largest singular values over all
+ * blocks are kept (values below 1e-13 of the largest are zero and never kept; ties go
+ * to the earlier block, then position).
+ *   psi       : device, dim doubles
+ *   sv        : host, sum_b min(rows_b, cols_b) doubles: each block's singular values,
+ *               descending, in block order
+ *   kept      : host, n_blocks: kept values per block (a prefix of its sv)
+ *   U, u_len  : device: the kept left vectors of block b, row-major rows_b x kept_b at
+ *               u_off[b] (host, n_blocks); u_len must hold sum rows_b kept_b (U may be
+ *               NULL when nothing is kept)
+ *   discarded : host: the sum of the squares of the singular values not kept.
+ * Synchronises the device; allocates and frees its scratch. */
+int dmrg_svd_truncate(dmrg_heff_t h, const double* psi, int32_t D, double* sv, int32_t* kept, double* U, int64_t u_len,
+                      int64_t* u_off, double* discarded);
+
 /* Release the handle and its device memory (NULL is ignored). */
 void dmrg_heff_destroy(dmrg_heff_t h);
 

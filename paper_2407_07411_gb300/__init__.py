@@ -32,7 +32,8 @@ SYMBOLS = ("dmrg_heff_create", "dmrg_heff_dim", "dmrg_heff_flops", "dmrg_heff_pl
            "dmrg_heff_destroy", "dmrg_strerror", "dmrg_last_error", "dmrg_heff_profile",
            "dmrg_heff_profile_read", "dmrg_probe_fp64_peak", "dmrg_heff_apply_noalloc",
            "dmrg_selftest_wait_timeout", "dmrg_heff_schedule_get", "dmrg_heff_schedule_set",
-           "dmrg_heff_autotune", "dmrg_heff_gemm_count", "dmrg_lanczos", "dmrg_renormalise")
+           "dmrg_heff_autotune", "dmrg_heff_gemm_count", "dmrg_lanczos", "dmrg_renormalise",
+           "dmrg_heff_psi_blocks", "dmrg_svd_truncate")
 
 
 class Opts(ctypes.Structure):
@@ -97,6 +98,8 @@ _lib.dmrg_heff_autotune.argtypes = [_P, _i32, _i32, ctypes.POINTER(TuneReport)]
 _lib.dmrg_heff_gemm_count.argtypes = [_P, _i32, _P]
 _lib.dmrg_lanczos.argtypes = [_P, _f64, _i32, _i32, _P, _P, ctypes.POINTER(DavidsonInfo)]
 _lib.dmrg_renormalise.argtypes = [_i32, _P, _P, _P, _P, _i64, _P, _i64, _P, _i64, _P, _P]
+_lib.dmrg_heff_psi_blocks.argtypes = [_P, _P, ctypes.POINTER(_i64)]
+_lib.dmrg_svd_truncate.argtypes = [_P, _P, _i32, _P, _P, _P, _i64, _P, ctypes.POINTER(_f64)]
 _lib.dmrg_heff_destroy.argtypes = [_P]
 _lib.dmrg_heff_destroy.restype = None
 _lib.dmrg_strerror.argtypes = [ctypes.c_int]
@@ -255,6 +258,34 @@ class HEff:
         _check(_lib.dmrg_heff_autotune(self._h, nvec, reps, ctypes.byref(r)))
         return dict(trials=r.trials, nvec=r.nvec, default_ms=r.default_ms, best_ms=r.best_ms,
                     best=r.best.to_dict())
+
+    def psi_blocks(self) -> np.ndarray:
+        """Wave-function layout: rows (left sector, right sector, rows, cols, offset)."""
+        n = _i64(0)
+        _check(_lib.dmrg_heff_psi_blocks(self._h, None, ctypes.byref(n)))
+        buf = np.zeros((max(n.value, 1), 5), np.int64)
+        _check(_lib.dmrg_heff_psi_blocks(self._h, _ptr(buf), ctypes.byref(n)))
+        return buf[:n.value]
+
+    def svd_truncate(self, psi, D: int) -> dict:
+        """Per-block SVD of the device wave function psi and truncation to the D largest
+        singular values; returns dict(sv=[per block], kept, U=device tensor of the kept
+        left vectors, u_off, discarded)."""
+        import torch
+        blk = self.psi_blocks()
+        rows, cols = blk[:, 2], blk[:, 3]
+        nsv = int(np.minimum(rows, cols).sum())
+        sv = np.zeros(max(nsv, 1), np.float64)
+        kept = np.zeros(max(len(blk), 1), np.int32)
+        u_off = np.zeros(max(len(blk), 1), np.int64)
+        disc = _f64(0.0)
+        cap = int((rows * np.minimum(np.minimum(rows, cols), D)).sum())
+        U = torch.empty(max(cap, 1), dtype=torch.float64, device="cuda")
+        _check(_lib.dmrg_svd_truncate(self._h, _dev_ptr(psi, self.dim, "psi"), D, _ptr(sv), _ptr(kept),
+                                      ctypes.c_void_p(U.data_ptr()), int(U.numel()), _ptr(u_off), ctypes.byref(disc)))
+        k = np.minimum(rows, cols)
+        parts = np.split(sv[:nsv], np.cumsum(k)[:-1]) if len(blk) else []
+        return dict(sv=parts, kept=kept[:len(blk)], U=U, u_off=u_off[:len(blk)], discarded=disc.value)
 
     def gemm_count(self, nvec: int = 1) -> tuple:
         """(stage-1, stage-2) grouped GEMMs of the plan for nvec vectors."""

@@ -1,0 +1,247 @@
+// Two-site decomposition and truncation: per wave-function block psi_b (rows = dim of
+// the left sector, cols = dim of the right sector) the singular values and left vectors
+// by one-sided (Hestenes) Jacobi in FP64, one CTA per block: column pairs in the
+// round-robin order, one warp per pair (fixed-order warp reductions), a sweep without
+// rotation above 1e-15 of the pair's norms ends it.  The columns then hold sigma_j u_j.
+// The host keeps the D largest singular values over all blocks and the kernel
+// k_svd_emit writes the kept left vectors.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <tuple>
+#include <vector>
+
+#include "../../include/dmrg_heff.h"
+#include "handle.h"
+
+namespace dmrg {
+namespace {
+
+constexpr int SVD_NT = 256;
+constexpr int SVD_WARPS = SVD_NT / 32;
+constexpr int SVD_MAX_SWEEPS = 40;
+constexpr double SVD_ZERO = 1e-13;   // singular values below this fraction of the largest are zero
+
+struct SvdJob {
+    int64_t off;      // of the block in psi and in the column-major scratch
+    int64_t sv_off;   // of its cols singular values / column order
+    int32_t rows, cols;
+};
+
+// Sum over the warp, the same value in every lane: lane 0's result is broadcast (the
+// butterfly leaves each lane with its own rounding order), so a rotation decision and
+// its (c, s) agree across the lanes that apply it.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
+__global__ void __launch_bounds__(SVD_NT) k_svd_jacobi(const double* __restrict__ psi, double* __restrict__ A,
+                                                       const SvdJob* __restrict__ jobs, double* __restrict__ raw,
+                                                       double* __restrict__ sv, int32_t* __restrict__ order) {
+    const SvdJob J = jobs[blockIdx.x];
+    const int rows = J.rows, cols = J.cols, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    double* a = A + J.off;   // column j at a + j * rows
+    for (int64_t e = tid; e < int64_t(rows) * cols; e += SVD_NT) {
+        const int r = int(e / cols), c = int(e % cols);
+        a[int64_t(c) * rows + r] = psi[J.off + e];
+    }
+    __syncthreads();
+    __shared__ int s_rot;
+    const int M = (cols + 1) & ~1, half = M / 2;
+    for (int sweep = 0; sweep < SVD_MAX_SWEEPS && cols >= 2; ++sweep) {
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        for (int r = 0; r < M - 1; ++r) {
+            for (int k = warp; k < half; k += SVD_WARPS) {
+                const int x = k == 0 ? 0 : ((k - 1 + r) % (M - 1)) + 1;
+                const int y = ((M - 2 - k + r) % (M - 1)) + 1;
+                const int p = min(x, y), q = max(x, y);
+                if (q >= cols) continue;   // the padding column of an odd count
+                double* ap = a + int64_t(p) * rows;
+                double* aq = a + int64_t(q) * rows;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = lane; i < rows; i += 32) {
+                    const double u = ap[i], w = aq[i];
+                    al += u * u; be += w * w; ga += u * w;
+                }
+                al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+                if (ga != 0.0 && ga * ga > 1e-30 * al * be) {
+                    const double zeta = (be - al) / (2.0 * ga);
+                    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                    for (int i = lane; i < rows; i += 32) {
+                        const double u = ap[i], w = aq[i];
+                        ap[i] = c * u - s * w;
+                        aq[i] = s * u + c * w;
+                    }
+                    if (lane == 0) s_rot = 1;
+                }
+            }
+            __syncthreads();   // the next round's pairs read these columns
+        }
+        const int rot = s_rot;   // every thread reads it before the barrier below
+        __syncthreads();
+        if (rot == 0) break;
+    }
+    // column norms (sigma_j, any order), then ranks: descending, ties to the lower index
+    for (int j = warp; j < cols; j += SVD_WARPS) {
+        const double* aj = a + int64_t(j) * rows;
+        double s = 0.0;
+        for (int i = lane; i < rows; i += 32) s += aj[i] * aj[i];
+        s = warp_sum(s);
+        if (lane == 0) raw[J.sv_off + j] = sqrt(s);
+    }
+    __syncthreads();
+    for (int j = tid; j < cols; j += SVD_NT) {
+        const double sj = raw[J.sv_off + j];
+        int rank = 0;
+        for (int k = 0; k < cols; ++k) {
+            const double sk = raw[J.sv_off + k];
+            rank += (sk > sj || (sk == sj && k < j)) ? 1 : 0;
+        }
+        sv[J.sv_off + rank] = sj;
+        order[J.sv_off + rank] = j;
+    }
+}
+
+// U_b (rows x kept_b, row-major at u_off[b]) = kept columns / their singular values
+__global__ void k_svd_emit(const double* __restrict__ A, const SvdJob* __restrict__ jobs, const double* __restrict__ sv,
+                           const int32_t* __restrict__ order, const int32_t* __restrict__ kept,
+                           const int64_t* __restrict__ u_off, double* __restrict__ U) {
+    const SvdJob J = jobs[blockIdx.x];
+    const int k = kept[blockIdx.x];
+    for (int64_t e = threadIdx.x; e < int64_t(J.rows) * k; e += blockDim.x) {
+        const int i = int(e / k), r = int(e % k);
+        const int col = order[J.sv_off + r];
+        U[u_off[blockIdx.x] + e] = A[J.off + int64_t(col) * J.rows + i] / sv[J.sv_off + r];
+    }
+}
+
+}  // namespace
+}  // namespace dmrg
+
+using dmrg::Handle;
+
+extern "C" int dmrg_heff_psi_blocks(dmrg_heff_t hh, int64_t* buf, int64_t* n_blocks) {
+    using namespace dmrg;
+    if (!hh || !n_blocks) return fail(DMRG_ERR_INVALID_ARG, "null argument");
+    const Handle* h = static_cast<Handle*>(hh);
+    const int64_t n = int64_t(h->plan.blocks.size());
+    if (buf) {
+        if (*n_blocks < n) return fail(DMRG_ERR_INVALID_ARG, "block buffer too small");
+        for (int64_t b = 0; b < n; ++b) {
+            const PsiBlock& B = h->plan.blocks[size_t(b)];
+            buf[5 * b] = B.iL; buf[5 * b + 1] = B.iR; buf[5 * b + 2] = B.rows; buf[5 * b + 3] = B.cols;
+            buf[5 * b + 4] = B.off;
+        }
+    }
+    *n_blocks = n;
+    return DMRG_OK;
+}
+
+extern "C" int dmrg_svd_truncate(dmrg_heff_t hh, const double* psi, int32_t D, double* sv_out, int32_t* kept_out,
+                                 double* U, int64_t u_len, int64_t* u_off, double* discarded) {
+    using namespace dmrg;
+    if (!hh) return fail(DMRG_ERR_INVALID_ARG, "null handle");
+    Handle* h = static_cast<Handle*>(hh);
+    if (h->plan_only) return fail(DMRG_ERR_INVALID_ARG, "plan-only handle");
+    const auto& blocks = h->plan.blocks;
+    const int64_t nb = int64_t(blocks.size());
+    if (D < 1 || u_len < 0) return fail(DMRG_ERR_INVALID_ARG, "D >= 1, u_len >= 0");
+    if (nb == 0) {
+        if (discarded) *discarded = 0.0;
+        return DMRG_OK;
+    }
+    if (!psi || !sv_out || !kept_out || !u_off || !discarded) return fail(DMRG_ERR_INVALID_ARG, "null argument");
+    std::vector<SvdJob> jobs(static_cast<size_t>(nb));
+    int64_t nsv = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        const PsiBlock& B = blocks[size_t(b)];
+        if (B.cols > 8192) return fail(DMRG_ERR_UNSUPPORTED, "a block with more than 8192 columns");
+        jobs[size_t(b)] = {B.off, nsv, B.rows, B.cols};
+        nsv += B.cols;
+    }
+    const int64_t dim = h->plan.dim;
+    double *A = nullptr, *raw = nullptr, *sv = nullptr;
+    int32_t *order = nullptr, *d_kept = nullptr;
+    int64_t* d_uoff = nullptr;
+    SvdJob* d_jobs = nullptr;
+    std::vector<void*> owned;
+    auto al = [&](void** p, size_t bytes) {
+        cudaError_t e = cudaMalloc(p, bytes > 0 ? bytes : 8);
+        if (e == cudaSuccess) owned.push_back(*p);
+        return e;
+    };
+    auto release = [&]() {
+        for (void* p : owned) cudaFree(p);
+    };
+    cudaError_t e = al(reinterpret_cast<void**>(&A), sizeof(double) * size_t(dim));
+    if (e == cudaSuccess) e = al(reinterpret_cast<void**>(&raw), sizeof(double) * size_t(nsv));
+    if (e == cudaSuccess) e = al(reinterpret_cast<void**>(&sv), sizeof(double) * size_t(nsv));
+    if (e == cudaSuccess) e = al(reinterpret_cast<void**>(&order), sizeof(int32_t) * size_t(nsv));
+    if (e == cudaSuccess) e = al(reinterpret_cast<void**>(&d_jobs), sizeof(SvdJob) * size_t(nb));
+    if (e == cudaSuccess) e = al(reinterpret_cast<void**>(&d_kept), sizeof(int32_t) * size_t(nb));
+    if (e == cudaSuccess) e = al(reinterpret_cast<void**>(&d_uoff), sizeof(int64_t) * size_t(nb));
+    if (e == cudaSuccess) e = cudaMemcpy(d_jobs, jobs.data(), sizeof(SvdJob) * size_t(nb), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_svd_jacobi<<<unsigned(nb), SVD_NT>>>(psi, A, d_jobs, raw, sv, order);
+        e = cudaGetLastError();
+    }
+    std::vector<double> hsv(static_cast<size_t>(nsv));
+    if (e == cudaSuccess) e = cudaMemcpy(hsv.data(), sv, sizeof(double) * size_t(nsv), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(e, "svd");
+    }
+    // the D largest over all blocks (ties: earlier block, then earlier position)
+    double smax = 0.0, total = 0.0;
+    for (double s : hsv) {
+        smax = std::max(smax, s);
+        total += s * s;
+    }
+    std::vector<std::tuple<double, int64_t, int32_t>> cand;
+    for (int64_t b = 0; b < nb; ++b) {
+        const int k = std::min(blocks[size_t(b)].rows, blocks[size_t(b)].cols);
+        for (int i = 0; i < k; ++i) {
+            const double s = hsv[size_t(jobs[size_t(b)].sv_off + i)];
+            if (s > SVD_ZERO * smax) cand.emplace_back(-s, b, i);
+        }
+    }
+    std::sort(cand.begin(), cand.end());
+    if (int64_t(cand.size()) > D) cand.resize(size_t(D));
+    std::vector<int32_t> kept(static_cast<size_t>(nb), 0);
+    double kept_w = 0.0;
+    for (const auto& c : cand) {
+        kept[size_t(std::get<1>(c))] += 1;
+        kept_w += std::get<0>(c) * std::get<0>(c);
+    }
+    int64_t pos = 0, ns = 0;
+    std::vector<int64_t> uo(static_cast<size_t>(nb));
+    for (int64_t b = 0; b < nb; ++b) {
+        uo[size_t(b)] = pos;
+        pos += int64_t(blocks[size_t(b)].rows) * kept[size_t(b)];
+        const int k = std::min(blocks[size_t(b)].rows, blocks[size_t(b)].cols);
+        for (int i = 0; i < k; ++i) sv_out[ns + i] = hsv[size_t(jobs[size_t(b)].sv_off + i)];
+        ns += k;
+        kept_out[b] = kept[size_t(b)];
+        u_off[b] = uo[size_t(b)];
+    }
+    *discarded = total - kept_w;
+    if (pos > 0 && (!U || pos > u_len)) {
+        release();
+        return fail(DMRG_ERR_INVALID_ARG, "U too small for the kept vectors");
+    }
+    e = cudaMemcpy(d_kept, kept.data(), sizeof(int32_t) * size_t(nb), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_uoff, uo.data(), sizeof(int64_t) * size_t(nb), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && pos > 0) {
+        k_svd_emit<<<unsigned(nb), SVD_NT>>>(A, d_jobs, sv, order, d_kept, d_uoff, U);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    release();
+    return e == cudaSuccess ? int(DMRG_OK) : cuda_fail(e, "svd emit");
+}
