@@ -58,6 +58,8 @@ def parse():
                     help="also run the Davidson time-to-E comparison on workloads other than tiny/mid")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule")
     ap.add_argument("--no-per-gemm", action="store_true", help="skip the one-launch-per-GEMM comparison")
+    ap.add_argument("--no-update-steps", action="store_true",
+                    help="skip timing the truncation and renormalisation steps of the update")
     return ap.parse_args()
 
 
@@ -186,6 +188,60 @@ def roofline(stats, precision, fp64_peak, timed_long):
             "traffic": tr, "algorithmic_bytes_per_launch": round(d["bytes"] / max(d["launches"], 1)),
             "launches": d["launches"], "avg_launch_ms": round(d["ms"] / max(d["launches"], 1), 5),
             "peak_source": src}
+
+
+def update_steps(lib, h, p, fp64_peak, reps=5):
+    """The steps after the eigensolver on this workload, CUDA events around each call:
+    decomposition/truncation of a wave function to D = |psi| / 4 states, and
+    renormalisation of every A_t block into random orthonormal bases keeping 60 % of each
+    sector (FP64 flops 2 d_p d_q d'_q + 2 d'_p d_p d'_q per block)."""
+    import numpy as np
+    import torch
+    out = {}
+    psi = torch.from_numpy(p.random_vectors(1)[0]).cuda()
+    D = max(1, p.dim // 4)
+    h.svd_truncate(psi, D)
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        h.svd_truncate(psi, D)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    out["svd_truncate"] = {"D": D, "ms": round(float(np.median(ts)), 4), "blocks": int(len(h.psi_blocks()))}
+    rng = np.random.default_rng(0)
+    dims = p.left[:, 2].astype(np.int32)
+    new = np.maximum(1, np.ceil(0.6 * dims)).astype(np.int32)
+    U = np.concatenate([np.linalg.qr(rng.standard_normal((d, d)))[0][:, :k].ravel() for d, k in zip(dims, new)])
+    idx = {(int(n), int(s)): i for i, (n, s, _) in enumerate(p.left)}
+    blocks, flops = [], 0
+    for t in range(p.n_terms):
+        for q in range(len(dims)):
+            if p.a_off[t, q] >= 0:
+                o = idx[(int(p.left[q][0]) + int(p.delta[t][0]), int(p.left[q][1]) + int(p.delta[t][1]))]
+                blocks.append((q, o, int(p.a_off[t, q])))
+                flops += 2 * int(dims[o]) * int(dims[q]) * int(new[q]) + 2 * int(new[o]) * int(dims[o]) * int(new[q])
+    blocks = np.array(blocks, np.int64)
+    n_out = int(sum(int(new[a]) * int(new[b]) for a, b, _ in blocks))
+    Ud = torch.from_numpy(U).cuda()
+    opd = torch.from_numpy(p.op_data).cuda()
+    outd = torch.empty(n_out, dtype=torch.float64, device="cuda")
+    lib.renormalise(dims, new, Ud, blocks, opd, outd)
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        lib.renormalise(dims, new, Ud, blocks, opd, outd)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = float(np.median(ts))
+    tf = flops / (ms * 1e-3) / 1e12
+    out["renormalise"] = {"blocks": int(len(blocks)), "ms": round(ms, 4), "fp64_tflops": round(tf, 4),
+                          "frac_of_fp64_peak": round(tf / fp64_peak, 4) if fp64_peak else None,
+                          "note": "includes its own scratch allocation and the basis transposition"}
+    return out
 
 
 def davidson_time_to_e(lib, p, args):
@@ -417,6 +473,8 @@ def run_ours(args):
             "flops_per_step": flops_vec * args.nvec}
     if rank == 0 and not args.no_davidson and (args.config in ("tiny", "mid") or args.davidson):
         line["davidson"] = davidson_time_to_e(lib, p, args)
+    if rank == 0 and not args.no_update_steps and args.config in ("tiny", "mid", "precision"):
+        line["update_steps"] = update_steps(lib, h, p, fp64_peak or lib.probe_fp64_peak())
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, flops_vec, args.cpu_seconds)
         line["cpu_baseline"].pop("_np", None)
