@@ -72,3 +72,15 @@ def test_random_vectors_unit_norm():
     V = p.random_vectors(3)
     np.testing.assert_allclose(np.linalg.norm(V, axis=1), 1.0, rtol=1e-15)
     assert not np.array_equal(V[0], V[1])
+
+
+def test_su2_pinned():
+    from dmrg_synth import su2 as G
+    g = json.load(open(os.path.join(GOLDEN, "synth_digests.json")))
+    for name in ("su2_tiny", "su2_mid"):
+        p = G.generate(name, seed=0)
+        assert p.digest() == g[name]["sha256"]
+        assert (p.dim, p.n_terms, p.op_data.size) == (g[name]["dim"], g[name]["n_terms"], g[name]["op_len"])
+    t = G.generate("su2_mid").left
+    assert len(t) == 38 and int(t[:, 2].sum()) == 1024 and int(t[:, 1].min()) >= 0
+    assert all((int(s) - int(n)) % 2 == 0 for n, s, _ in t)
