@@ -58,6 +58,7 @@ def parse():
                     help="also run the Davidson time-to-E comparison on workloads other than tiny/mid")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedule")
     ap.add_argument("--no-per-gemm", action="store_true", help="skip the one-launch-per-GEMM comparison")
+    ap.add_argument("--no-su2", action="store_true", help="skip the spin-adapted (SU(2)) measurement")
     ap.add_argument("--no-update-steps", action="store_true",
                     help="skip timing the truncation and renormalisation steps of the update")
     return ap.parse_args()
@@ -294,6 +295,45 @@ def davidson_time_to_e(lib, p, args):
     return out
 
 
+def su2_section(lib, args, steps=200):
+    """Spin-adapted (SU(2)) H_eff*psi on the 1024-multiplet mid workload (600 terms,
+    singlet target): FP64-equivalent TFLOP/s of both paths (graph replays after an
+    autotune, CUDA events), the relative difference of the split result from the FP64
+    one, and Davidson (and Lanczos) time-to-eigenvalue split vs FP64."""
+    import numpy as np
+    import torch
+    from dmrg_synth import su2 as G
+    p = G.generate("su2_mid", seed=args.seed)
+    X = torch.from_numpy(p.random_vectors(1)).cuda()
+    st = torch.cuda.current_stream()
+    out = {"workload": f"su2_mid: {int(p.left[:, 2].sum())} multiplets per block over {len(p.left)} (n,2S) sectors, "
+                       f"T={p.n_terms} terms, singlet target (20,0), |psi|={p.dim}, seed {args.seed}",
+           "operator_GB": round(p.op_data.size * 8 / 1e9, 3)}
+    ys = {}
+    for prec in ("fp64", "split"):
+        h = lib.HEff.from_problem(p, precision="fp64" if prec == "fp64" else "split_bf16")
+        h.autotune(nvec=1, reps=2)
+        Y = torch.empty_like(X)
+        for _ in range(3):
+            h.apply(X, Y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            h.apply(X, Y)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[prec] = {"ms_per_apply": round(ms, 5), "value": round(h.flops / (ms * 1e-3) / 1e12, 4), "unit": UNIT,
+                     "steps": steps}
+        out["flops_per_apply"] = h.flops
+        ys[prec] = Y.cpu().numpy()
+        h.close()
+    out["split_rel_fro_vs_fp64"] = float(np.linalg.norm(ys["split"] - ys["fp64"]) / np.linalg.norm(ys["fp64"]))
+    out["davidson"] = davidson_time_to_e(lib, p, args)
+    return out
+
+
 def cpu_baseline(p, flops_per_vec, seconds):
     """The oracle as it stands, timed on the host cores on a bounded sample."""
     import numpy as np
@@ -473,6 +513,8 @@ def run_ours(args):
             "flops_per_step": flops_vec * args.nvec}
     if rank == 0 and not args.no_davidson and (args.config in ("tiny", "mid") or args.davidson):
         line["davidson"] = davidson_time_to_e(lib, p, args)
+    if rank == 0 and not args.no_su2 and args.config == "mid":
+        line["su2"] = su2_section(lib, args)
     if rank == 0 and not args.no_update_steps and args.config in ("tiny", "mid", "precision"):
         line["update_steps"] = update_steps(lib, h, p, fp64_peak or lib.probe_fp64_peak())
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -108,6 +108,40 @@ int dmrg_heff_create(const int32_t* left, int32_t nl, const int32_t* right, int3
                      const double* op_data, int64_t op_len,
                      const dmrg_heff_opts* opts, dmrg_heff_t* out);
 
+/*
+ * Spin-adapted (SU(2)) H_eff (paper: the DMRG is spin-adapted, Introduction and
+ * Numerical procedure).  Sectors are (n, 2S) multiplets: tables (n, two_s, dim) with
+ * dim = number of multiplets, 0 <= two_s <= 40, strictly ascending in (n, two_s).
+ * Term t is c_t sum_mu (-1)^{k-mu} T_mu U_-mu (times (-1)^{n_L(input)} if parity[t]),
+ * T and U rank-k tensors (rank2[t] = 2k <= 40) shifting n by +dn[t] (left) and -dn[t]
+ * (right), given by reduced blocks in the Clebsch-Gordan-normalised Wigner-Eckart
+ * convention <S' m'| T_mu |S m> = <S m; k mu | S' m'> A[S' <- S].
+ *   a_blocks (n_a x 4), b_blocks (n_b x 4): rows (term, in sector, out sector, offset of
+ *       the row-major dim(out) x dim(in) block in op_data), any order, each at most once;
+ *       out n = in n + dn (A) or in n - dn (B), (S_in, k, S_out) a triangle.
+ * The reduced wave function of (target_n, target_2s) holds one block per sector pair
+ * with n_L + n_R = target_n and (S_L, S_R, S) a triangle, in (left, right) order
+ * (dmrg_heff_psi_blocks lists them); every (term, A block, B block) between two such
+ * blocks contributes c_t s_t W A x B^T with W the recoupling coefficient of
+ * dmrg_su2_recoupling.  The plan dump, apply, diagonal, Davidson and Lanczos entry
+ * points work as for dmrg_heff_create; dmrg_svd_truncate refuses these handles.
+ * Returns DMRG_ERR_INVALID_ARG / _SECTOR_MISMATCH for malformed input, _OOM, _CUDA. */
+int dmrg_heff_create_su2(const int32_t* left, int32_t nl, const int32_t* right, int32_t nr,
+                         int32_t target_n, int32_t target_2s,
+                         const double* coef, const int32_t* rank2, const int32_t* dn,
+                         const int32_t* parity, int64_t n_terms,
+                         const int64_t* a_blocks, int64_t n_a, const int64_t* b_blocks, int64_t n_b,
+                         const double* op_data, int64_t op_len,
+                         const dmrg_heff_opts* opts, dmrg_heff_t* out);
+
+/* Recoupling coefficient of the spin-adapted terms (host only, all arguments twice the
+ * spins): W = <(S_L' S_R') S M | sum_mu (-1)^{k-mu} T_mu U_-mu | (S_L S_R) S M> for unit
+ * reduced blocks, computed as (-1)^{S_L+S_R'+k+S} sqrt((2S_L'+1)(2S_R'+1))
+ * {S_L' S_L k; S_R S_R' S} (Racah's 6j sum); 0 unless every triangle holds.
+ * DMRG_ERR_INVALID_ARG for a spin outside [0, 20] (total spin [0, 40]) or w NULL. */
+int dmrg_su2_recoupling(int32_t two_sl_out, int32_t two_sr_out, int32_t two_sl_in, int32_t two_sr_in,
+                        int32_t two_k, int32_t two_s, double* w);
+
 /* Number of wave-function entries |psi| (0 for an empty target sector). */
 int64_t dmrg_heff_dim(dmrg_heff_t h);
 

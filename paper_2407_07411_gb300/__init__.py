@@ -33,7 +33,7 @@ SYMBOLS = ("dmrg_heff_create", "dmrg_heff_dim", "dmrg_heff_flops", "dmrg_heff_pl
            "dmrg_heff_profile_read", "dmrg_probe_fp64_peak", "dmrg_heff_apply_noalloc",
            "dmrg_selftest_wait_timeout", "dmrg_heff_schedule_get", "dmrg_heff_schedule_set",
            "dmrg_heff_autotune", "dmrg_heff_gemm_count", "dmrg_lanczos", "dmrg_renormalise",
-           "dmrg_heff_psi_blocks", "dmrg_svd_truncate")
+           "dmrg_heff_psi_blocks", "dmrg_svd_truncate", "dmrg_heff_create_su2", "dmrg_su2_recoupling")
 
 
 class Opts(ctypes.Structure):
@@ -84,6 +84,10 @@ _i32, _i64, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 _lib.dmrg_heff_create.argtypes = [_P, _i32, _P, _i32, _i32, _i32, _P, _P, _P, _P, _P, _i64, _P, _i64,
                                   ctypes.POINTER(Opts), ctypes.POINTER(_P)]
 _lib.dmrg_heff_create.restype = ctypes.c_int
+_lib.dmrg_heff_create_su2.argtypes = [_P, _i32, _P, _i32, _i32, _i32, _P, _P, _P, _P, _i64, _P, _i64, _P, _i64,
+                                      _P, _i64, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_void_p)]
+_lib.dmrg_heff_create_su2.restype = ctypes.c_int
+_lib.dmrg_su2_recoupling.argtypes = [_i32, _i32, _i32, _i32, _i32, _i32, ctypes.POINTER(_f64)]
 _lib.dmrg_heff_dim.argtypes = [_P]
 _lib.dmrg_heff_dim.restype = _i64
 _lib.dmrg_heff_flops.argtypes = [_P, ctypes.POINTER(_i64)]
@@ -186,8 +190,38 @@ class HEff:
     @classmethod
     def from_problem(cls, p, **kw) -> "HEff":
         """Build from any object with the fields of a two-site problem
-        (left, right, target, coef, delta, parity, a_off, b_off, op_data)."""
+        (left, right, target, coef, delta, parity, a_off, b_off, op_data), or of a
+        spin-adapted one (see from_su2)."""
+        if hasattr(p, "rank2"):
+            return cls.from_su2(p, **kw)
         return cls(p.left, p.right, p.target, p.coef, p.delta, p.parity, p.a_off, p.b_off, p.op_data, **kw)
+
+    @classmethod
+    def from_su2(cls, p, precision: str = "fp64", max_nvec: int = 1, n_slices: int = 0, plan_only: bool = False,
+                 graphs: bool = True) -> "HEff":
+        """Spin-adapted handle (dmrg_heff_create_su2) from an object with the fields
+        left, right, target, coef, rank2, dn, parity, a_blocks, b_blocks, op_data."""
+        self = cls.__new__(cls)
+        self._h = None
+        arr = lambda a, dt: np.ascontiguousarray(np.asarray(a, dtype=dt))  # noqa: E731
+        self._left = arr(p.left, np.int32).reshape(-1, 3)
+        self._right = arr(p.right, np.int32).reshape(-1, 3)
+        coef = arr(p.coef, np.float64)
+        rank2, dn, parity = arr(p.rank2, np.int32), arr(p.dn, np.int32), arr(p.parity, np.int32)
+        ab = arr(p.a_blocks, np.int64).reshape(-1, 4)
+        bb = arr(p.b_blocks, np.int64).reshape(-1, 4)
+        op_data = arr(p.op_data, np.float64)
+        opts = Opts(_PREC[precision] if isinstance(precision, str) else int(precision), n_slices, max_nvec,
+                    (FLAG_PLAN_ONLY if plan_only else 0) | (0 if graphs else FLAG_NO_GRAPH))
+        h = ctypes.c_void_p()
+        _check(_lib.dmrg_heff_create_su2(_ptr(self._left), len(self._left), _ptr(self._right), len(self._right),
+                                         int(p.target[0]), int(p.target[1]), _ptr(coef), _ptr(rank2), _ptr(dn),
+                                         _ptr(parity), coef.shape[0], _ptr(ab), ab.shape[0], _ptr(bb), bb.shape[0],
+                                         _ptr(op_data), op_data.size, ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+        self.max_nvec = max_nvec
+        self.precision = precision
+        return self
 
     def close(self):
         if self._h:
@@ -367,6 +401,15 @@ def renormalise(dims, dims_new, U, blocks, op, out, stream=None) -> np.ndarray:
                                  len(blocks), _dev_ptr(op, 0, "op"), int(op.numel()), _dev_ptr(out, 0, "out"),
                                  int(out.numel()), _ptr(out_off), _stream_ptr(stream)))
     return out_off[:len(blocks)]
+
+
+def su2_recoupling(two_sl_out: int, two_sr_out: int, two_sl_in: int, two_sr_in: int, two_k: int,
+                   two_s: int) -> float:
+    """Recoupling coefficient the spin-adapted planner applies (dmrg_su2_recoupling);
+    host only, arguments twice the spins."""
+    w = _f64()
+    _check(_lib.dmrg_su2_recoupling(two_sl_out, two_sr_out, two_sl_in, two_sr_in, two_k, two_s, ctypes.byref(w)))
+    return float(w.value)
 
 
 def probe_fp64_peak() -> float:

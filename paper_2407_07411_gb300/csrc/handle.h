@@ -114,7 +114,7 @@ struct Handle : dmrg_heff {
     int init_diag();
     int diagonal(double* diag, cudaStream_t st);
     // split-precision path (k_split.cu)
-    int init_split(const double* coef, const int64_t* a_off, const int64_t* b_off, const double* op_data);
+    int init_split();   // slices the device operator copy
     int apply_split(const double* x, double* y, int32_t nvec, cudaStream_t st);
     void release_split();
     // reads and clears the device status word of the split kernels (synchronises)

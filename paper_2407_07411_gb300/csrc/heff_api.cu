@@ -253,31 +253,27 @@ Handle::~Handle() {
 
 using dmrg::Handle;
 
-extern "C" {
+namespace {
 
-int dmrg_heff_create(const int32_t* left, int32_t nl, const int32_t* right, int32_t nr,
-                     int32_t target_n, int32_t target_2sz, const double* coef, const int32_t* delta,
-                     const int32_t* parity, const int64_t* a_off, const int64_t* b_off,
-                     int64_t n_terms, const double* op_data, int64_t op_len,
-                     const dmrg_heff_opts* opts, dmrg_heff_t* out) {
+int check_opts(const dmrg_heff_opts* opts, const double* op_data, int64_t op_len, dmrg_heff_opts* o,
+               dmrg_heff_t* out) {
     if (!out) return dmrg::fail(DMRG_ERR_INVALID_ARG, "null output handle");
     *out = nullptr;
-    dmrg_heff_opts o{DMRG_PREC_FP64, 0, 1, 0};
-    if (opts) o = *opts;
-    if (o.precision != DMRG_PREC_FP64 && o.precision != DMRG_PREC_SPLIT_BF16)
+    *o = dmrg_heff_opts{DMRG_PREC_FP64, 0, 1, 0};
+    if (opts) *o = *opts;
+    if (o->precision != DMRG_PREC_FP64 && o->precision != DMRG_PREC_SPLIT_BF16)
         return dmrg::fail(DMRG_ERR_INVALID_ARG, "unknown precision");
-    if (o.max_nvec < 1 || o.max_nvec > 64 || (o.flags & ~(DMRG_FLAG_PLAN_ONLY | DMRG_FLAG_NO_GRAPH)) != 0)
+    if (o->max_nvec < 1 || o->max_nvec > 64 || (o->flags & ~(DMRG_FLAG_PLAN_ONLY | DMRG_FLAG_NO_GRAPH)) != 0)
         return dmrg::fail(DMRG_ERR_INVALID_ARG, "max_nvec must be in [1, 64], unknown flags must be 0");
     if (op_len > 0 && !op_data) return dmrg::fail(DMRG_ERR_INVALID_ARG, "null op_data");
-    Handle* h = new (std::nothrow) Handle();
-    if (!h) return dmrg::fail(DMRG_ERR_OOM, "host allocation");
+    return DMRG_OK;
+}
+
+// Everything after the plan: device operator copy, work lists, precision state, diagonal.
+// Takes ownership of h (deleted on failure).
+int create_from_plan(Handle* h, const dmrg_heff_opts& o, const double* op_data, dmrg_heff_t* out) {
+    int rc = DMRG_OK;
     std::string err;
-    int rc = dmrg::build_plan(left, nl, right, nr, target_n, target_2sz, coef, delta, parity, a_off,
-                              b_off, n_terms, op_len, h->plan, &err);
-    if (rc != DMRG_OK) {
-        delete h;
-        return dmrg::fail(rc, err);
-    }
     h->precision = o.precision;
     h->max_nvec = o.max_nvec;
     h->n_slices = o.n_slices;
@@ -350,7 +346,7 @@ int dmrg_heff_create(const int32_t* left, int32_t nl, const int32_t* right, int3
             dst += int64_t(fill);
             fill = 0;
         };
-        dmrg::stream_ops(P, coef, a_off, b_off, op_data, [&](const double* src, int64_t n, double scale) {
+        dmrg::stream_ops(P, op_data, [&](const double* src, int64_t n, double scale) {
             while (n > 0) {
                 const int64_t k = std::min<int64_t>(n, int64_t(cap - fill));
                 for (int64_t e = 0; e < k; ++e) stage[fill + size_t(e)] = scale * src[e];
@@ -373,10 +369,65 @@ int dmrg_heff_create(const int32_t* left, int32_t nl, const int32_t* right, int3
                                "stage-1 scratch")) != DMRG_OK)
             return bail(rc);
     } else {
-        if ((rc = h->init_split(coef, a_off, b_off, op_data)) != DMRG_OK) return bail(rc);
+        if ((rc = h->init_split()) != DMRG_OK) return bail(rc);
     }
     if ((rc = h->init_diag()) != DMRG_OK) return bail(rc);
     *out = h;
+    return DMRG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dmrg_heff_create(const int32_t* left, int32_t nl, const int32_t* right, int32_t nr,
+                     int32_t target_n, int32_t target_2sz, const double* coef, const int32_t* delta,
+                     const int32_t* parity, const int64_t* a_off, const int64_t* b_off,
+                     int64_t n_terms, const double* op_data, int64_t op_len,
+                     const dmrg_heff_opts* opts, dmrg_heff_t* out) {
+    dmrg_heff_opts o;
+    int rc = check_opts(opts, op_data, op_len, &o, out);
+    if (rc != DMRG_OK) return rc;
+    Handle* h = new (std::nothrow) Handle();
+    if (!h) return dmrg::fail(DMRG_ERR_OOM, "host allocation");
+    std::string err;
+    rc = dmrg::build_plan(left, nl, right, nr, target_n, target_2sz, coef, delta, parity, a_off, b_off, n_terms,
+                          op_len, h->plan, &err);
+    if (rc != DMRG_OK) {
+        delete h;
+        return dmrg::fail(rc, err);
+    }
+    return create_from_plan(h, o, op_data, out);
+}
+
+int dmrg_heff_create_su2(const int32_t* left, int32_t nl, const int32_t* right, int32_t nr, int32_t target_n,
+                         int32_t target_2s, const double* coef, const int32_t* rank2, const int32_t* dn,
+                         const int32_t* parity, int64_t n_terms, const int64_t* a_blocks, int64_t n_a,
+                         const int64_t* b_blocks, int64_t n_b, const double* op_data, int64_t op_len,
+                         const dmrg_heff_opts* opts, dmrg_heff_t* out) {
+    dmrg_heff_opts o;
+    int rc = check_opts(opts, op_data, op_len, &o, out);
+    if (rc != DMRG_OK) return rc;
+    Handle* h = new (std::nothrow) Handle();
+    if (!h) return dmrg::fail(DMRG_ERR_OOM, "host allocation");
+    std::string err;
+    rc = dmrg::build_plan_su2(left, nl, right, nr, target_n, target_2s, coef, rank2, dn, parity, n_terms, a_blocks,
+                              n_a, b_blocks, n_b, op_len, h->plan, &err);
+    if (rc != DMRG_OK) {
+        delete h;
+        return dmrg::fail(rc, err);
+    }
+    return create_from_plan(h, o, op_data, out);
+}
+
+int dmrg_su2_recoupling(int32_t two_sl_out, int32_t two_sr_out, int32_t two_sl_in, int32_t two_sr_in,
+                        int32_t two_k, int32_t two_s, double* w) {
+    const int32_t a[6] = {two_sl_out, two_sr_out, two_sl_in, two_sr_in, two_k, two_s};
+    if (!w) return dmrg::fail(DMRG_ERR_INVALID_ARG, "null output");
+    for (int i = 0; i < 6; ++i)
+        if (a[i] < 0 || a[i] > (i == 5 ? 2 : 1) * dmrg::SU2_MAX_TWO_S)
+            return dmrg::fail(DMRG_ERR_INVALID_ARG, "spin outside [0, 20] (total spin [0, 40])");
+    *w = dmrg::su2_recoupling(two_sl_out, two_sr_out, two_sl_in, two_sr_in, two_k, two_s);
     return DMRG_OK;
 }
 

@@ -1147,7 +1147,7 @@ int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err, cons
     return validate_split_plan(P, H, err);
 }
 
-int Handle::init_split(const double*, const int64_t*, const int64_t*, const double*) {
+int Handle::init_split() {
     const Plan& P = plan;
     SplitState* S = new SplitState();
     split = S;

@@ -159,9 +159,17 @@ int build_plan(const int32_t* left, int32_t nl, const int32_t* right, int32_t nr
             } else {
                 g = it->second;
             }
-            P.groups[g].terms.push_back(int32_t(t));
+            Group& G = P.groups[g];
+            G.terms.push_back(int32_t(t));
+            G.a_src.push_back(a_off[t * nl + B.iL]);
+            G.b_src.push_back(b_off[t * nr + B.iR]);
+            G.a_scale.push_back(coef[t]);
         }
     }
+    return finish_plan(P, items, err);
+}
+
+int finish_plan(Plan& P, std::vector<std::array<int64_t, 5>>& items, std::string* err) {
     std::sort(items.begin(), items.end());
     P.canon.resize(items.size() * 5);
     P.flops = 0;
@@ -178,7 +186,7 @@ int build_plan(const int32_t* left, int32_t nl, const int32_t* right, int32_t nr
         G.b_stack = pos; pos += n * G.d * G.c;
         G.scratch = scr;
         scr += G.order == 0 ? n * G.a * G.c : n * G.d * G.b;
-        if (G.dn == 0 && G.d2sz == 0) P.diag_terms += n;
+        if (G.in_block == G.out_block) P.diag_terms += n;
     }
     P.ops_len = pos;
     P.scratch_len = scr;
@@ -318,13 +326,12 @@ int build_fp64_work(Plan& P, const Schedule& S, std::string* err) {
     return DMRG_OK;
 }
 
-void stream_ops(const Plan& P, const double* coef, const int64_t* a_off, const int64_t* b_off,
-                const double* op_data, const std::function<void(const double*, int64_t, double)>& sink) {
+void stream_ops(const Plan& P, const double* op_data,
+                const std::function<void(const double*, int64_t, double)>& sink) {
     for (const Group& G : P.groups) {
-        const PsiBlock& B = P.blocks[G.in_block];
         const int64_t na = int64_t(G.a) * G.b, nb = int64_t(G.d) * G.c;
-        for (int32_t t : G.terms) sink(op_data + a_off[int64_t(t) * P.nl + B.iL], na, coef[t]);
-        for (int32_t t : G.terms) sink(op_data + b_off[int64_t(t) * P.nr + B.iR], nb, 1.0);
+        for (size_t i = 0; i < G.terms.size(); ++i) sink(op_data + G.a_src[i], na, G.a_scale[i]);
+        for (size_t i = 0; i < G.terms.size(); ++i) sink(op_data + G.b_src[i], nb, 1.0);
     }
 }
 

@@ -11,6 +11,7 @@
 // so stage 1 is one tall GEMM per group and stage 2 one long-K GEMM per output block
 // (all groups that land on it), reduced in a fixed order without atomics.
 #pragma once
+#include <array>
 #include <cstdint>
 #include <functional>
 #include <string>
@@ -73,6 +74,8 @@ struct Group {
     int32_t a, b, c, d;
     double sign;            // (-1)^{n_L(in)} for parity groups, else 1
     std::vector<int32_t> terms;
+    std::vector<int64_t> a_src, b_src;  // per term: op_data offsets of its A and B blocks
+    std::vector<double> a_scale;        // per term: factor of its stacked A copy
     int64_t a_stack, b_stack;  // offsets of the stacked operator copies (device ops)
     int64_t scratch;           // offset of X_g or Z_g^T in the per-vector scratch
 };
@@ -97,6 +100,7 @@ struct Plan {
     // per-GEMM launch ranges [first, last) into tiles1 / tiles2 (per_gemm schedules)
     std::vector<std::pair<int32_t, int32_t>> ranges1, ranges2;
     int64_t diag_terms = 0;
+    bool su2 = false;                   // spin-adapted plan (blocks need not be unique per left sector)
 };
 
 // Tile shape of the FP64 kernels (the K extent of stage-2 items is scheduled).
@@ -109,14 +113,34 @@ int build_plan(const int32_t* left, int32_t nl, const int32_t* right, int32_t nr
                const int32_t* parity, const int64_t* a_off, const int64_t* b_off,
                int64_t T, int64_t op_len, Plan& P, std::string* err);
 
+// Spin-adapted (SU(2)) plan: sectors are (n, 2S, dim) multiplet tables, terms rank-k
+// tensor products coupled to a scalar, blocks rows (term, in, out, offset).  The
+// recoupling coefficient of each (term, in block, out block) and the parity sign
+// are folded with c_t into the stacked A copies; the work lists are the U(1) ones.
+int build_plan_su2(const int32_t* left, int32_t nl, const int32_t* right, int32_t nr,
+                   int32_t tn, int32_t t2s, const double* coef, const int32_t* rank2,
+                   const int32_t* dn, const int32_t* parity, int64_t T, const int64_t* a_blocks,
+                   int64_t n_a, const int64_t* b_blocks, int64_t n_b, int64_t op_len, Plan& P,
+                   std::string* err);
+
+// Scalar-coupling recoupling coefficient of the spin-adapted terms (arguments twice
+// the spins): <(S_L' S_R') S || sum_mu (-1)^{k-mu} T_mu U_-mu || (S_L S_R) S> for unit
+// Clebsch-Gordan-normalised reduced blocks, 0 unless every triangle holds.
+double su2_recoupling(int sl_out, int sr_out, int sl_in, int sr_in, int k2, int s2);
+constexpr int SU2_MAX_TWO_S = 40;   // spins up to 20 (factorials stay far inside the double range)
+
+// Sorts the items, fills the canonical dump and flop total, lays out the stacked
+// operator copies and scratch of P.groups and builds the FP64 work lists.
+int finish_plan(Plan& P, std::vector<std::array<int64_t, 5>>& items, std::string* err);
+
 // (Re)builds the FP64 tile lists of P for schedule S; returns 0 or DMRG_ERR_INVALID_ARG.
 int build_fp64_work(Plan& P, const Schedule& S, std::string* err);
 // Checks the ranges of a schedule (not its fit to a plan).
 int check_schedule(const Schedule& S, std::string* err);
 
-// Visits the device operator layout in memory order: per group its stacked c_t A_t
-// blocks, then its B_t blocks; sink(src, n, scale) receives n doubles to be scaled.
-void stream_ops(const Plan& P, const double* coef, const int64_t* a_off, const int64_t* b_off,
-                const double* op_data, const std::function<void(const double*, int64_t, double)>& sink);
+// Visits the device operator layout in memory order: per group its stacked scaled A
+// blocks, then its B blocks; sink(src, n, scale) receives n doubles to be scaled.
+void stream_ops(const Plan& P, const double* op_data,
+                const std::function<void(const double*, int64_t, double)>& sink);
 
 }  // namespace dmrg

@@ -149,6 +149,7 @@ extern "C" int dmrg_svd_truncate(dmrg_heff_t hh, const double* psi, int32_t D, d
     if (!hh) return fail(DMRG_ERR_INVALID_ARG, "null handle");
     Handle* h = static_cast<Handle*>(hh);
     if (h->plan_only) return fail(DMRG_ERR_INVALID_ARG, "plan-only handle");
+    if (h->plan.su2) return fail(DMRG_ERR_INVALID_ARG, "truncation of a spin-adapted wave function is not built");
     const auto& blocks = h->plan.blocks;
     const int64_t nb = int64_t(blocks.size());
     if (D < 1 || u_len < 0) return fail(DMRG_ERR_INVALID_ARG, "D >= 1, u_len >= 0");
