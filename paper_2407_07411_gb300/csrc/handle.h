@@ -19,8 +19,8 @@ int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 
 // One diagonal contribution list entry: block `blk` of the wave function gets
-// sign * sum_t A_stack[t][i][i] * B_stack[t][j][j] over the n terms of a
-// Delta = 0 group (A_stack already carries c_t).
+// sign * sum_t A_stack[t][i][i] * B_stack[t][j][j] over the n terms of a group
+// whose output block is its input block (A_stack already carries c_t).
 struct DiagJob {
     int64_t a_stack, b_stack, off;
     int32_t n, rows, cols, pad;

@@ -1,5 +1,6 @@
-// Diagonal of H_eff, the Davidson preconditioner's input: only Delta = 0 terms
-// have diagonal entries, diag[(l, r)] = sum_t c_t s_t A_t[l, l] B_t[r, r].
+// Diagonal of H_eff, the Davidson preconditioner's input: only groups whose output
+// block is their input block (Delta = 0 in U(1); Delta n = 0 and unchanged spins in
+// SU(2)) have diagonal entries, diag[(l, r)] = sum_t (scaled A_t)[l, l] B_t[r, r].
 #include <vector>
 
 #include "../../include/dmrg_heff.h"
@@ -38,7 +39,7 @@ int Handle::init_diag() {
     std::vector<std::vector<int32_t>> per_block(plan.blocks.size());
     for (int32_t g = 0; g < int32_t(plan.groups.size()); ++g) {
         const Group& G = plan.groups[g];
-        if (G.dn == 0 && G.d2sz == 0) per_block[G.in_block].push_back(g);
+        if (G.in_block == G.out_block) per_block[G.in_block].push_back(g);   // U(1): Delta = 0
     }
     for (size_t k = 0; k < plan.blocks.size(); ++k) {
         for (int32_t g : per_block[k]) {
