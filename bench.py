@@ -34,9 +34,9 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 NCU_TRAFFIC = {
     # k_fp64_tiles, mid workload: (280.8 + 358.1) / 2 MB per launch (profiles/fp64_tiles_mid.md)
     "7ea6b95187a63352e09b039a09918be5e89d2a14561ebf2f4d93d0eae118ec22": 319.5e6,
-    # k_umma, mid workload: (470.6 + 541.3) / 2 MB per launch (profiles/split_umma_mid.md;
-    # captured on the source with hash 884c5da3..., this one differs in comments only)
-    "9a5ada8923ff558fa0c4f5b393f327dc822f8dda19e36782501b1bf4c0f05318": 505.9e6,
+    # k_umma, mid workload: mean of two stage-1 and two stage-2 launches, (470.5 + 538.5 +
+    # 467.5 + 538.4) / 4 MB per launch, captured on this source (profiles/split_umma_mid.md)
+    "1d4e0711bb97b9a9e36d9a142b4bae3ef00a40cd9656b8dffcb7a602e566ed1e": 503.7e6,
 }
 
 
