@@ -123,8 +123,8 @@ int dmrg_heff_create(const int32_t* left, int32_t nl, const int32_t* right, int3
  * with n_L + n_R = target_n and (S_L, S_R, S) a triangle, in (left, right) order
  * (dmrg_heff_psi_blocks lists them); every (term, A block, B block) between two such
  * blocks contributes c_t s_t W A x B^T with W the recoupling coefficient of
- * dmrg_su2_recoupling.  The plan dump, apply, diagonal, Davidson and Lanczos entry
- * points work as for dmrg_heff_create; dmrg_svd_truncate refuses these handles.
+ * dmrg_su2_recoupling.  The plan dump, apply, diagonal, Davidson, Lanczos and truncation
+ * entry points work as for dmrg_heff_create.
  * Returns DMRG_ERR_INVALID_ARG / _SECTOR_MISMATCH for malformed input, _OOM, _CUDA. */
 int dmrg_heff_create_su2(const int32_t* left, int32_t nl, const int32_t* right, int32_t nr,
                          int32_t target_n, int32_t target_2s,
@@ -311,19 +311,23 @@ int dmrg_heff_psi_blocks(dmrg_heff_t h, int64_t* buf, int64_t* n_blocks);
 
 /*
  * Two-site decomposition and truncation (paper: the matrix factorisation of the two-site
- * wave function after each local update, Numerical procedure): per wave-function block
- * psi_b (rows = dim of its left sector, cols = dim of its right sector) the singular
- * values and left singular vectors (one-sided Jacobi in FP64 on the device, one CTA
- * per block, blocks up to 8192 columns), then the D largest singular values over all
- * blocks are kept (values below 1e-13 of the largest are zero and never kept; ties go
- * to the earlier block, then position).
+ * wave function after each local update, Numerical procedure).  One matrix per left
+ * sector present in psi: its wave-function blocks side by side in block order (rows = dim
+ * of the left sector, cols = the sum of their right dims).  A U(1) handle has one block per
+ * left sector; a spin-adapted one has one per right spin coupling to the target, and the
+ * squared singular values are then the multiplet weights of the left block's density
+ * matrix summed over the magnetic sublevels.  Per matrix the singular values and left
+ * singular vectors (one-sided Jacobi in FP64 on the device, one CTA per matrix, up to 8192
+ * columns), then the D largest singular values over all matrices are kept (values below
+ * 1e-13 of the largest are zero and never kept; ties go to the earlier matrix, then
+ * position).  Matrices are indexed in the order of their left sectors.
  *   psi       : device, dim doubles
- *   sv        : host, sum_b min(rows_b, cols_b) doubles: each block's singular values,
- *               descending, in block order
- *   kept      : host, n_blocks: kept values per block (a prefix of its sv)
- *   U, u_len  : device: the kept left vectors of block b, row-major rows_b x kept_b at
- *               u_off[b] (host, n_blocks); u_len must hold sum rows_b kept_b (U may be
- *               NULL when nothing is kept)
+ *   sv        : host, sum_m min(rows_m, cols_m) doubles: each matrix's singular values,
+ *               descending, in matrix order
+ *   kept      : host, one per matrix: kept values (a prefix of its sv)
+ *   U, u_len  : device: the kept left vectors of matrix m, row-major rows_m x kept_m at
+ *               u_off[m] (host, one per matrix); u_len must hold sum rows_m kept_m (U may
+ *               be NULL when nothing is kept)
  *   discarded : host: the sum of the squares of the singular values not kept.
  * Synchronises the device; allocates and frees its scratch. */
 int dmrg_svd_truncate(dmrg_heff_t h, const double* psi, int32_t D, double* sv, int32_t* kept, double* U, int64_t u_len,

@@ -217,6 +217,31 @@ def diagonal(problem) -> np.ndarray:
     return out
 
 
+def truncate(problem, psi, D):
+    """Two-site decomposition of the reduced wave function: per left sector the matrix of
+    its blocks side by side (in block order), then the rule of oracle.svd.truncate over
+    these matrices.  Returns its dict plus sectors (the left sector of each matrix).
+    Reading: the squared singular values of that matrix are the eigenvalues of the left
+    block's density matrix summed over the magnetic sublevels (the tests check this on the
+    full space), so a kept singular vector is a kept multiplet."""
+    from . import svd
+    groups = []
+    for iL, _, off, rows, cols in psi_blocks(problem):
+        if groups and groups[-1][0] == iL:
+            groups[-1][2].append((off, cols))
+        else:
+            groups.append((iL, rows, [(off, cols)]))
+    flat, mats, pos = [], [], 0
+    for _, rows, parts in groups:
+        M = np.hstack([psi[o:o + rows * c].reshape(rows, c) for o, c in parts])
+        flat.append(M.ravel())
+        mats.append((pos, rows, M.shape[1]))
+        pos += M.size
+    r = svd.truncate(mats, np.concatenate(flat) if flat else np.zeros(0), D)
+    r["sectors"] = [g[0] for g in groups]
+    return r
+
+
 # ---------------------------------------------------------------------------
 # M-resolved (full) space of tiny problems
 

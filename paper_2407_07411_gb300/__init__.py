@@ -301,25 +301,38 @@ class HEff:
         _check(_lib.dmrg_heff_psi_blocks(self._h, _ptr(buf), ctypes.byref(n)))
         return buf[:n.value]
 
+    def svd_matrices(self) -> np.ndarray:
+        """Matrices of the two-site decomposition: rows (left sector, rows, cols, offset of
+        its first block) -- per left sector its wave-function blocks side by side."""
+        out = []
+        for iL, _, rows, cols, off in self.psi_blocks():
+            if out and out[-1][0] == iL:
+                out[-1][2] += int(cols)
+            else:
+                out.append([int(iL), int(rows), int(cols), int(off)])
+        return np.array(out, np.int64).reshape(-1, 4)
+
     def svd_truncate(self, psi, D: int) -> dict:
-        """Per-block SVD of the device wave function psi and truncation to the D largest
-        singular values; returns dict(sv=[per block], kept, U=device tensor of the kept
-        left vectors, u_off, discarded)."""
+        """SVD per left sector of the device wave function psi (its blocks side by side,
+        see svd_matrices) and truncation to the D largest singular values; returns
+        dict(sectors, sv=[per matrix], kept, U=device tensor of the kept left vectors,
+        u_off, discarded)."""
         import torch
-        blk = self.psi_blocks()
-        rows, cols = blk[:, 2], blk[:, 3]
+        mats = self.svd_matrices()
+        rows, cols = mats[:, 1], mats[:, 2]
         nsv = int(np.minimum(rows, cols).sum())
         sv = np.zeros(max(nsv, 1), np.float64)
-        kept = np.zeros(max(len(blk), 1), np.int32)
-        u_off = np.zeros(max(len(blk), 1), np.int64)
+        kept = np.zeros(max(len(mats), 1), np.int32)
+        u_off = np.zeros(max(len(mats), 1), np.int64)
         disc = _f64(0.0)
         cap = int((rows * np.minimum(np.minimum(rows, cols), D)).sum())
         U = torch.empty(max(cap, 1), dtype=torch.float64, device="cuda")
         _check(_lib.dmrg_svd_truncate(self._h, _dev_ptr(psi, self.dim, "psi"), D, _ptr(sv), _ptr(kept),
                                       ctypes.c_void_p(U.data_ptr()), int(U.numel()), _ptr(u_off), ctypes.byref(disc)))
         k = np.minimum(rows, cols)
-        parts = np.split(sv[:nsv], np.cumsum(k)[:-1]) if len(blk) else []
-        return dict(sv=parts, kept=kept[:len(blk)], U=U, u_off=u_off[:len(blk)], discarded=disc.value)
+        parts = np.split(sv[:nsv], np.cumsum(k)[:-1]) if len(mats) else []
+        return dict(sectors=mats[:, 0].copy(), sv=parts, kept=kept[:len(mats)], U=U, u_off=u_off[:len(mats)],
+                    discarded=disc.value)
 
     def gemm_count(self, nvec: int = 1) -> tuple:
         """(stage-1, stage-2) grouped GEMMs of the plan for nvec vectors."""

@@ -1,10 +1,11 @@
-// Two-site decomposition and truncation: per wave-function block psi_b (rows = dim of
-// the left sector, cols = dim of the right sector) the singular values and left vectors
-// by one-sided (Hestenes) Jacobi in FP64, one CTA per block: column pairs in the
-// round-robin order, one warp per pair (fixed-order warp reductions), a sweep without
-// rotation above 1e-15 of the pair's norms ends it.  The columns then hold sigma_j u_j.
-// The host keeps the D largest singular values over all blocks and the kernel
-// k_svd_emit writes the kept left vectors.
+// Two-site decomposition and truncation: per left sector of the wave function the matrix
+// M_q = [psi_b ...] of its blocks side by side (rows = dim of the left sector; one block
+// per left sector in U(1), one per coupled right spin in SU(2)), its singular values and
+// left vectors by one-sided (Hestenes) Jacobi in FP64, one CTA per matrix: column pairs
+// in the round-robin order, one warp per pair (fixed-order warp reductions), a sweep
+// without rotation above 1e-15 of the pair's norms ends it.  The columns then hold
+// sigma_j u_j.  The host keeps the D largest singular values over all matrices and the
+// kernel k_svd_emit writes the kept left vectors.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,9 +26,10 @@ constexpr int SVD_MAX_SWEEPS = 40;
 constexpr double SVD_ZERO = 1e-13;   // singular values below this fraction of the largest are zero
 
 struct SvdJob {
-    int64_t off;      // of the block in psi and in the column-major scratch
+    int64_t off;      // of the matrix's first block in psi and of the matrix in the scratch
     int64_t sv_off;   // of its cols singular values / column order
     int32_t rows, cols;
+    int32_t b0, nb;   // its blocks: consecutive in psi, cols bcols[b0 .. b0 + nb)
 };
 
 // Sum over the warp, the same value in every lane: lane 0's result is broadcast (the
@@ -40,14 +42,22 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 __global__ void __launch_bounds__(SVD_NT) k_svd_jacobi(const double* __restrict__ psi, double* __restrict__ A,
-                                                       const SvdJob* __restrict__ jobs, double* __restrict__ raw,
+                                                       const SvdJob* __restrict__ jobs,
+                                                       const int32_t* __restrict__ bcols, double* __restrict__ raw,
                                                        double* __restrict__ sv, int32_t* __restrict__ order) {
     const SvdJob J = jobs[blockIdx.x];
     const int rows = J.rows, cols = J.cols, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     double* a = A + J.off;   // column j at a + j * rows
-    for (int64_t e = tid; e < int64_t(rows) * cols; e += SVD_NT) {
-        const int r = int(e / cols), c = int(e % cols);
-        a[int64_t(c) * rows + r] = psi[J.off + e];
+    int cbase = 0;
+    int64_t boff = J.off;
+    for (int bi = 0; bi < J.nb; ++bi) {   // block bi: row-major rows x cb, columns [cbase, cbase + cb)
+        const int cb = bcols[J.b0 + bi];
+        for (int64_t e = tid; e < int64_t(rows) * cb; e += SVD_NT) {
+            const int r = int(e / cb), c = int(e % cb);
+            a[int64_t(cbase + c) * rows + r] = psi[boff + e];
+        }
+        cbase += cb;
+        boff += int64_t(rows) * cb;
     }
     __syncthreads();
     __shared__ int s_rot;
@@ -108,7 +118,7 @@ __global__ void __launch_bounds__(SVD_NT) k_svd_jacobi(const double* __restrict_
     }
 }
 
-// U_b (rows x kept_b, row-major at u_off[b]) = kept columns / their singular values
+// U_q (rows x kept_q, row-major at u_off[q]) = kept columns / their singular values
 __global__ void k_svd_emit(const double* __restrict__ A, const SvdJob* __restrict__ jobs, const double* __restrict__ sv,
                            const int32_t* __restrict__ order, const int32_t* __restrict__ kept,
                            const int64_t* __restrict__ u_off, double* __restrict__ U) {
@@ -149,8 +159,21 @@ extern "C" int dmrg_svd_truncate(dmrg_heff_t hh, const double* psi, int32_t D, d
     if (!hh) return fail(DMRG_ERR_INVALID_ARG, "null handle");
     Handle* h = static_cast<Handle*>(hh);
     if (h->plan_only) return fail(DMRG_ERR_INVALID_ARG, "plan-only handle");
-    if (h->plan.su2) return fail(DMRG_ERR_INVALID_ARG, "truncation of a spin-adapted wave function is not built");
-    const auto& blocks = h->plan.blocks;
+    const auto& pblocks = h->plan.blocks;
+    // one matrix per left sector: its blocks are consecutive in the layout
+    struct Mat { int64_t off; int32_t rows, cols, b0, nb; };
+    std::vector<Mat> blocks;
+    std::vector<int32_t> bcols(pblocks.size());
+    for (size_t b = 0; b < pblocks.size(); ++b) {
+        const PsiBlock& B = pblocks[b];
+        bcols[b] = B.cols;
+        if (!blocks.empty() && pblocks[b - 1].iL == B.iL) {
+            blocks.back().cols += B.cols;
+            blocks.back().nb += 1;
+        } else {
+            blocks.push_back({B.off, B.rows, B.cols, int32_t(b), 1});
+        }
+    }
     const int64_t nb = int64_t(blocks.size());
     if (D < 1 || u_len < 0) return fail(DMRG_ERR_INVALID_ARG, "D >= 1, u_len >= 0");
     if (nb == 0) {
@@ -161,14 +184,14 @@ extern "C" int dmrg_svd_truncate(dmrg_heff_t hh, const double* psi, int32_t D, d
     std::vector<SvdJob> jobs(static_cast<size_t>(nb));
     int64_t nsv = 0;
     for (int64_t b = 0; b < nb; ++b) {
-        const PsiBlock& B = blocks[size_t(b)];
-        if (B.cols > 8192) return fail(DMRG_ERR_UNSUPPORTED, "a block with more than 8192 columns");
-        jobs[size_t(b)] = {B.off, nsv, B.rows, B.cols};
+        const Mat& B = blocks[size_t(b)];
+        if (B.cols > 8192) return fail(DMRG_ERR_UNSUPPORTED, "a left sector with more than 8192 columns");
+        jobs[size_t(b)] = {B.off, nsv, B.rows, B.cols, B.b0, B.nb};
         nsv += B.cols;
     }
     const int64_t dim = h->plan.dim;
     double *A = nullptr, *raw = nullptr, *sv = nullptr;
-    int32_t *order = nullptr, *d_kept = nullptr;
+    int32_t *order = nullptr, *d_kept = nullptr, *d_bcols = nullptr;
     int64_t* d_uoff = nullptr;
     SvdJob* d_jobs = nullptr;
     std::vector<void*> owned;
@@ -187,9 +210,12 @@ extern "C" int dmrg_svd_truncate(dmrg_heff_t hh, const double* psi, int32_t D, d
     if (e == cudaSuccess) e = al(reinterpret_cast<void**>(&d_jobs), sizeof(SvdJob) * size_t(nb));
     if (e == cudaSuccess) e = al(reinterpret_cast<void**>(&d_kept), sizeof(int32_t) * size_t(nb));
     if (e == cudaSuccess) e = al(reinterpret_cast<void**>(&d_uoff), sizeof(int64_t) * size_t(nb));
+    if (e == cudaSuccess) e = al(reinterpret_cast<void**>(&d_bcols), sizeof(int32_t) * bcols.size());
     if (e == cudaSuccess) e = cudaMemcpy(d_jobs, jobs.data(), sizeof(SvdJob) * size_t(nb), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_bcols, bcols.data(), sizeof(int32_t) * bcols.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        k_svd_jacobi<<<unsigned(nb), SVD_NT>>>(psi, A, d_jobs, raw, sv, order);
+        k_svd_jacobi<<<unsigned(nb), SVD_NT>>>(psi, A, d_jobs, d_bcols, raw, sv, order);
         e = cudaGetLastError();
     }
     std::vector<double> hsv(static_cast<size_t>(nsv));
@@ -198,7 +224,7 @@ extern "C" int dmrg_svd_truncate(dmrg_heff_t hh, const double* psi, int32_t D, d
         release();
         return cuda_fail(e, "svd");
     }
-    // the D largest over all blocks (ties: earlier block, then earlier position)
+    // the D largest over all matrices (ties: earlier matrix, then earlier position)
     double smax = 0.0, total = 0.0;
     for (double s : hsv) {
         smax = std::max(smax, s);

@@ -3,7 +3,7 @@ both precision paths: full products on the tiny workload for a triplet, a single
 and a doublet target (several stacked vectors), the mid workload (1024 multiplets,
 600 terms), the diagonal, the lowest eigenvalue from Davidson and Lanczos against the
 dense reduced operator (tiny) and the converged oracle energy of the mid workload
-(pinned in tests/golden), and the refusal of spin-adapted truncation."""
+(pinned in tests/golden), and the two-site decomposition per left sector."""
 import json
 import os
 
@@ -90,9 +90,29 @@ def test_mid_ground_state(precision):
     assert info["resid_max"] <= 1e-9
 
 
-def test_truncation_refused():
+@pytest.mark.parametrize("name,target,D", [("su2_tiny", (6, 2), 30), ("su2_tiny", (5, 1), 12),
+                                           ("su2_mid", None, 400)])
+def test_truncation_matches_oracle(name, target, D):
+    """Per left sector (its blocks side by side): singular values, kept counts,
+    discarded weight and the kept bases through their projectors."""
     import torch
-    p = G.generate("su2_tiny")
+    p = G.generate(name, target=target)
     h = lib.HEff.from_problem(p)
-    with pytest.raises(lib.DmrgError):
-        h.svd_truncate(torch.from_numpy(p.random_vectors(1)[0]).cuda(), 8)
+    psi = p.random_vectors(1)[0]
+    r = h.svd_truncate(torch.from_numpy(psi).cuda(), D)
+    ref = O.truncate(p, psi, D)
+    assert list(r["sectors"]) == ref["sectors"]
+    smax = max(s[0] for s in ref["sv"])
+    for s, t in zip(r["sv"], ref["sv"]):
+        np.testing.assert_allclose(s, t, rtol=0, atol=1e-13 * smax)
+    assert list(r["kept"]) == ref["kept"] and sum(ref["kept"]) == D
+    assert abs(r["discarded"] - ref["discarded"]) <= 1e-12
+    U = r["U"].cpu().numpy()
+    mats = h.svd_matrices()
+    for m, k in enumerate(r["kept"]):
+        if k == 0:
+            continue
+        rows = int(mats[m, 1])
+        Ug = U[r["u_off"][m]:r["u_off"][m] + rows * k].reshape(rows, k)
+        np.testing.assert_allclose(Ug.T @ Ug, np.eye(k), atol=1e-12)
+        assert np.linalg.norm(Ug @ Ug.T - ref["U"][m] @ ref["U"][m].T) <= 1e-9

@@ -5,7 +5,8 @@ values; the Heisenberg dimer S_L . S_R, whose energies are the closed form
 sublevel, assembled from the reduced blocks by Wigner-Eckart, which must commute
 with the total spin (built from the ladder formula alone) and reproduce the reduced
 operator on the coupled states; the reduction to the U(1) oracle when every spin is
-0; symmetry and linearity."""
+0; symmetry and linearity; the truncation weights against the density matrix of the
+full state."""
 import itertools
 import math
 
@@ -164,3 +165,29 @@ def test_generator_is_deterministic():
     a, b = G.generate("su2_tiny"), G.generate("su2_tiny")
     assert a.digest() == b.digest()
     assert G.generate("su2_tiny", seed=1).digest() != a.digest()
+
+
+def test_truncation_weights_are_the_summed_density_matrix(tiny_full):
+    """Per left sector the stacked matrix M_q = [psi_b ...] satisfies
+    M_q M_q^T = sum_m rho_L[(q, ., m), (q, ., m)], rho_L the left density matrix of the
+    full state E psi; its squared singular values are therefore the multiplet weights."""
+    p, F, _ = tiny_full
+    psi = p.random_vectors(1)[0]
+    full = F["E"] @ psi
+    bl, br = O.m_basis(p.left), O.m_basis(p.right)
+    Psi = np.zeros((len(bl), len(br)))
+    Psi.ravel()[F["index"]] = full
+    rho = Psi @ Psi.T
+    r = O.truncate(p, psi, 10 ** 6)
+    assert abs(sum(float((s ** 2).sum()) for s in r["sv"]) - 1.0) <= 1e-13
+    for q, sv in zip(r["sectors"], r["sv"]):
+        d = int(p.left[q][2])
+        acc = np.zeros((d, d))
+        for m in range(-int(p.left[q][1]), int(p.left[q][1]) + 1, 2):
+            idx = [i for i, st in enumerate(bl) if st[0] == q and st[2] == m]
+            acc += rho[np.ix_(idx, idx)]
+        w = np.sort(np.linalg.eigvalsh(acc))[::-1][:len(sv)]
+        np.testing.assert_allclose(w, sv ** 2, atol=1e-14)
+    assert r["discarded"] <= 1e-12
+    n_blocks = len(O.psi_blocks(p))   # S > 0: some left sectors own several blocks
+    assert len(r["sectors"]) < n_blocks if p.target[1] > 0 else len(r["sectors"]) == n_blocks
