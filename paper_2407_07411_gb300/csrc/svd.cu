@@ -2,8 +2,8 @@
 // M_q = [psi_b ...] of its blocks side by side (rows = dim of the left sector; one block
 // per left sector in U(1), one per coupled right spin in SU(2)), its singular values and
 // left vectors by one-sided (Hestenes) Jacobi in FP64, one CTA per matrix: column pairs
-// in the round-robin order, one warp per pair (fixed-order warp reductions), a sweep
-// without rotation above 1e-15 of the pair's norms ends it.  The columns then hold
+// in the round-robin order, 8 lanes per pair (fixed-order sums), a sweep without
+// rotation above 1e-15 of the pair's norms ends it.  The columns then hold
 // sigma_j u_j.  The host keeps the D largest singular values over all matrices and the
 // kernel k_svd_emit writes the kept left vectors.
 #include <cuda_runtime.h>
@@ -20,8 +20,11 @@
 namespace dmrg {
 namespace {
 
-constexpr int SVD_NT = 256;
+constexpr int SVD_NT = 512;
+constexpr int64_t SVD_SMEM_MAX = 200 * 1024;   // matrices up to this size are rotated in shared memory
 constexpr int SVD_WARPS = SVD_NT / 32;
+constexpr int SVD_LPP = 8;                               // lanes per column pair
+constexpr int SVD_BATCH = SVD_WARPS * (32 / SVD_LPP);    // pairs in flight (64)
 constexpr int SVD_MAX_SWEEPS = 40;
 constexpr double SVD_ZERO = 1e-13;   // singular values below this fraction of the largest are zero
 
@@ -41,13 +44,17 @@ __device__ __forceinline__ double warp_sum(double v) {
     return __shfl_sync(0xffffffffu, v, 0);
 }
 
+// SMEM: the matrix is rotated in dynamic shared memory (rows * cols doubles) and copied to
+// the scratch A at the end; otherwise it is rotated in A.  The arithmetic is the same.
+template <bool SMEM>
 __global__ void __launch_bounds__(SVD_NT) k_svd_jacobi(const double* __restrict__ psi, double* __restrict__ A,
                                                        const SvdJob* __restrict__ jobs,
                                                        const int32_t* __restrict__ bcols, double* __restrict__ raw,
                                                        double* __restrict__ sv, int32_t* __restrict__ order) {
+    extern __shared__ __align__(16) double s_mat[];
     const SvdJob J = jobs[blockIdx.x];
     const int rows = J.rows, cols = J.cols, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    double* a = A + J.off;   // column j at a + j * rows
+    double* a = SMEM ? s_mat : A + J.off;   // column j at a + j * rows
     int cbase = 0;
     int64_t boff = J.off;
     for (int bi = 0; bi < J.nb; ++bi) {   // block bi: row-major rows x cb, columns [cbase, cbase + cb)
@@ -60,35 +67,79 @@ __global__ void __launch_bounds__(SVD_NT) k_svd_jacobi(const double* __restrict_
         boff += int64_t(rows) * cb;
     }
     __syncthreads();
+    // Each round's disjoint pairs go in batches of SVD_BATCH: (1) 8 lanes per pair form
+    // partial dot products over a stride-8 row stripe, (2) one thread per pair sums them
+    // in lane order and computes the rotation, (3) the 8 lanes apply it.  The rotation's
+    // divisions and square roots are then paid once per pair, not once per lane (FP64
+    // issue slots are the limit of this kernel).
+    __shared__ double s_part[SVD_BATCH][3][SVD_LPP];
+    __shared__ double s_cs[SVD_BATCH][2];
     __shared__ int s_rot;
     const int M = (cols + 1) & ~1, half = M / 2;
+    const int sub = lane % SVD_LPP, slot = warp * (32 / SVD_LPP) + lane / SVD_LPP;   // pair slot in a batch
     for (int sweep = 0; sweep < SVD_MAX_SWEEPS && cols >= 2; ++sweep) {
         if (tid == 0) s_rot = 0;
         __syncthreads();
         for (int r = 0; r < M - 1; ++r) {
-            for (int k = warp; k < half; k += SVD_WARPS) {
-                const int x = k == 0 ? 0 : ((k - 1 + r) % (M - 1)) + 1;
-                const int y = ((M - 2 - k + r) % (M - 1)) + 1;
-                const int p = min(x, y), q = max(x, y);
-                if (q >= cols) continue;   // the padding column of an odd count
+            for (int kb = 0; kb < half; kb += SVD_BATCH) {
+                // round-robin pair k of round r: columns p < q (q == cols is the padding column)
+                const int k = kb + slot;
+                int p = 0, q = cols;
+                if (k < half) {
+                    const int x = k == 0 ? 0 : ((k - 1 + r) % (M - 1)) + 1;
+                    const int y = ((M - 2 - k + r) % (M - 1)) + 1;
+                    p = min(x, y);
+                    q = max(x, y);
+                }
+                const bool act = k < half && q < cols;
                 double* ap = a + int64_t(p) * rows;
                 double* aq = a + int64_t(q) * rows;
-                double al = 0.0, be = 0.0, ga = 0.0;
-                for (int i = lane; i < rows; i += 32) {
-                    const double u = ap[i], w = aq[i];
-                    al += u * u; be += w * w; ga += u * w;
-                }
-                al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-                if (ga != 0.0 && ga * ga > 1e-30 * al * be) {
-                    const double zeta = (be - al) / (2.0 * ga);
-                    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                    const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-                    for (int i = lane; i < rows; i += 32) {
+                if (act) {
+                    double al = 0.0, be = 0.0, ga = 0.0;
+                    for (int i = sub; i < rows; i += SVD_LPP) {
                         const double u = ap[i], w = aq[i];
-                        ap[i] = c * u - s * w;
-                        aq[i] = s * u + c * w;
+                        al += u * u; be += w * w; ga += u * w;
                     }
-                    if (lane == 0) s_rot = 1;
+                    s_part[slot][0][sub] = al;
+                    s_part[slot][1][sub] = be;
+                    s_part[slot][2][sub] = ga;
+                }
+                __syncthreads();
+                if (tid < SVD_BATCH) {
+                    const int kk = kb + tid;
+                    double c = 1.0, sn = 0.0;
+                    if (kk < half) {
+                        const int x = kk == 0 ? 0 : ((kk - 1 + r) % (M - 1)) + 1;
+                        const int y = ((M - 2 - kk + r) % (M - 1)) + 1;
+                        if (max(x, y) < cols) {
+                            double al = 0.0, be = 0.0, ga = 0.0;
+#pragma unroll
+                            for (int l = 0; l < SVD_LPP; ++l) {
+                                al += s_part[tid][0][l];
+                                be += s_part[tid][1][l];
+                                ga += s_part[tid][2][l];
+                            }
+                            if (ga != 0.0 && ga * ga > 1e-30 * al * be) {
+                                const double zeta = (be - al) / (2.0 * ga);
+                                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                                c = 1.0 / sqrt(1.0 + t * t);
+                                sn = c * t;
+                                s_rot = 1;
+                            }
+                        }
+                    }
+                    s_cs[tid][0] = c;
+                    s_cs[tid][1] = sn;
+                }
+                __syncthreads();
+                if (act) {
+                    const double c = s_cs[slot][0], sn = s_cs[slot][1];
+                    if (sn != 0.0)
+                        for (int i = sub; i < rows; i += SVD_LPP) {
+                            const double u = ap[i], w = aq[i];
+                            ap[i] = c * u - sn * w;
+                            aq[i] = sn * u + c * w;
+                        }
                 }
             }
             __syncthreads();   // the next round's pairs read these columns
@@ -116,6 +167,8 @@ __global__ void __launch_bounds__(SVD_NT) k_svd_jacobi(const double* __restrict_
         sv[J.sv_off + rank] = sj;
         order[J.sv_off + rank] = j;
     }
+    if (SMEM)   // the emit kernel reads the rotated columns from A
+        for (int64_t e = tid; e < int64_t(rows) * cols; e += SVD_NT) A[J.off + e] = s_mat[e];
 }
 
 // U_q (rows x kept_q, row-major at u_off[q]) = kept columns / their singular values
@@ -214,8 +267,33 @@ extern "C" int dmrg_svd_truncate(dmrg_heff_t hh, const double* psi, int32_t D, d
     if (e == cudaSuccess) e = cudaMemcpy(d_jobs, jobs.data(), sizeof(SvdJob) * size_t(nb), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(d_bcols, bcols.data(), sizeof(int32_t) * bcols.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-        k_svd_jacobi<<<unsigned(nb), SVD_NT>>>(psi, A, d_jobs, d_bcols, raw, sv, order);
+    // matrices that fit in shared memory first, then the others (rotated in A)
+    std::vector<SvdJob> small, large;
+    int64_t smem = 0;
+    for (const SvdJob& J : jobs) {
+        const int64_t bytes = int64_t(J.rows) * J.cols * int64_t(sizeof(double));
+        if (bytes <= SVD_SMEM_MAX) {
+            small.push_back(J);
+            smem = std::max(smem, bytes);
+        } else {
+            large.push_back(J);
+        }
+    }
+    SvdJob *d_small = nullptr, *d_large = nullptr;
+    if (e == cudaSuccess && !small.empty()) e = al(reinterpret_cast<void**>(&d_small), sizeof(SvdJob) * small.size());
+    if (e == cudaSuccess && !large.empty()) e = al(reinterpret_cast<void**>(&d_large), sizeof(SvdJob) * large.size());
+    if (e == cudaSuccess && !small.empty())
+        e = cudaMemcpy(d_small, small.data(), sizeof(SvdJob) * small.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !large.empty())
+        e = cudaMemcpy(d_large, large.data(), sizeof(SvdJob) * large.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !small.empty())
+        e = cudaFuncSetAttribute(k_svd_jacobi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess && !small.empty()) {
+        k_svd_jacobi<true><<<unsigned(small.size()), SVD_NT, size_t(smem)>>>(psi, A, d_small, d_bcols, raw, sv, order);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && !large.empty()) {
+        k_svd_jacobi<false><<<unsigned(large.size()), SVD_NT>>>(psi, A, d_large, d_bcols, raw, sv, order);
         e = cudaGetLastError();
     }
     std::vector<double> hsv(static_cast<size_t>(nsv));
