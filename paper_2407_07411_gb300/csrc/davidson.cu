@@ -249,9 +249,11 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ S, in
                 const int b = ((M - 2 - k + r) % (M - 1)) + 1;
                 const int p = min(a, b), q = max(a, b);
                 const double apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
-                // rotate only while the off-diagonal entry is above rounding level
-                // (|apq| > 1e-18 sqrt|app aqq|, compared in squares)
-                if (apq * apq > 1e-36 * fabs(app * aqq) + 1e-300) {
+                // rotate only while the off-diagonal entry is above rounding level,
+                // |apq| > 1e-15 sqrt|app aqq| (compared in squares): a smaller one moves
+                // the eigenvalues by < 1e-30 relative, and rotations below rounding level
+                // only regenerate rounding noise and run sweeps up to the limit
+                if (apq * apq > 1e-30 * fabs(app * aqq) + 1e-300) {
                     const double tau = (aqq - app) / (2.0 * apq);
                     const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
                     const double c = 1.0 / sqrt(1.0 + t * t);
