@@ -30,13 +30,18 @@ UNIT = "TFLOP/s"
 SPLIT_PAIRS = 21   # BF16 slice-pair products per FP64-equivalent product (6 slices, i+j<=5)
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes per launch of the dominant kernel from one ncu capture, keyed by the
-# sha256 of the kernel source it was taken on (a changed kernel reports null).
+# sha256 of the kernel source it was taken on and the workload (a changed kernel or
+# an uncaptured workload reports null).
 NCU_TRAFFIC = {
     # k_fp64_tiles, mid workload: (280.8 + 358.1) / 2 MB per launch (profiles/fp64_tiles_mid.md)
-    "7ea6b95187a63352e09b039a09918be5e89d2a14561ebf2f4d93d0eae118ec22": 319.5e6,
+    ("7ea6b95187a63352e09b039a09918be5e89d2a14561ebf2f4d93d0eae118ec22", "mid"): 319.5e6,
     # k_umma, mid workload: mean of two stage-1 and two stage-2 launches, (470.5 + 538.5 +
     # 467.5 + 538.4) / 4 MB per launch, captured on this source (profiles/split_umma_mid.md)
-    "1d4e0711bb97b9a9e36d9a142b4bae3ef00a40cd9656b8dffcb7a602e566ed1e": 503.7e6,
+    ("1d4e0711bb97b9a9e36d9a142b4bae3ef00a40cd9656b8dffcb7a602e566ed1e", "mid"): 503.7e6,
+    # spin-adapted su2_mid (profiles/su2_mid.md): k_umma (1199.5 + 1215.7 + 1195.8 +
+    # 1216.0) / 4 MB, k_fp64_tiles (708.0 + 998.8) / 2 MB per launch
+    ("1d4e0711bb97b9a9e36d9a142b4bae3ef00a40cd9656b8dffcb7a602e566ed1e", "su2_mid"): 1206.8e6,
+    ("7ea6b95187a63352e09b039a09918be5e89d2a14561ebf2f4d93d0eae118ec22", "su2_mid"): 853.4e6,
 }
 
 
@@ -84,7 +89,37 @@ def whole_job_tflops(flops_per_step, steps, world, t_max_ms):
     return flops_per_step * steps * world / (t_max_ms * 1e-3) / 1e12
 
 
+def load_workload(name, seed, n_terms=None):
+    """The named workload: U(1) (dmrg_synth) or spin-adapted (names su2_*)."""
+    if name.startswith("su2_"):
+        from dmrg_synth import su2 as G
+        return G.generate(name, seed=seed, n_terms=n_terms)
+    import dmrg_synth as S
+    return S.generate(name, seed=seed, n_terms=n_terms)
+
+
+def oracle_for(p):
+    """The oracle module of the problem's symmetry (apply, plan)."""
+    if hasattr(p, "rank2"):
+        from oracle import su2 as o
+    else:
+        from oracle import heff as o
+    return o
+
+
 def workload_config(p, args, precision):
+    if hasattr(p, "rank2"):
+        from dmrg_synth import su2 as G
+        cfg = G.CONFIGS[args.config]
+        return {
+            "workload": f"{args.config}{'' if args.terms is None else f' (first {args.terms} terms)'}: spin-adapted "
+                        f"two-site H_eff, {cfg['D']} multiplets per block over {len(p.left)} (n,2S) sectors, "
+                        f"T={p.n_terms} terms, target (n,2S)={tuple(p.target)}, |psi|={p.dim}, seed {args.seed}",
+            "D": cfg["D"], "sectors": int(len(p.left)), "terms": int(p.n_terms), "psi_dim": int(p.dim),
+            "operator_GB": round(p.op_data.size * 8 / 1e9, 3), "nvec": args.nvec, "precision": precision,
+            "l2": "inputs larger than L2 (all operator blocks are read every step)",
+            "parallelism": "replicas",
+        }
     import dmrg_synth as S
     cfg = S.CONFIGS[args.config]
     return {
@@ -157,7 +192,7 @@ def kernel_sha(name: str) -> str:
     return hashlib.sha256(open(os.path.join(ROOT, "paper_2407_07411_gb300", "csrc", name), "rb").read()).hexdigest()
 
 
-def roofline(stats, precision, fp64_peak, timed_long):
+def roofline(stats, precision, fp64_peak, timed_long, config):
     """Dominant kernel (largest summed event time) against its tensor peak."""
     by_kernel = {}
     for s in stats:
@@ -183,7 +218,7 @@ def roofline(stats, precision, fp64_peak, timed_long):
         src = (f"MEASURED_PEAKS.json {key} ({bf16} TFLOP/s bf16) / {SPLIT_PAIRS} slice pairs" if key in pk
                else f"profiling recipe fallback bf16 / {SPLIT_PAIRS}")
         src_name = "k_split.cu"
-    tr = NCU_TRAFFIC.get(kernel_sha(src_name))
+    tr = NCU_TRAFFIC.get((kernel_sha(src_name), config))
     return {"kernel": name, "bound": "tensor", "achieved": round(achieved, 4), "peak": round(peak, 4),
             "unit": "TFLOP/s", "frac": round(achieved / peak, 4) if peak else None,
             "traffic": tr, "algorithmic_bytes_per_launch": round(d["bytes"] / max(d["launches"], 1)),
@@ -295,11 +330,12 @@ def davidson_time_to_e(lib, p, args):
     return out
 
 
-def su2_section(lib, args, steps=200):
+def su2_section(lib, args, fp64_peak, steps=200):
     """Spin-adapted (SU(2)) H_eff*psi on the 1024-multiplet mid workload (600 terms,
     singlet target): FP64-equivalent TFLOP/s of both paths (graph replays after an
-    autotune, CUDA events), the relative difference of the split result from the FP64
-    one, and Davidson (and Lanczos) time-to-eigenvalue split vs FP64."""
+    autotune, CUDA events) with their fraction of the FP64 and BF16-per-pair peaks, the
+    relative difference of the split result from the FP64 one, and Davidson (and
+    Lanczos) time-to-eigenvalue split vs FP64."""
     import numpy as np
     import torch
     from dmrg_synth import su2 as G
@@ -324,8 +360,15 @@ def su2_section(lib, args, steps=200):
         e1.record(st)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
-        out[prec] = {"ms_per_apply": round(ms, 5), "value": round(h.flops / (ms * 1e-3) / 1e12, 4), "unit": UNIT,
-                     "steps": steps}
+        tf = h.flops / (ms * 1e-3) / 1e12
+        if prec == "fp64":
+            pk, src = fp64_peak, "DMMA probe (dmrg_probe_fp64_peak)"
+        else:
+            bf16 = peaks().get("bf16_tflops")
+            pk, src = (bf16 / SPLIT_PAIRS, "MEASURED_PEAKS.json bf16_tflops / 21 slice pairs") if bf16 else (None, None)
+        out[prec] = {"ms_per_apply": round(ms, 5), "value": round(tf, 4), "unit": UNIT, "steps": steps,
+                     "frac_of_peak": round(tf / pk, 4) if pk else None, "peak": round(pk, 4) if pk else None,
+                     "peak_source": src}
         out["flops_per_apply"] = h.flops
         ys[prec] = Y.cpu().numpy()
         h.close()
@@ -337,7 +380,7 @@ def su2_section(lib, args, steps=200):
 def cpu_baseline(p, flops_per_vec, seconds):
     """The oracle as it stands, timed on the host cores on a bounded sample."""
     import numpy as np
-    from oracle import heff as oheff
+    oheff = oracle_for(p)
     x = p.random_vectors(1)[0]
     calls, t0, c0 = 0, time.perf_counter(), time.process_time()
     while True:
@@ -358,10 +401,9 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    import dmrg_synth as S
-    from oracle import heff as oheff
-    p = S.generate(args.config, seed=args.seed)
-    flops = oheff.plan_flops(p)
+    p = load_workload(args.config, args.seed)
+    oheff = oracle_for(p)
+    flops = int(oheff.plan(p)[:, 4].sum())
     x = p.random_vectors(1)[0]
     t0 = time.perf_counter()
     oheff.apply(p, x)
@@ -370,8 +412,8 @@ def run_reference(args):
     frac = min(1.0, budget / max(one * (args.steps + args.warmup), 1e-9))
     if frac < 1.0:   # bounded sample: the first fraction of the terms
         T = max(1, int(p.n_terms * frac))
-        p = S.generate(args.config, seed=args.seed, n_terms=T)
-        flops = oheff.plan_flops(p)
+        p = load_workload(args.config, args.seed, n_terms=T)
+        flops = int(oheff.plan(p)[:, 4].sum())
     for _ in range(args.warmup):
         oheff.apply(p, x)
     t0, c0 = time.perf_counter(), time.process_time()
@@ -402,11 +444,10 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    import dmrg_synth as S
     import paper_2407_07411_gb300 as lib
 
     precision = {"fp64": "fp64", "split": "split_bf16", "split_bf16": "split_bf16"}[args.precision]
-    p = S.generate(args.config, seed=args.seed, n_terms=args.terms)
+    p = load_workload(args.config, args.seed, n_terms=args.terms)
     h = lib.HEff.from_problem(p, precision=precision, max_nvec=args.nvec)
     flops_vec = h.flops
     fp64_peak = lib.probe_fp64_peak() if precision == "fp64" else None
@@ -506,7 +547,8 @@ def run_ours(args):
                       "FP32 partial sums recombined in int64, FP64 output"),
             "data": "synthetic (seeded sector structure, random operator blocks)",
             "config": workload_config(p, args, precision),
-            "roofline": roofline(stats, precision, fp64_peak, timed_long=t_max > 2000),
+            "roofline": roofline(stats, precision, fp64_peak, timed_long=t_max > 2000,
+                                 config=args.config if args.terms is None and args.nvec == 1 else None),
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches, "graphs": graphs,
             "autotune": tune, "per_gemm": per_gemm,
             "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()} for s in stats],
@@ -514,7 +556,7 @@ def run_ours(args):
     if rank == 0 and not args.no_davidson and (args.config in ("tiny", "mid") or args.davidson):
         line["davidson"] = davidson_time_to_e(lib, p, args)
     if rank == 0 and not args.no_su2 and args.config == "mid":
-        line["su2"] = su2_section(lib, args)
+        line["su2"] = su2_section(lib, args, fp64_peak or lib.probe_fp64_peak())
     if rank == 0 and not args.no_update_steps and args.config in ("tiny", "mid", "precision"):
         line["update_steps"] = update_steps(lib, h, p, fp64_peak or lib.probe_fp64_peak())
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

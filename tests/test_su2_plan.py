@@ -88,3 +88,18 @@ def test_empty_target():
     p = G.generate("su2_tiny", target=(30, 0))
     h = lib.HEff.from_problem(p, plan_only=True)
     assert h.dim == 0 and h.flops == 0 and len(h.plan_dump()) == 0
+
+
+@pytest.mark.parametrize("target", [(6, 2), (6, 0), (5, 1)])
+def test_svd_matrices_group_blocks_by_left_sector(target):
+    p = G.generate("su2_tiny", target=target)
+    h = lib.HEff.from_problem(p, plan_only=True)
+    mats = h.svd_matrices()
+    blocks = O.psi_blocks(p)
+    lefts = sorted({b[0] for b in blocks})
+    assert list(mats[:, 0]) == lefts
+    for iL, rows, cols, off in mats:
+        mine = [b for b in blocks if b[0] == iL]
+        assert rows == mine[0][3] and cols == sum(b[4] for b in mine) and off == mine[0][2]
+    if target[1] > 0:
+        assert len(mats) < len(blocks)
