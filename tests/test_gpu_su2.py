@@ -3,7 +3,8 @@ both precision paths: full products on the tiny workload for a triplet, a single
 and a doublet target (several stacked vectors), the mid workload (1024 multiplets,
 600 terms), the diagonal, the lowest eigenvalue from Davidson and Lanczos against the
 dense reduced operator (tiny) and the converged oracle energy of the mid workload
-(pinned in tests/golden), and the two-site decomposition per left sector."""
+(pinned in tests/golden), a block Davidson for the two lowest, results bit-identical
+across schedules and after autotuning, and the two-site decomposition per left sector."""
 import json
 import os
 
@@ -116,3 +117,33 @@ def test_truncation_matches_oracle(name, target, D):
         Ug = U[r["u_off"][m]:r["u_off"][m] + rows * k].reshape(rows, k)
         np.testing.assert_allclose(Ug.T @ Ug, np.eye(k), atol=1e-12)
         assert np.linalg.norm(Ug @ Ug.T - ref["U"][m] @ ref["U"][m].T) <= 1e-9
+
+
+def test_split_schedules_and_autotune():
+    """Spin-adapted plans under other schedules: the split result bit for bit, and the
+    autotuned schedule within tolerance (same contract as the U(1) path)."""
+    p = G.generate("su2_mid", n_terms=150, target=(20, 2))
+    X = p.random_vectors(2)
+    ref = O.apply(p, X)
+    h = lib.HEff.from_problem(p, precision="split", max_nvec=2)
+    y0 = gpu_apply(h, X)
+    assert rel_fro(y0, ref) <= TOL["split"]
+    base = dict(fp64_kchunk=[512, 512, 2048], fp64_ctas_per_sm=0, split_kchunk=[0, 0, 0], per_gemm=0)
+    for sched in (dict(base, split_kchunk=[8, 64, 256]), dict(base, per_gemm=1)):
+        h.schedule = sched
+        assert np.array_equal(gpu_apply(h, X), y0)
+    r = h.autotune(nvec=2, reps=2)
+    assert 0 < r["best_ms"] <= r["default_ms"] and h.schedule == r["best"]
+    assert rel_fro(gpu_apply(h, X), ref) <= TOL["split"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_tiny_block_davidson_two_lowest(precision):
+    import torch
+    p = G.generate("su2_tiny", target=(6, 2))
+    w = np.linalg.eigvalsh(O.apply(p, np.eye(p.dim)).T)
+    h = lib.HEff.from_problem(p, precision=precision, max_nvec=2)
+    x = torch.from_numpy(p.random_vectors(2)).cuda()
+    ev, info = h.davidson(x, k_eig=2, tol=1e-9, max_iter=300, block=2)
+    assert info["converged"]
+    np.testing.assert_allclose(ev[:2], w[:2], rtol=1e-10)
