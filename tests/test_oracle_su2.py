@@ -191,3 +191,21 @@ def test_truncation_weights_are_the_summed_density_matrix(tiny_full):
     assert r["discarded"] <= 1e-12
     n_blocks = len(O.psi_blocks(p))   # S > 0: some left sectors own several blocks
     assert len(r["sectors"]) < n_blocks if p.target[1] > 0 else len(r["sectors"]) == n_blocks
+
+
+def test_plan_hand_computed():
+    """Two multiplet sectors per block, (n, 2S) = (1, 1) dim 2 and (1, 3) dim 1, target
+    (2, 2S=2): the four sector pairs all couple to S = 1, blocks b0 = (0,0) 2x2,
+    b1 = (0,1) 2x1, b2 = (1,0) 1x2, b3 = (1,1) 1x1.  Term 0 (rank 1) has only
+    A[1 <- 0] (1x2) and B[1 <- 1] (1x1): one contribution b1 -> b3 with a=1, b=2, c=1,
+    d=1, (A x) B^T = 2*1*2*1 + 2*1*1*1 = 6 < A (x B^T) = 8.  Term 1 (rank 0) has A[0 <- 0]
+    and B[0 <- 0] (2x2): b0 -> b0, 2*8 + 2*8 = 32 either way, a tie, so A-first."""
+    table = [(1, 1, 2), (1, 3, 1)]
+    rng = np.random.default_rng(2)
+    terms = [(0.5, 2, 0, 0, {(0, 1): rng.standard_normal((1, 2))}, {(1, 1): rng.standard_normal((1, 1))}),
+             (0.3, 0, 0, 0, {(0, 0): rng.standard_normal((2, 2))}, {(0, 0): rng.standard_normal((2, 2))})]
+    p = G.pack(table, table, (2, 2), terms)
+    assert [(b[0], b[1], b[2], b[3], b[4]) for b in O.psi_blocks(p)] == \
+        [(0, 0, 0, 2, 2), (0, 1, 4, 2, 1), (1, 0, 6, 1, 2), (1, 1, 8, 1, 1)]
+    assert p.dim == 9
+    np.testing.assert_array_equal(O.plan(p), np.array([[0, 1, 0, 0, 32], [3, 0, 1, 0, 6]]))
