@@ -103,3 +103,22 @@ def test_svd_matrices_group_blocks_by_left_sector(target):
         assert rows == mine[0][3] and cols == sum(b[4] for b in mine) and off == mine[0][2]
     if target[1] > 0:
         assert len(mats) < len(blocks)
+
+
+def test_full_mid_plan_bit_exact():
+    p = G.generate("su2_mid")
+    h = lib.HEff.from_problem(p, plan_only=True)
+    ref = O.plan(p)
+    assert np.array_equal(h.plan_dump(), ref) and h.flops == int(ref[:, 4].sum()) == 13631489180
+
+
+def test_bench_workload_dispatch():
+    """bench.py serves the spin-adapted workloads: generator, oracle and description."""
+    import argparse
+    import bench
+    p = bench.load_workload("su2_tiny", 0)
+    assert hasattr(p, "rank2") and bench.oracle_for(p) is O
+    args = argparse.Namespace(config="su2_tiny", terms=None, seed=0, nvec=1)
+    cfg = bench.workload_config(p, args, "split_bf16")
+    assert cfg["psi_dim"] == p.dim and "spin-adapted" in cfg["workload"]
+    assert all(isinstance(k, tuple) and len(k) == 2 for k in bench.NCU_TRAFFIC)
