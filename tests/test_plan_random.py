@@ -1,7 +1,7 @@
 """Randomised planning checks (CPU, plan-only handles): on seeded random small problems of
 both symmetries -- random sector tables, term kinds and subsets of present blocks -- the
 library's plan, wave-function size and flop total equal the oracle's independent
-planner bit for bit."""
+planner bit for bit, and the split planner proves its bounds."""
 import numpy as np
 import pytest
 
@@ -80,3 +80,12 @@ def test_su2_random_plan(seed):
     assert h.dim == p.dim == sum(b[3] * b[4] for b in O.psi_blocks(p))
     assert np.array_equal(h.plan_dump(), ref)
     assert h.flops == (int(ref[:, 4].sum()) if len(ref) else 0)
+
+
+@pytest.mark.parametrize("seed", range(20))
+@pytest.mark.parametrize("nvec", [1, 3])
+def test_random_split_plans_prove_bounds(seed, nvec):
+    """The split planner's host-side bounds proof (every copy, slice write, exponent and
+    store in range) on the random shapes above, both symmetries."""
+    for p in (_u1_problem(np.random.default_rng(1000 + seed)), _su2_problem(np.random.default_rng(2000 + seed))):
+        lib.HEff.from_problem(p, precision="split", plan_only=True, max_nvec=nvec).close()
