@@ -10,7 +10,14 @@ Modules
   heff     sector indexing, contraction-order planner, H_eff*psi from its
            blockwise definition, dense Kronecker H (tiny cases), diagonal of H.
   davidson block Davidson with CGS2 orthogonalisation and thick restart.
+  lanczos  restarted Lanczos with full reorthogonalisation.
   ozaki    split-precision (Ozaki) slicing and the exact slice-product sum.
+  svd      two-site decomposition and truncation to the D largest singular values.
+  renorm   operator renormalisation O' = U_p^T O U_q in per-sector bases.
+  su2      the spin-adapted form: Clebsch-Gordan coefficients, the recoupling
+           coefficient from its definition, the reduced H_eff*psi, its planner and
+           diagonal, the truncation per left sector, and the full operator with every
+           magnetic sublevel (tiny cases).
 
 Pins (what ties each function to something other than itself) live in
 ``tests/test_oracle_*.py``: dense Kronecker assembly through ``numpy.kron``,
@@ -18,5 +25,7 @@ closed-form ground-state energies of textbook models (Heisenberg, eta-pairing
 and Hubbard dimers, the free-fermion chain), exact diagonalisation of a
 four-site Hubbard chain in its full Fock space, ``numpy.linalg.eigh`` and
 ARPACK (``scipy.sparse.linalg.eigsh``), Hermiticity, linearity, sector
-conservation, hand-computed plans, and exact integer arithmetic for the slices.
+conservation, hand-computed plans, exact integer arithmetic for the slices, and for
+the spin-adapted form sympy's Clebsch-Gordan coefficients, the Heisenberg dimer and
+the total-spin invariance of the full operator.
 """
