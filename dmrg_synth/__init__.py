@@ -30,6 +30,8 @@ is silent the readings are:
 * block entries N(0,1)/sqrt(d_in), c_t ~ N(0,1)/sqrt(T);
 * random numbers come from numpy's Philox counter-based generator keyed by
   (seed, stream), one stream per term so that any term can be rebuilt alone.
+
+The spin-adapted ((n, S) multiplet) inputs are built by ``dmrg_synth.su2``.
 """
 from __future__ import annotations
 
