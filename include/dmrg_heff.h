@@ -51,7 +51,7 @@ extern "C" {
 #define DMRG_ERR_DEVICE_TIMEOUT  -5  /* a bounded device-side wait gave up */
 #define DMRG_ERR_NOT_CONVERGED   -6  /* Davidson stopped before reaching tol */
 #define DMRG_ERR_BOUNDS          -7  /* bounds-checked build saw an out-of-range access */
-#define DMRG_ERR_UNSUPPORTED     -8  /* option not available in this build */
+#define DMRG_ERR_UNSUPPORTED     -8  /* option or size the library does not support  */
 
 /* Arithmetic of the contractions. */
 #define DMRG_PREC_FP64        0  /* FP64 DMMA tensor-core tiles (mma.sync m16n8k16 f64) */
