@@ -46,9 +46,9 @@ def test_plan_bit_exact(name, target, n_terms):
     assert list(blocks[:, 4]) == [b[2] for b in ob]
 
 
-@pytest.mark.parametrize("nvec", [1, 4])
-def test_split_plan_bounds_proof(nvec):
-    p = G.generate("su2_mid", n_terms=60)
+@pytest.mark.parametrize("n_terms,nvec", [(60, 1), (60, 4), (None, 1), (None, 8)])
+def test_split_plan_bounds_proof(n_terms, nvec):
+    p = G.generate("su2_mid", n_terms=n_terms)
     lib.HEff.from_problem(p, precision="split", plan_only=True, max_nvec=nvec).close()
 
 
