@@ -205,12 +205,12 @@ int dmrg_lanczos(dmrg_heff_t h, double tol, int32_t max_iter, int32_t m_max, dou
 
 /* y = H_eff x for one vector, allocating no GPU memory.  The paper has no counterpart:
  * this entry point exists for callers that must not allocate device memory themselves,
- * e.g. code whose GPU memory is owned and budgeted by a host framework's allocator, a
- * plugin that only receives device buffers from its host application, or a loop where
- * an allocation's implicit synchronisation would stall other work.
+ * e.g. code whose GPU memory is owned and budgeted by a host framework's allocator, or
+ * a plugin that only receives device buffers from its host application.
  *   left .. b_off, n_terms : host arrays, exactly as for dmrg_heff_create
  *   op_data (op_len doubles), x, y (dim doubles each): device pointers owned by the
- *   caller, in the layouts of this header; y is fully overwritten.
+ *   caller, in the layouts of this header; y is fully overwritten and must not overlap
+ *   x (DMRG_ERR_INVALID_ARG otherwise).
  * Everything else lives in one file-scope device array of DMRG_NOALLOC_SCRATCH_BYTES that
  * every GPU loading the library keeps until the process exits: the term tables (staged
  * from the host arrays, which the call has finished reading when it returns) and one
@@ -218,10 +218,13 @@ int dmrg_lanczos(dmrg_heff_t h, double tol, int32_t max_iter, int32_t m_max, dou
  * 512 sectors per block, or whose tables plus one such block exceed the array, are
  * rejected with DMRG_ERR_INVALID_ARG.  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  The call waits for earlier work on `stream`, queues the kernel and returns.
- * All calls share the array: calls whose work overlaps on the GPU (e.g. on two streams
- * without ordering) race and give wrong results.  Arithmetic: FP64, terms summed in
- * order per output block. */
+ * capture.  Each call waits for earlier work on `stream` and for its staged tables to
+ * land (a stream synchronisation), then queues the kernel and returns; on a stream that
+ * is capturing it returns DMRG_ERR_UNSUPPORTED without touching the stream.  All calls
+ * share the array: calls from several host threads are serialised per device from the
+ * staging of the tables to the kernel launch, but calls whose kernels overlap on the GPU
+ * (e.g. on two streams without ordering) race and give wrong results.  Arithmetic: FP64,
+ * terms summed in order per output block. */
 int dmrg_heff_apply_noalloc(const int32_t* left, int32_t nl, const int32_t* right, int32_t nr,
                             int32_t target_n, int32_t target_2sz,
                             const double* coef, const int32_t* delta, const int32_t* parity,

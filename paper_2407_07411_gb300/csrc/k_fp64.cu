@@ -2,9 +2,9 @@
 // m16n8k16 .f64), one 32x32 output tile per CTA iteration, K staged through
 // shared memory 16 columns at a time.
 //
-// On GB300 the FP64 tensor pipe peaks near 2.1 TFLOP/s (m16n8k16; m8n8k4 and
-// DFMA reach half of that), three orders of magnitude below the BF16 pipe, so
-// this kernel is bound by DMMA issue alone: the design goals are no padded MMA
+// On GB300 the FP64 tensor pipe sustains about 1.1 TFLOP/s (m16n8k16, measured by
+// the library's probe; m8n8k4 and plain DFMA about 1.0-1.05), three orders of
+// magnitude below the BF16 pipe, so this kernel is bound by DMMA issue alone: the design goals are no padded MMA
 // work beyond the 16x8x16 granularity (warps skip strips that lie outside the
 // GEMM), enough resident warps to keep the pipe busy, and balanced work
 // (dynamic tile queue, largest K range first).  Operand staging is plain loads;

@@ -112,10 +112,14 @@ namespace {
 // ----------------------------------------------------------------------------------
 // slicing
 
+// Smallest E with |a| < 2^E (INT_MIN for zero).  Subnormals count: |a| = m 2^-1074 with
+// m < 2^52, so |a| < 2^(msb(m) + 1 - 1074).
 __device__ __forceinline__ int exp_f64(double a) {
     const uint64_t b = static_cast<uint64_t>(__double_as_longlong(a));
     const int ex = int((b >> 52) & 0x7FF);
-    return ex == 0 ? INT_MIN : ex - 1022;   // |a| < 2^(ex-1022); zero and subnormal -> none
+    if (ex != 0) return ex - 1022;          // |a| < 2^(ex-1022)
+    const unsigned long long m = b & ((1ull << 52) - 1);
+    return m == 0 ? INT_MIN : (64 - __clzll(m)) - 1074;
 }
 
 __device__ __forceinline__ int exp_i64(long long F, int eF) {
@@ -140,15 +144,19 @@ __device__ __forceinline__ void balanced_digits(unsigned long long R, bool neg, 
     }
 }
 
-// R = round(|a| 2^(47 - E)) from the FP64 bit pattern (integer ops only).
+// R = round(|a| 2^(47 - E)) from the FP64 bit pattern (integer ops only).  |a| =
+// m 2^(ex - 1075) for normal numbers (m with its leading bit) and m 2^-1074 for
+// subnormals, i.e. the normal formula with ex = 1 and no leading bit.
 __device__ __forceinline__ void digits_f64(double a, int E, int (&d)[SPL_S]) {
     const uint64_t b = static_cast<uint64_t>(__double_as_longlong(a));
     const int ex = int((b >> 52) & 0x7FF);
+    const unsigned long long m = (b & ((1ull << 52) - 1)) | (ex != 0 ? (1ull << 52) : 0ull);
     unsigned long long R = 0;
-    if (ex != 0) {
-        const unsigned long long m = (b & ((1ull << 52) - 1)) | (1ull << 52);
-        const int sh = 1028 + E - ex;       // >= 6 because |a| < 2^E
-        R = sh >= 64 ? 0ull : (m + (1ull << (sh - 1))) >> sh;
+    if (m != 0) {
+        // >= 6 for normal a because |a| < 2^E; a subnormal a in a vector of subnormals
+        // can need a left shift (R < 2^47 either way)
+        const int sh = 1028 + E - (ex != 0 ? ex : 1);
+        R = sh > 0 ? (sh >= 64 ? 0ull : (m + (1ull << (sh - 1))) >> sh) : m << (-sh);
     }
     balanced_digits(R, (b >> 63) != 0, d);
 }

@@ -1,15 +1,17 @@
 // H_eff*psi without any device allocation, for callers that must not allocate GPU
 // memory themselves: a process whose device memory is owned and budgeted by a host
 // framework's allocator (an extra cudaMalloc would escape its accounting or fail once
-// its pool holds the memory), a plugin embedded in another application that only
-// receives device buffers, or a latency-critical loop where an allocation's implicit
-// synchronisation would stall other work on the device.
+// its pool holds the memory), or a plugin embedded in another application that only
+// receives device buffers.  The call is synchronous with respect to its stream's
+// earlier work (it waits for the staged tables to land), so it is meant for set-up,
+// checking and fallback use rather than for a tight loop.
 //
 // The caller passes the inputs and the output; everything else this path needs (the
 // staged term tables and one intermediate block per CTA) lives in the fixed file-scope
 // array below, which exists once per GPU that loads the library and stays resident
-// until the process exits.  All calls share it, so calls whose work overlaps on the
-// GPU race with each other.
+// until the process exits.  All calls share it: calls from several host threads are
+// serialised per device from the staging of the tables to the kernel launch, but calls
+// whose work overlaps on the GPU (two streams without ordering) race with each other.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -102,6 +104,9 @@ __global__ void __launch_bounds__(256) k_heff_noalloc(NaArgs a) {
 
 std::mutex g_setup_mutex;
 unsigned char* g_scratch_ptr[NOALLOC_MAX_DEVICES] = {};
+// Per device: held from the first table copy into the array to the kernel launch, so
+// that two host threads on one stream cannot interleave their copies and kernels.
+std::mutex g_call_mutex[NOALLOC_MAX_DEVICES];
 
 // Device address of the static array on the current device, looked up once per device.
 int scratch_address(unsigned char** out) {
@@ -185,6 +190,12 @@ extern "C" int dmrg_heff_apply_noalloc(const int32_t* left, int32_t nl, const in
     }
     if (dim == 0) return DMRG_OK;
     if (!op_data || !x || !y) return fail(DMRG_ERR_INVALID_ARG, "null device pointer");
+    {
+        const char* xb = reinterpret_cast<const char*>(x);
+        const char* yb = reinterpret_cast<const char*>(y);
+        const size_t bytes = sizeof(double) * size_t(dim);
+        if (xb < yb + bytes && yb < xb + bytes) return fail(DMRG_ERR_INVALID_ARG, "x and y overlap");
+    }
     // layout of the static array: tables, then one intermediate block per CTA
     const size_t T = size_t(n_terms);
     size_t off = 0;
@@ -208,10 +219,18 @@ extern "C" int dmrg_heff_apply_noalloc(const int32_t* left, int32_t nl, const in
     if (grid > 2 * int64_t(sms)) grid = 2 * int64_t(sms);
     const int64_t fit = int64_t((NOALLOC_BYTES - off) / per_cta);
     if (grid > fit) grid = fit;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the call synchronises its stream (below), which a capturing stream does not allow:
+    // refuse before touching the stream, so that the caller's capture stays valid
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return cuda_fail(e, "stream query");
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(DMRG_ERR_UNSUPPORTED, "the stream is capturing; this call synchronises its stream");
     unsigned char* base = nullptr;
     int rc = scratch_address(&base);
     if (rc != DMRG_OK) return rc;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> call_lock(g_call_mutex[dev]);
     struct Copy { size_t off; const void* src; size_t bytes; } copies[] = {
         {o_left, left, 12 * size_t(nl)},       {o_right, right, 12 * size_t(nr)},
         {o_blk, blk, sizeof(NaBlock) * nl},    {o_coef, coef, 8 * T},

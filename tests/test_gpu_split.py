@@ -118,6 +118,19 @@ def test_edge_long_reduction_and_scales():
     assert rel_fro(gpu_apply(split_handle(p), x)[0], heff.apply(p, x)) <= TOL_SPLIT
 
 
+def test_edge_subnormal_vector(tiny_problem):
+    # every entry of x subnormal: x is sliced relative to its own (subnormal) exponent,
+    # not flushed to zero; both sides round y to the subnormal grid (about 2^-44 of its
+    # entries here), far inside the tolerance
+    p = tiny_problem
+    x = p.random_vectors(1)[0] * 2.0 ** -1030
+    assert np.all(np.abs(x) < np.finfo(np.float64).tiny)
+    y = gpu_apply(split_handle(p), x)[0]
+    ref = heff.apply(p, x)
+    assert np.count_nonzero(y) == np.count_nonzero(ref) > 0
+    assert rel_fro(y, ref) <= TOL_SPLIT
+
+
 def test_edge_absent_blocks_and_zero_vector(tiny_problem):
     p = tiny_problem
     rng = np.random.default_rng(12)
@@ -131,15 +144,6 @@ def test_edge_absent_blocks_and_zero_vector(tiny_problem):
     Y = gpu_apply(h, X)
     assert rel_fro(Y[0], heff.apply(q, X[0])) <= TOL_SPLIT
     assert not np.any(Y[1])
-
-
-def test_precision_size_sampled():
-    p = S.generate("precision")
-    h = split_handle(p)
-    x = p.random_vectors(1)[0]
-    y = gpu_apply(h, x)[0]
-    idx = np.random.default_rng(4).choice(p.dim, 400, replace=False)
-    assert rel_fro(y[idx], heff.apply_entries(p, x, idx)) <= TOL_SPLIT
 
 
 def test_davidson_split_tiny_and_mid(tiny_problem, tiny_dense):

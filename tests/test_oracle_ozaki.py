@@ -72,3 +72,16 @@ def test_six_slices_reach_fp64_level():
     assert err < 1e-13
     err5 = np.linalg.norm(ozaki.split_product(L, R, S=5) - ref) / np.linalg.norm(ref)
     assert err5 > err   # one slice fewer loses ~8 bits
+
+
+def test_subnormal_vector_is_sliced_exactly():
+    # every entry subnormal: the vector still gets its own exponent (2^(E-1) <= max|a|
+    # < 2^E) and, since subnormals are multiples of 2^-1074 and the last digit weighs
+    # 2^(E-47) < 2^-1074 here, the six digits hold every entry exactly
+    rng = np.random.default_rng(5)
+    v = rng.standard_normal(64) * 2.0 ** -1040
+    assert np.all((np.abs(v) < np.finfo(np.float64).tiny) & (v != 0))
+    E, D = ozaki.digits(v)
+    m = max(abs(Fraction(float(a))) for a in v)
+    assert Fraction(2) ** (E - 1) <= m < Fraction(2) ** E
+    assert ozaki.reconstruct(E, D) == [Fraction(float(a)) for a in v]
