@@ -288,7 +288,7 @@ int create_from_plan(Handle* h, const dmrg_heff_opts& o, const double* op_data, 
                     delete h;
                     return dmrg::fail(rc, err);
                 }
-                h->split_host_bytes = sh.op_sl * 2 + sh.ap_sl_vs * 2 + sh.s1_vs * 8 + sh.s2_vs * 8;
+                h->split_host_bytes = sh.op_sl * 2 + sh.ap_sl_vs * 2 + sh.s2_vs * 8;
             }
         }
         *out = h;

@@ -1,21 +1,25 @@
-// Split-precision (Ozaki) H_eff*psi on the tcgen05 tensor cores (the arithmetic is
-// described in split.h).  Kernels:
+// Split-precision (Ozaki) H_eff*psi on the tcgen05 tensor cores (the arithmetic, the
+// exponent bounds and the layouts are described in split.h).  Kernels:
 //   k_slice_max, k_slice_digits
-//             FP64 or int64 operand vectors -> 6 BF16 digit slices in the UMMA
-//             canonical K-major layout, plus the vectors' exponents (integer ops only
-//             for int64 sources).  The nvec vectors of an apply are stacked inside
-//             every GEMM (along N in stage 1, along M or N in stage 2).
-//   k_umma    warp-specialised slice GEMM: one producer thread streams up to 72 KB
-//             stages with cp.async.bulk (the row groups that hold GEMM rows), one
-//             thread issues the 42 tcgen05.mma of each K tile into five accumulators
-//             (8 TMEM slots: accumulators 2-4 alternate between two), eight epilogue
-//             warps drain the exact FP32 sums into int64 every 256 K and store /
-//             atomically add.
+//             operator vectors -> their exponents (and the row-norm bounds of the
+//             stage-1 operators) and 6 BF16 digit slices in the UMMA canonical K-major
+//             layout; run once when the handle is created.
+//   k_xprep   per apply: every psi operand of stage 1 -> exponents, digit slices and
+//             the sums the bound needs; also clears the stage-2 sums and bounds.
+//   k_uest    per apply: the estimate pass, one slice pair over the stage-1 GEMMs, that
+//             fixes the exponent bound of every stage-2 intermediate vector.
+//   k_umma    warp-specialised slice GEMM: one producer thread streams 42 KB stages with
+//             cp.async.bulk (the row groups that hold GEMM rows), one thread issues the
+//             21 tcgen05.mma of each 16-K tile into five TMEM accumulators, twelve
+//             epilogue warps drain the exact FP32 sums into int64 every 256 K.  Stage 1
+//             turns its results into the stage-2 digit slices in the epilogue; stage 2
+//             adds its int64 results atomically (exact, so order-independent).
 //   k_finalize  stage-2 int64 sums -> FP64 wave-function blocks.
 // Every mbarrier wait is bounded; on timeout the CTA records DMRG_ERR_DEVICE_TIMEOUT in
 // the handle's status word, drains its own copies and MMAs and releases TMEM.
 #include <algorithm>
 #include <climits>
+#include <type_traits>
 #include <cstddef>
 #include <cstdint>
 #include <vector>
@@ -26,40 +30,26 @@
 
 namespace dmrg {
 
-constexpr int UM_STAGES = 3;
-constexpr int UM_EPI_WARPS = 8;       // two per TMEM lane quarter, each drains 32 of the 64 columns
+constexpr int UM_STAGES = 5;
+constexpr int UM_EPI_WARPS = 12;      // 4 TMEM lane quarters x 3 column thirds of 32
 constexpr int UM_THREADS = 64 + 32 * UM_EPI_WARPS;   // warp 0 producer, warp 1 MMA, the rest epilogue
-constexpr int UM_EPI_COLS = SPL_TN / (UM_EPI_WARPS / 4);
-constexpr int UM_TMEM_COLS = 512;     // 8 accumulator slots x 64 columns
-// TMEM slots: accumulators 0 and 1 have one slot each, 2-4 two each (alternating drain
-// chunks), so the epilogue drains a chunk while the MMAs of the next one run; the
-// epilogue reads accumulators 0 and 1 first, the only ones the next chunk waits for.
-constexpr int UM_SLOTS = 8;
-constexpr int UM_SINGLE = 2;          // accumulators 0 .. UM_SINGLE-1 have one slot
-__host__ __device__ constexpr int um_slot(int c, int64_t chunk) {
-    return c < UM_SINGLE ? c : UM_SINGLE + 2 * (c - UM_SINGLE) + int(chunk & 1);
-}
-// completions of a slot's barriers before the one of this chunk
-__host__ __device__ constexpr uint32_t um_use(int c, int64_t chunk) {
-    return uint32_t(c < UM_SINGLE ? chunk : chunk >> 1);
-}
-static_assert(UM_SINGLE + 2 * (SPL_ACCS - UM_SINGLE) <= UM_SLOTS && UM_SLOTS * SPL_TN <= UM_TMEM_COLS, "TMEM slots");
-constexpr uint32_t UM_L_BYTES = SPL_S * SPL_LT * 2;   // 48 KB
-constexpr uint32_t UM_R_BYTES = SPL_S * SPL_RT * 2;   // 24 KB
+constexpr int UM_EPI_COLS = 32;
+constexpr int UM_TMEM_COLS = 512;     // five accumulators of SPL_TN columns
+static_assert(SPL_ACCS * SPL_TN <= UM_TMEM_COLS && SPL_TN % 32 == 0, "TMEM accumulators");
+static_assert(SPL_TN == 3 * UM_EPI_COLS, "three epilogue column thirds");
+constexpr uint32_t UM_L_BYTES = SPL_S * SPL_LT * 2;   // 24 KB
+constexpr uint32_t UM_R_BYTES = SPL_S * SPL_RT * 2;   // 18 KB
 constexpr long long UM_WAIT_CYCLES = 4000000000ll;     // ~2 s at 2 GHz
 
-constexpr int UM_TR_LD = 5;           // row pitch (int64) of an epilogue warp's transpose patch
 struct UmmaSmem {
     uint16_t L[UM_STAGES][SPL_S * SPL_LT];
     uint16_t R[UM_STAGES][SPL_S * SPL_RT];
-    long long tr[UM_EPI_WARPS][32 * UM_TR_LD];   // 32 rows x 4 columns per pass of the stage-1 store
-    uint64_t full[UM_STAGES], empty[UM_STAGES], tfull[UM_SLOTS], tempty[UM_SLOTS], done;
+    uint64_t full[UM_STAGES], empty[UM_STAGES], tfull[SPL_ACCS], tempty[SPL_ACCS], done;
     uint32_t tmem_base;
     volatile int abort;
 };
 
 static_assert(sizeof(UmmaSmem) <= 232448, "slice GEMM shared memory exceeds the opt-in limit");
-static_assert(UM_EPI_COLS % 4 == 0, "the stage-1 store moves 4 columns per pass");
 static_assert(SPL_S2_KCHUNK / SPL_DRAIN_KT <= SPL_MAX_DRAINS, "stage-2 items span too many drains");
 
 // Device descriptors of the split plan for one number of stacked vectors.
@@ -69,19 +59,18 @@ struct SplitDevPlan {
     SWork* work2 = nullptr;
     SSeg* segs = nullptr;
     SJob* jobs = nullptr;
+    SXJob* xjobs = nullptr;
     SSlab* slabs = nullptr;
-    SItem* items = nullptr;     // [operator items | x items | intermediate items]
-    STile* tiles = nullptr;     // [operator tiles | x tiles | intermediate tiles]
+    SItem* items = nullptr;
+    STile* tiles = nullptr;
     SBlock* blocks = nullptr;
     SPart* parts = nullptr;
-    int64_t n_work1 = 0, n_work2 = 0, n_blocks = 0;
+    int64_t n_work1 = 0, n_work2 = 0, n_blocks = 0, n_xjobs = 0, n_items = 0, n_tiles = 0;
     std::vector<std::pair<int32_t, int32_t>> r1, r2;   // per-GEMM work ranges (per_gemm)
-    int64_t it_op0 = 0, it_x0 = 0, it_mid0 = 0, it_end = 0;      // item ranges
-    int64_t tl_op0 = 0, tl_x0 = 0, tl_mid0 = 0, tl_end = 0;      // tile ranges
-    int64_t ap_ex_len = 0, s2_len = 0;
-    double s1_bytes = 0, s2_bytes = 0;                           // algorithmic DRAM bytes
+    int64_t s2_len = 0, mid0 = 0, mid1 = 0;
+    double s1_bytes = 0, s2_bytes = 0, x_bytes = 0, e_bytes = 0;    // algorithmic DRAM bytes
     void release() {
-        void* p[] = {gemms, work1, work2, segs, jobs, slabs, items, tiles, blocks, parts};
+        void* p[] = {gemms, work1, work2, segs, jobs, xjobs, slabs, items, tiles, blocks, parts};
         for (void* q : p)
             if (q) cudaFree(q);
     }
@@ -90,18 +79,19 @@ struct SplitDevPlan {
 struct SplitState {
     uint16_t* op_sl = nullptr;   // operator slices (shared by every plan)
     int32_t* op_ex = nullptr;
+    int32_t* srow = nullptr;     // stage-1 operator rows: sum of |top digit|
     uint16_t* ap_sl = nullptr;   // per-apply buffers, sized for the largest plan
     int32_t* ap_ex = nullptr;
-    int64_t* s1 = nullptr;
+    float* xs = nullptr;         // psi vectors: the bound's scaled sum of |x|
     int64_t* s2 = nullptr;
     int32_t* status = nullptr;
     std::vector<SplitDevPlan> plans;   // plans[nv - 1]
     std::vector<SplitHost> hosts;      // their host copies (work lists rebuilt per schedule)
     std::vector<size_t> cap_w1, cap_w2;
-    int kid_x = -1, kid_s1 = -1, kid_mid = -1, kid_s2 = -1, kid_fin = -1;
+    int kid_x = -1, kid_e = -1, kid_s1 = -1, kid_s2 = -1, kid_fin = -1;
     ~SplitState() {
         for (SplitDevPlan& d : plans) d.release();
-        void* p[] = {op_sl, op_ex, ap_sl, ap_ex, s1, s2, status};
+        void* p[] = {op_sl, op_ex, srow, ap_sl, ap_ex, xs, s2, status};
         for (void* q : p)
             if (q) cudaFree(q);
     }
@@ -110,7 +100,7 @@ struct SplitState {
 namespace {
 
 // ----------------------------------------------------------------------------------
-// slicing
+// digits
 
 // Smallest E with |a| < 2^E (INT_MIN for zero).  Subnormals count: |a| = m 2^-1074 with
 // m < 2^52, so |a| < 2^(msb(m) + 1 - 1074).
@@ -120,12 +110,6 @@ __device__ __forceinline__ int exp_f64(double a) {
     if (ex != 0) return ex - 1022;          // |a| < 2^(ex-1022)
     const unsigned long long m = b & ((1ull << 52) - 1);
     return m == 0 ? INT_MIN : (64 - __clzll(m)) - 1074;
-}
-
-__device__ __forceinline__ int exp_i64(long long F, int eF) {
-    if (F == 0) return INT_MIN;
-    const unsigned long long u = F < 0 ? static_cast<unsigned long long>(-F) : static_cast<unsigned long long>(F);
-    return (64 - __clzll(u)) + eF;          // |F 2^eF| < 2^(msb+1+eF)
 }
 
 // Balanced base-256 digits (each in [-127, 128]) of the non-negative integer R <= 2^47,
@@ -161,16 +145,6 @@ __device__ __forceinline__ void digits_f64(double a, int E, int (&d)[SPL_S]) {
     balanced_digits(R, (b >> 63) != 0, d);
 }
 
-// value = F 2^eF; R = round(|F| 2^(eF + 47 - E)).
-__device__ __forceinline__ void digits_i64(long long F, int eF, int E, int (&d)[SPL_S]) {
-    unsigned long long u = F < 0 ? static_cast<unsigned long long>(-F) : static_cast<unsigned long long>(F);
-    const int sh = E - eF - 47;
-    unsigned long long R;
-    if (sh > 0) R = sh >= 63 ? 0ull : (u + (1ull << (sh - 1))) >> sh;
-    else R = u << (-sh);
-    balanced_digits(R, F < 0, d);
-}
-
 // BF16 bit pattern of d 2^(-8k) for a digit |d| <= 128 (exact: 8 significant bits).
 // float(d) is formed as (2^23 + (d + 128)) - (2^23 + 128): both lie in [2^23, 2^24)
 // where FP32 holds every integer, so the difference is exact, with full-rate FP32
@@ -181,14 +155,22 @@ __device__ __forceinline__ uint16_t digit_bf16(int d, int k) {
     return uint16_t(__float_as_uint(f) >> 16);
 }
 
-// Position of (vector v, K index K) inside a job's tile array (bf16 elements), slice s.
-__device__ __forceinline__ int64_t tile_pos(const SJob& J, int v, int K, int s) {
-    const int sh = J.rows_tile == SPL_TM ? 7 : 6;   // rows_tile is 128 (L) or 64 (R)
-    const int vt = v >> sh, vr = v & (J.rows_tile - 1), kt = K / SPL_TK, kr = K % SPL_TK;
-    const int64_t tile = (int64_t(vt) * J.kt + kt) * SPL_S + s;
-    return J.out_tiles + tile * (int64_t(J.rows_tile) * SPL_TK) + ((vr >> 3) * 4 + (kr >> 3)) * 64 + (vr & 7) * 8 +
-           (kr & 7);
+// Slice k of R (<= 2^47; the sign is applied by the caller) as the FP32 bit pattern of
+// d_k 2^(-8k), given Rb = R + 0x7F7F7F7F7F7F: d_k is byte (5 - k) of Rb minus 127, one
+// byte permute places that byte b under the exponent of 2^23, and one fused
+// multiply-add forms (2^23 + b) 2^(-8k) - (2^23 + 127) 2^(-8k), exact because the result
+// has at most 8 significant bits.  Only the upper 16 bits (the BF16 value) are used.
+template <int k>
+__device__ __forceinline__ uint32_t digit_float(unsigned long long Rb) {
+    constexpr int byte = SPL_S - 1 - k;
+    const uint32_t src = byte < 4 ? uint32_t(Rb) : uint32_t(Rb >> 32);
+    const uint32_t u = __byte_perm(src, 0x4B000000u, 0x7540u | uint32_t(byte & 3));   // 2^23 + b
+    const float s = __int_as_float((127 - 8 * k) << 23);
+    return __float_as_uint(fmaf(__uint_as_float(u), s, -8388735.0f * s));
 }
+
+// ----------------------------------------------------------------------------------
+// operator slicing (once per handle)
 
 struct SliceArgs {
     const SItem* items;
@@ -197,42 +179,28 @@ struct SliceArgs {
     const SJob* jobs;
     const SSeg* segs;
     const double* ops;
-    const double* x;
-    int64_t x_vs;
-    const int64_t* s1;
-    int64_t s1_vs;
-    uint16_t* op_sl;
-    uint16_t* ap_sl;
-    int64_t ap_sl_vs;
     int32_t* op_ex;
-    int32_t* ap_ex;
-    int64_t ap_ex_vs;
-    int nvec;
 };
 
-// Pass 1 (FP64 sources): every source row (term t, vector v) raises its vector's
-// exponent with an integer atomicMax (exact, so the result does not depend on order).
-// Exponents of int64 intermediates are raised by the stage-1 epilogue instead.
+// Exponent pass: every source row (term t, vector v) raises its vector's exponent with
+// an integer atomicMax (exact, so the result does not depend on order).
 __global__ void __launch_bounds__(256) k_slice_max(SliceArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t item = blockIdx.x; item < a.n_items * a.nvec; item += gridDim.x) {
-        const SItem I = a.items[item / a.nvec];
-        const int v = int(item % a.nvec);
+    for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+        const SItem I = a.items[item];
         const SSlab S = a.slabs[I.slab];
         const SJob J = a.jobs[S.job];
         const SSeg g = a.segs[S.seg];
-        const double* src = g.space == SP_OPS ? a.ops : a.x + int64_t(v) * a.x_vs;
-        int32_t* oex = J.out_buf ? a.ap_ex + int64_t(v) * a.ap_ex_vs : a.op_ex;
         for (int rr = warp; rr < I.nrows; rr += 8) {
             const int64_t r = I.r0 + rr;
             const int t = int(r / J.nvalid), vec = int(r - int64_t(t) * J.nvalid);
             const int vg = vec / g.vper, vr = vec - vg * g.vper;
             const int64_t base = g.off + t * g.ts + vg * g.vgs + int64_t(vr) * g.vs;
             int E = INT_MIN;
-            for (int k = lane; k < g.kc; k += 32) E = max(E, exp_f64(src[base + k * g.ks]));
+            for (int k = lane; k < g.kc; k += 32) E = max(E, exp_f64(a.ops[base + k * g.ks]));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
-            if (lane == 0 && E != INT_MIN) atomicMax(oex + J.out_exp + vec, E);
+            if (lane == 0 && E != INT_MIN) atomicMax(a.op_ex + J.out_exp + vec, E);
         }
     }
 }
@@ -243,72 +211,65 @@ struct TileArgs {
     const SJob* jobs;
     const SSeg* segs;
     const double* ops;
-    const double* x;
-    int64_t x_vs;
-    const int64_t* s1;
-    int64_t s1_vs;
     uint16_t* op_sl;
-    uint16_t* ap_sl;
-    int64_t ap_sl_vs;
     const int32_t* op_ex;
-    const int32_t* ap_ex;
-    int64_t ap_ex_vs;
-    int nvec;
+    int32_t* srow;
 };
 
-// Pass 2: digits of 8 vectors x 256 K of one job relative to the vectors' exponents,
-// one warp per such item.  For each 32-K sub-tile every lane decodes one K column
-// (segment, term, entry) and forms the digits of its 8 entries; the warp assembles the
-// 8x8 core matrices of every slice in its own shared-memory patch and writes them as
-// 16-byte chunks (512 contiguous bytes per slice and sub-tile).  Positions outside the
-// valid vectors and K stay zero from set-up.
 constexpr int DIG_WARPS = 8;
 
+// Writes the digits held in sd[q][vv][0..32) (8 vectors x 32 K of slice q) as the
+// 16-byte chunks of the two 16-K tiles they belong to: lanes 0-15 the first tile, lanes
+// 16-31 the second (skipped beyond the job's last tile).
+__device__ __forceinline__ void store_digit_block(uint16_t (*sd)[8][32], uint16_t* out, const SJob& J, int vt, int rg,
+                                                  int kt0, int lane) {
+    const int64_t te = int64_t(J.rows_tile) * SPL_TK;
+    const int h = lane >> 4, kg = (lane >> 3) & 1, vv = lane & 7;
+    const int kt = kt0 + h;
+    if (kt >= J.kt) return;
+#pragma unroll
+    for (int q = 0; q < SPL_S; ++q) {
+        const int64_t dst = J.out_tiles + ((int64_t(vt) * J.kt + kt) * SPL_S + q) * te + (rg * 2 + kg) * 64 + vv * 8;
+        *reinterpret_cast<uint4*>(out + dst) = *reinterpret_cast<const uint4*>(&sd[q][vv][h * 16 + kg * 8]);
+    }
+}
+
+// Digit pass: 8 vectors x 256 K of one operator job, one warp per item.  For each
+// 32-K sub-block every lane decodes one K index (segment, term, entry; the padding of
+// a term's run up to kcp is zero) and forms the digits of its 8 entries.
 __global__ void __launch_bounds__(32 * DIG_WARPS) k_slice_digits(TileArgs a) {
-    __shared__ __align__(16) uint16_t sd_all[DIG_WARPS][SPL_S][8][SPL_TK];
+    __shared__ __align__(16) uint16_t sd_all[DIG_WARPS][SPL_S][8][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint16_t (*sd)[8][SPL_TK] = sd_all[warp];
-    const int64_t n_items = a.n_tiles * a.nvec;
-    for (int64_t item = int64_t(blockIdx.x) * DIG_WARPS + warp; item < n_items;
+    uint16_t (*sd)[8][32] = sd_all[warp];
+    for (int64_t item = int64_t(blockIdx.x) * DIG_WARPS + warp; item < a.n_tiles;
          item += int64_t(gridDim.x) * DIG_WARPS) {
-        const STile T = a.tiles[item / a.nvec];
-        const int v = int(item % a.nvec);
+        const STile T = a.tiles[item];
         const SJob J = a.jobs[T.job];
-        const int32_t* oex = J.out_buf ? a.ap_ex + int64_t(v) * a.ap_ex_vs : a.op_ex;
         const int nv = min(8, J.nvalid - 8 * T.vg);
         int E[8];
 #pragma unroll
-        for (int vv = 0; vv < 8; ++vv) E[vv] = vv < nv ? oex[J.out_exp + 8 * T.vg + vv] : 0;
-        uint16_t* out = J.out_buf ? a.ap_sl + int64_t(v) * a.ap_sl_vs : a.op_sl;
-        const int64_t tile_elems = int64_t(J.rows_tile) * SPL_TK;
+        for (int vv = 0; vv < 8; ++vv) E[vv] = vv < nv ? a.op_ex[J.out_exp + 8 * T.vg + vv] : 0;
         const int vt = (8 * T.vg) / J.rows_tile, rg = ((8 * T.vg) % J.rows_tile) >> 3;
-        const int kt0 = T.k0 / SPL_TK;
-        const int nkt = min(SPL_TILE_K / SPL_TK, J.kt - kt0);
-        for (int kt = 0; kt < nkt; ++kt) {
-            const int K = T.k0 + kt * SPL_TK + lane;
+        const int nsub = min(SPL_TILE_K / 32, (J.kt * SPL_TK - T.k0 + 31) / 32);
+        for (int sb = 0; sb < nsub; ++sb) {
+            const int K = T.k0 + sb * 32 + lane;
             int d[8][SPL_S];
 #pragma unroll
             for (int vv = 0; vv < 8; ++vv)
 #pragma unroll
                 for (int q = 0; q < SPL_S; ++q) d[vv][q] = 0;
             if (K < J.K) {
-                int sg = T.seg;   // holds the tile's first K; later runs follow in order
+                int sg = T.seg;   // holds the item's first K; later runs follow in order
                 while (sg < J.seg0 + J.nseg - 1 && K >= a.segs[sg + 1].kbase) ++sg;
                 const SSeg g = a.segs[sg];
-                const int kb = g.kbase;
-                const int t = (K - kb) / g.kc, k = (K - kb) - t * g.kc;
-                const int64_t base = g.off + t * g.ts + k * g.ks;
-                int vg = (8 * T.vg) / g.vper, vr = 8 * T.vg - vg * g.vper;
-                if (g.is_i64) {   // loads first, then the integer digit arithmetic
-                    const int64_t* s1 = a.s1 + int64_t(v) * a.s1_vs;
-                    const int32_t* cex = a.ap_ex + int64_t(v) * a.ap_ex_vs + g.ec_off + k;
-                    const int32_t* er = a.op_ex + g.er_off + int64_t(t) * g.er_ts;
-                    long long F[8];
-                    int e[8];
+                const int t = (K - g.kbase) / g.kcp, k = (K - g.kbase) - t * g.kcp;
+                if (k < g.kc) {
+                    const int64_t base = g.off + t * g.ts + k * g.ks;
+                    int vg = (8 * T.vg) / g.vper, vr = 8 * T.vg - vg * g.vper;
+                    double xv[8];
 #pragma unroll
                     for (int vv = 0; vv < 8; ++vv) {
-                        F[vv] = vv < nv ? s1[base + vg * g.vgs + int64_t(vr) * g.vs] : 0;
-                        e[vv] = vv < nv ? er[vr] + cex[int64_t(vg) * g.ec_vgs] - g.e_off : 0;
+                        xv[vv] = vv < nv ? a.ops[base + vg * g.vgs + int64_t(vr) * g.vs] : 0.0;
                         if (++vr == g.vper) {
                             vr = 0;
                             ++vg;
@@ -316,37 +277,104 @@ __global__ void __launch_bounds__(32 * DIG_WARPS) k_slice_digits(TileArgs a) {
                     }
 #pragma unroll
                     for (int vv = 0; vv < 8; ++vv)
-                        if (F[vv] != 0) digits_i64(F[vv], e[vv], E[vv], d[vv]);
-                } else {
-                    const double* src = g.space == SP_OPS ? a.ops : a.x + int64_t(v) * a.x_vs;
-                    double xv[8];
-#pragma unroll
-                    for (int vv = 0; vv < 8; ++vv) {
-                        xv[vv] = vv < nv ? src[base + vg * g.vgs + int64_t(vr) * g.vs] : 0.0;
-                        if (++vr == g.vper) {
-                            vr = 0;
-                            ++vg;
-                        }
-                    }
-#pragma unroll
-                    for (int vv = 0; vv < 8; ++vv) digits_f64(xv[vv], E[vv], d[vv]);
+                        if (vv < nv) digits_f64(xv[vv], E[vv], d[vv]);
                 }
             }
 #pragma unroll
             for (int vv = 0; vv < 8; ++vv)
 #pragma unroll
                 for (int q = 0; q < SPL_S; ++q) sd[q][vv][lane] = digit_bf16(d[vv][q], q);
-            __syncwarp();
-            // lane -> core matrix kg = lane / 8 (K [8 kg, +8)), row vv = lane % 8
-            const int kg = lane >> 3, vv = lane & 7;
+            if (J.top_sums) {   // sum |d_0| per row for the estimate pass (exact integers)
 #pragma unroll
-            for (int q = 0; q < SPL_S; ++q) {
-                const int64_t dst = J.out_tiles + ((int64_t(vt) * J.kt + kt0 + kt) * SPL_S + q) * tile_elems +
-                                    (rg * 4 + kg) * 64 + vv * 8;
-                *reinterpret_cast<uint4*>(out + dst) = *reinterpret_cast<const uint4*>(&sd[q][vv][kg * 8]);
+                for (int vv = 0; vv < 8; ++vv) {
+                    int t0 = abs(d[vv][0]);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+                    if (lane == 0 && vv < nv && t0 != 0) atomicAdd(a.srow + J.out_exp + 8 * T.vg + vv, t0);
+                }
             }
             __syncwarp();
+            store_digit_block(sd, a.op_sl, J, vt, rg, T.k0 / SPL_TK + sb * 2, lane);
+            __syncwarp();
         }
+    }
+}
+
+// ----------------------------------------------------------------------------------
+// psi operands (per apply)
+
+struct XArgs {
+    const SXJob* xjobs;
+    const SJob* jobs;
+    const double* x;
+    int64_t dim;
+    uint16_t* ap_sl;
+    int32_t* ap_ex;
+    float* xs;
+    int64_t* s2;
+    int64_t s2_len;
+    int64_t mid0, mid1;   // exponents of the stage-2 intermediate vectors (reset to none)
+};
+
+// One CTA per (psi job, Davidson vector): pass 1, one warp per vector (a column or a
+// row of the block), the exact exponent E and the estimate pass's term 1.005 2^-8
+// sum |x| 2^-E (rounded up); pass 2, the digits of 8 vectors x 32 K per warp item,
+// written as the 16-byte chunks of two 16-K tiles.  The grid also clears the stage-2
+// sums and resets the stage-2 vector bounds to "none".
+__global__ void __launch_bounds__(256) k_xprep(XArgs a) {
+    __shared__ __align__(16) uint16_t sd_all[8][SPL_S][8][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    {
+        const int64_t nthr = int64_t(gridDim.x) * gridDim.y * blockDim.x;
+        const int64_t t0 = (int64_t(blockIdx.y) * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
+        for (int64_t i = t0; i < a.s2_len; i += nthr) a.s2[i] = 0;
+        for (int64_t i = a.mid0 + t0; i < a.mid1; i += nthr) a.ap_ex[i] = SPL_EXP_NONE;
+    }
+    const SXJob X = a.xjobs[blockIdx.x];
+    const SJob J = a.jobs[X.job];
+    const int v = blockIdx.y;
+    const double* src = a.x + int64_t(v) * a.dim + X.off;
+    int32_t* ex = a.ap_ex + J.out_exp + int64_t(v) * X.cp;
+    float* xs = a.xs + J.out_exp + int64_t(v) * X.cp;
+    for (int k = warp; k < X.cp; k += 8) {
+        int E = INT_MIN;
+        if (k < X.nk)
+            for (int K = lane; K < X.K; K += 32) E = max(E, exp_f64(src[int64_t(K) * X.ks + int64_t(k) * X.vs]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+        double s1 = 0.0;
+        if (E != INT_MIN) {
+            for (int K = lane; K < X.K; K += 32) s1 += fabs(scalbn(src[int64_t(K) * X.ks + int64_t(k) * X.vs], -E));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        }
+        if (lane == 0) {
+            ex[k] = E == INT_MIN ? SPL_EXP_NONE : E;
+            // the sum's rounding (relative 2^-40 at most) is covered by the 1.005 factor
+            xs[k] = __double2float_ru(s1 * (1.005 / 256.0));
+        }
+    }
+    __syncthreads();   // the exponents written above are visible to the whole CTA
+    uint16_t (*sd)[8][32] = sd_all[warp];
+    const int ngrp = X.cp / 8, nsub = (X.K + 31) / 32;
+    for (int it = warp; it < ngrp * nsub; it += 8) {
+        const int g8 = it / nsub, sb = it - g8 * nsub;
+        const int K = sb * 32 + lane;
+#pragma unroll
+        for (int vv = 0; vv < 8; ++vv) {
+            const int k = 8 * g8 + vv;
+            int d[SPL_S] = {0, 0, 0, 0, 0, 0};
+            if (K < X.K && k < X.nk) {
+                const int E = ex[k];
+                if (E != SPL_EXP_NONE) digits_f64(src[int64_t(K) * X.ks + int64_t(k) * X.vs], E, d);
+            }
+#pragma unroll
+            for (int q = 0; q < SPL_S; ++q) sd[q][vv][lane] = digit_bf16(d[q], q);
+        }
+        __syncwarp();
+        const int n0 = v * X.cp + 8 * g8;   // job vector of this group's first vector
+        store_digit_block(sd, a.ap_sl, J, n0 / J.rows_tile, (n0 % J.rows_tile) >> 3, sb * 2, lane);
+        __syncwarp();
     }
 }
 
@@ -356,17 +384,19 @@ __global__ void __launch_bounds__(32 * DIG_WARPS) k_slice_digits(TileArgs a) {
 __device__ __forceinline__ uint32_t su32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
 
 // Shared-memory matrix descriptor, K-major without swizzle: 8x8 core matrices of 128
-// contiguous bytes, LBO = 128 B between K-adjacent cores, SBO = 512 B between 8-row groups.
-// The low word holds the start address (bits 0-13, address / 16) and LBO / 16 (bits
-// 16-29); the high word SBO / 16 (bits 32-45) and the fixed version bit 46.  Every
-// operand of a stage sits below 256 KB of shared memory, so operand offsets are added to
-// the low word without a carry out of the address field.
+// contiguous bytes, LBO = 128 B between the two K-adjacent cores of a 16-K tile, SBO =
+// 256 B between 8-row groups.  The low word holds the start address (bits 0-13, address
+// / 16) and LBO / 16 (bits 16-29); the high word SBO / 16 (bits 32-45) and the fixed
+// version bit 46.  Every operand of a stage sits below 256 KB of shared memory, so
+// operand offsets are added to the low word without a carry out of the address field.
 __device__ __forceinline__ uint32_t sdesc_lo(uint32_t addr) { return ((addr >> 4) & 0x3FFF) | ((128u >> 4) << 16); }
-constexpr uint32_t UM_DESC_HI = (512u >> 4) | (1u << (46 - 32));
+constexpr uint32_t UM_DESC_HI = (256u >> 4) | (1u << (46 - 32));
 
-// Instruction descriptor of kind::f16: BF16 x BF16 -> FP32, both K-major, M=128, N=64.
-constexpr uint32_t UM_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(SPL_TN >> 3) << 17) |
-                              (uint32_t(SPL_TM >> 4) << 24);
+// Instruction descriptor of kind::f16: BF16 x BF16 -> FP32, both K-major, M=128, N=n
+// (a multiple of 16 up to SPL_TN).
+__host__ __device__ constexpr uint32_t um_idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(SPL_TM >> 4) << 24);
+}
 
 __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t ph) {
     uint32_t ok;
@@ -380,18 +410,24 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t ph) {
 
 // Bounded wait; false on timeout (recorded in *abort and the status word) or when
 // another role of the CTA has aborted.
+// The abort flag and the clock are looked at only every 16th poll: the flag lives in
+// shared memory, whose bandwidth the tensor cores' operand reads need, and twelve
+// epilogue warps wait at once.
 __device__ __forceinline__ bool mbar_wait_limit(uint64_t* b, uint32_t ph, long long limit, volatile int* abort,
                                                 int* status) {
+    if (mbar_try(b, ph)) return true;
     const long long t0 = clock64();
-    while (!mbar_try(b, ph)) {
-        if (*abort) return false;
-        if (clock64() - t0 > limit) {
-            *abort = 1;
-            atomicExch(status, DMRG_ERR_DEVICE_TIMEOUT);
-            return false;
+    for (unsigned n = 1;; ++n) {
+        if (mbar_try(b, ph)) return true;
+        if ((n & 15u) == 0) {
+            if (*abort) return false;
+            if (clock64() - t0 > limit) {
+                *abort = 1;
+                atomicExch(status, DMRG_ERR_DEVICE_TIMEOUT);
+                return false;
+            }
         }
     }
-    return true;
 }
 
 __device__ __forceinline__ bool mbar_wait(UmmaSmem& sm, uint64_t* b, uint32_t ph, int* status) {
@@ -420,11 +456,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  "l"(src), "r"(bytes), "r"(su32(b))
                  : "memory");
 }
-__device__ __forceinline__ void umma(uint32_t d, uint32_t a_lo, uint32_t b_lo, uint32_t accumulate) {
+__device__ __forceinline__ void umma(uint32_t d, uint32_t a_lo, uint32_t b_lo, uint32_t accumulate, uint32_t idesc) {
     asm volatile(
         "{\n.reg .pred p;\n.reg .b64 da, db;\nsetp.ne.b32 p, %3, 0;\nmov.b64 da, {%1, %4};\nmov.b64 db, {%2, %4};\n"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n}\n" ::"r"(d),
-        "r"(a_lo), "r"(b_lo), "r"(accumulate), "r"(UM_DESC_HI), "r"(UM_IDESC));
+        "r"(a_lo), "r"(b_lo), "r"(accumulate), "r"(UM_DESC_HI), "r"(idesc));
 }
 __device__ __forceinline__ void umma_commit(uint64_t* b) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
@@ -433,10 +469,15 @@ __device__ __forceinline__ void umma_commit(uint64_t* b) {
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&r)[8]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(addr));
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(addr));
 }
 
 // Work list of one slice-GEMM launch (the Davidson vectors of an apply are stacked
@@ -446,50 +487,181 @@ struct UmmaArgs {
     int64_t n_work;
     const SGemm* gemms;
     const uint16_t* op_sl;
-    const uint16_t* ap_sl;
-    int64_t* s1;
+    uint16_t* ap_sl;
     int64_t* s2;
     const int32_t* op_ex;
     int32_t* ap_ex;
     int* status;
 };
 
-// The 42 MMAs of one K tile (two K=16 steps x 21 slice pairs), fully unrolled so that
-// each costs two 32-bit adds besides the MMA itself.  Order: K step, then level
-// l = i + j, then i (consecutive MMAs mostly feed different accumulators; a run into one
-// accumulator stalls on its own sum).  Level l feeds accumulator c = min(l, 4) in the
-// chunk's TMEM slot.  first: the tile opens drain chunk `chunk`, so the first pair of
-// every accumulator overwrites it, once the epilogue has emptied the slot (tempty).
-// last: the tile closes the chunk and hands its accumulators to the epilogue (tfull);
-// the next chunk waits only for accumulators 0 and 1 to be read.
-__device__ __forceinline__ bool umma_ktile(UmmaSmem& sm, uint32_t tmem, uint32_t la, uint32_t ra, bool first,
-                                           bool last, int64_t chunk, int* status) {
-    const uint32_t a0 = sdesc_lo(la), b0 = sdesc_lo(ra);
+// Issue order of the 21 slice pairs (i, j) of a 16-K tile: accumulator c (pair level c
+// for c < 4, levels 4 and 5 for c = 4) alternates with the others, so that consecutive
+// MMAs never feed the same accumulator (a run into one accumulator stalls on its own
+// sum), and the first use of each accumulator follows the order 4, 3, 2, 1, 0 in which
+// the epilogue empties them.
+#define UM_ORDER_C {4, 3, 4, 2, 4, 3, 4, 1, 4, 2, 4, 3, 4, 0, 4, 1, 4, 2, 4, 3, 4}
+#define UM_ORDER_I {0, 0, 1, 0, 2, 1, 3, 0, 4, 1, 0, 2, 1, 0, 2, 1, 3, 2, 4, 3, 5}
+#define UM_ORDER_J {4, 3, 3, 2, 2, 2, 1, 1, 0, 1, 5, 1, 4, 0, 3, 0, 2, 0, 1, 0, 0}
+
+// Drain schedule: every accumulator is emptied after item-relative K tile kt when the
+// tile closes a chunk of 16 tiles (256 K, the limit of the exact levels) or the work
+// item.  Stage-2 items start at multiples of 16 tiles, so the rounding points of the
+// inexact accumulator 4 (and hence the result) do not depend on how a stage-2 GEMM is cut
+// into items.  (Staggering the five accumulators' chunk ends was measured slower: the
+// MMAs of the accumulator whose chunk starts had to run back to back, and consecutive
+// MMAs into one accumulator stall on its sum.)
+__host__ __device__ __forceinline__ bool um_drains(int kt, int len) {
+    return kt == len - 1 || kt % SPL_DRAIN_KT == SPL_DRAIN_KT - 1;
+}
+
+// The 21 MMAs of one 16-K tile, fully unrolled.  OPEN < 0: every accumulator keeps
+// accumulating.  OPEN = 5: the tile starts a chunk, and each accumulator waits for its
+// own drain (tempty) before its first pair, which overwrites it; the issue order makes
+// these waits follow the order 4, 3, 2, 1, 0 of the epilogue.  nd[c] counts the drains of
+// accumulator c so far in this CTA.
+template <int OPEN>
+__device__ __forceinline__ bool issue_tile(UmmaSmem& sm, uint32_t tmem, uint32_t a0, uint32_t b0, uint32_t idesc,
+                                           const int (&nd)[SPL_ACCS], int* status) {
+    constexpr int oc[SPL_PAIRS] = UM_ORDER_C, oi[SPL_PAIRS] = UM_ORDER_I, oj[SPL_PAIRS] = UM_ORDER_J;
 #pragma unroll
-    for (int ks = 0; ks < 2; ++ks)
+    for (int p = 0; p < SPL_PAIRS; ++p) {
+        const int c = oc[p];
+        bool first = OPEN == SPL_ACCS;
 #pragma unroll
-        for (int l = 0; l < SPL_S; ++l) {
-            const int c = l < SPL_ACCS - 1 ? l : SPL_ACCS - 1;
-            const int slot = um_slot(c, chunk);
-            if (first && ks == 0 && l == c) {   // previous use of the slot: chunk - 1 or chunk - 2
-                const uint32_t use = um_use(c, chunk);
-                if (use > 0) {
-                    if (!mbar_wait(sm, &sm.tempty[slot], (use - 1) & 1, status)) return false;
-                    tc_fence_after();
-                }
-            }
-#pragma unroll
-            for (int i = 0; i <= l; ++i) {
-                const int j = l - i;
-                const uint32_t accumulate = (first && ks == 0 && i == 0 && l == c) ? 0u : 1u;
-                umma(tmem + uint32_t(slot) * SPL_TN, a0 + uint32_t(i * (SPL_LT * 2) + ks * 256) / 16,
-                     b0 + uint32_t(j * (SPL_RT * 2) + ks * 256) / 16, accumulate);
-            }
+        for (int p2 = 0; p2 < p; ++p2)
+            if (oc[p2] == c) first = false;
+        if (first && nd[c] > 0) {
+            if (!mbar_wait(sm, &sm.tempty[c], uint32_t((nd[c] - 1) & 1), status)) return false;
+            tc_fence_after();
         }
-    if (last)
-#pragma unroll
-        for (int c = 0; c < SPL_ACCS; ++c) umma_commit(&sm.tfull[um_slot(c, chunk)]);
+        umma(tmem + uint32_t(c * SPL_TN), a0 + uint32_t(oi[p] * (SPL_LT * 2)) / 16,
+             b0 + uint32_t(oj[p] * (SPL_RT * 2)) / 16, first ? 0u : 1u, idesc);
+    }
     return true;
+}
+
+// Drain of accumulator c into the int64 sums acc (units of 2^-31 of the digit-product
+// unit).  32-bit conversions only (the 64-bit one is an FP64-rate operation): acc c holds
+// the exact level sum in units of 2^(-8c) for c < 4 (|sum| <= (c+1) 2^22 in those units),
+// acc 4 the rest, rounded to units of 2^-31 (< 2^24 of them); each is added in units of
+// 2^-31, a chunk's total staying below 2^53.01 and a work item's (at most 8192 K) below
+// 2^58.01.  The accumulator is handed back to the MMA issuer as soon as it is in
+// registers.  n: the drains of accumulator c before this one.
+template <int c>
+__device__ __forceinline__ bool drain_acc(UmmaSmem& sm, uint32_t tmem_row, int col0, int n,
+                                          long long (&acc)[UM_EPI_COLS], int* status) {
+    // warp-uniform outcome: the TMEM loads below are .sync.aligned
+    if (!__all_sync(0xffffffffu, mbar_wait(sm, &sm.tfull[c], uint32_t(n & 1), status))) return false;
+    tc_fence_after();
+    uint32_t rv[UM_EPI_COLS];
+    tmem_ld32(tmem_row + uint32_t(c * SPL_TN + col0), rv);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    tc_fence_before();
+    mbar_arrive(&sm.tempty[c]);
+    constexpr float scale = c == 0 ? 1.0f : c == 1 ? 256.0f : c == 2 ? 65536.0f : c == 3 ? 16777216.0f : 2147483648.0f;
+#pragma unroll
+    for (int j = 0; j < UM_EPI_COLS; ++j) {
+        const int iv = __float2int_rn(__uint_as_float(rv[j]) * scale);
+        if constexpr (c < SPL_ACCS - 1)
+            acc[j] += static_cast<long long>(iv) * (1ll << (31 - 8 * c));
+        else
+            acc[j] += iv;
+    }
+    return true;
+}
+
+// The exponents the stage-1 epilogue needs, loaded before the drain so that no global
+// load sits between the drain and the stores: the psi vector exponents of the warp's 32
+// columns (lane l holds column cbase + l), the row's operator exponent and the bound of
+// the stage-2 vector of each group of 8 columns.
+struct S1Pre { int ec_lane, erow, E[UM_EPI_COLS / 8]; };
+
+__device__ __forceinline__ S1Pre stage1_prefetch(const UmmaArgs& a, const SGemm& G, int r, int cbase, int lane) {
+    S1Pre p;
+    p.ec_lane = cbase + lane < G.N ? a.ap_ex[G.ec_off + cbase + lane] : 0;
+    p.erow = 0;
+#pragma unroll
+    for (int g = 0; g < UM_EPI_COLS / 8; ++g) p.E[g] = SPL_EXP_NONE;
+    if (r < G.M) {
+        p.erow = a.op_ex[G.er_off + r];
+        const int i = r % G.per;
+#pragma unroll
+        for (int g = 0; g < UM_EPI_COLS / 8; ++g) {
+            const int col = cbase + 8 * g;
+            if (col < G.N) p.E[g] = a.ap_ex[G.dst_exp + (col / G.cp) * G.per + i];
+        }
+    }
+    return p;
+}
+
+// Stage-1 epilogue: this thread's row of the tile and its 32 columns (4 groups of 8; a
+// group lies inside one Davidson vector because cp is a multiple of 8) -> 6 digits per
+// entry relative to the stage-2 vector bound, stored as 16-byte chunks (8 K of one
+// slice) straight into the stage-2 job's tiles.
+__device__ __forceinline__ void stage1_store(const UmmaArgs& a, const SGemm& G, int r, int cbase, const S1Pre& pre,
+                                             const long long (&acc)[UM_EPI_COLS]) {
+    const bool rv = r < G.M;
+    const int t = rv ? r / G.per : 0, i = rv ? r - t * G.per : 0;
+    const int erow = pre.erow;
+    const int ec_lane = pre.ec_lane;
+    int vprev = -1, E = SPL_EXP_NONE;
+    int64_t tile_base = 0;
+    int vr = 0;
+    const int64_t tile_elems = int64_t(SPL_S) * G.dst_rows_tile * SPL_TK;
+#pragma unroll
+    for (int g = 0; g < UM_EPI_COLS / 8; ++g) {
+        const int col = cbase + 8 * g;   // the same for every lane
+        int ec[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) ec[e] = __shfl_sync(0xffffffffu, ec_lane, 8 * g + e);
+        if (!rv || col >= G.N) continue;
+        const int v = col / G.cp, k0 = col - v * G.cp;
+        E = pre.E[g];   // bound from the estimate pass
+        if (v != vprev) {
+            vprev = v;
+            const int V = v * G.per + i;
+            const int vt = V / G.dst_rows_tile;
+            vr = V - vt * G.dst_rows_tile;
+            tile_base = G.d_off + int64_t(vt) * G.dst_kt * tile_elems;
+        }
+        const int K0 = G.kbase + t * G.cp + k0;
+        unsigned long long Rb[8];
+        uint32_t sgn[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const long long F = G.sign > 0 ? acc[8 * g + e] : -acc[8 * g + e];
+            unsigned long long R = 0;
+            if (F != 0) {
+                const unsigned long long u =
+                    F < 0 ? static_cast<unsigned long long>(-F) : static_cast<unsigned long long>(F);
+                // value = F 2^(erow + ec - 45) < 2^E; R = round(|value| 2^(47 - E)) = round(|F| 2^-sh)
+                // (the bound keeps sh > -47; the clamp only keeps shifts defined)
+                const int sh = E - erow - ec[e] - 2;
+                R = sh > 0 ? (sh >= 64 ? 0ull : (u + (1ull << (sh - 1))) >> sh) : (sh > -64 ? u << (-sh) : 0ull);
+            }
+            Rb[e] = R + 0x7F7F7F7F7F7Full;
+            sgn[e] = F < 0 ? 0x80000000u : 0u;
+        }
+        const int kt = K0 >> 4, kh = (K0 >> 3) & 1;
+        uint4* dst = reinterpret_cast<uint4*>(a.ap_sl + tile_base + int64_t(kt) * tile_elems +
+                                              ((vr >> 3) * 2 + kh) * 64 + (vr & 7) * 8);
+        const int64_t qstride = int64_t(G.dst_rows_tile) * SPL_TK / 8;   // one slice, in 16-byte units
+        auto put = [&](auto kc) {
+            constexpr int q = decltype(kc)::value;
+            uint32_t w[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+                w[p] = __byte_perm(digit_float<q>(Rb[2 * p]) ^ sgn[2 * p], digit_float<q>(Rb[2 * p + 1]) ^ sgn[2 * p + 1],
+                                   0x7632);
+            dst[q * qstride] = make_uint4(w[0], w[1], w[2], w[3]);
+        };
+        put(std::integral_constant<int, 0>{});
+        put(std::integral_constant<int, 1>{});
+        put(std::integral_constant<int, 2>{});
+        put(std::integral_constant<int, 3>{});
+        put(std::integral_constant<int, 4>{});
+        put(std::integral_constant<int, 5>{});
+    }
 }
 
 __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
@@ -514,7 +686,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
             mbar_init(&sm.full[s], 1);
             mbar_init(&sm.empty[s], 1);
         }
-        for (int c = 0; c < UM_SLOTS; ++c) {
+        for (int c = 0; c < SPL_ACCS; ++c) {
             mbar_init(&sm.tfull[c], 1);
             mbar_init(&sm.tempty[c], 32 * UM_EPI_WARPS);
         }
@@ -551,12 +723,12 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
             const uint16_t* Lb = (G.l_buf ? a.ap_sl : a.op_sl) + G.l_tiles;
             const uint16_t* Rb = (G.r_buf ? a.ap_sl : a.op_sl) + G.r_tiles;
             // only the 8-row groups that hold rows of the GEMM are copied: the first lg (rg)
-            // 512-byte groups of every slice; the rest of the stage keeps digits of an
+            // 256-byte groups of every slice; the rest of the stage keeps digits of an
             // earlier tile (or the zeros of set-up), whose products land in accumulator
             // rows / columns that the epilogue never reads
             const int lg = (min(SPL_TM, G.M - W.mtile * SPL_TM) + 7) >> 3;
             const int rg = (min(SPL_TN, G.N - W.ntile * SPL_TN) + 7) >> 3;
-            const uint32_t lbytes = uint32_t(lg) * 512u, rbytes = uint32_t(rg) * 512u;
+            const uint32_t lbytes = uint32_t(lg) * 256u, rbytes = uint32_t(rg) * 256u;
             for (int kt = W.k0; kt < W.k1; ++kt, ++kidx) {
                 const int s = int(kidx % UM_STAGES);
                 const int64_t n = kidx / UM_STAGES;
@@ -581,23 +753,43 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
             if (q >= 0) mbar_wait_final(&sm.full[q % UM_STAGES], uint32_t((q / UM_STAGES) & 1));
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer
-        int64_t kidx = 0, dchunk = 0;
+        int64_t kidx = 0;
+        int nd[SPL_ACCS] = {0, 0, 0, 0, 0};
         bool ok = true;
         SWork Wn{};
-        if (blockIdx.x < total) Wn = a.work[blockIdx.x];
+        SGemm Gn{};
+        if (blockIdx.x < total) {
+            Wn = a.work[blockIdx.x];
+            Gn = a.gemms[Wn.gemm];
+        }
         for (int64_t it = blockIdx.x; it < total && ok; it += step) {
             const SWork W = Wn;
-            if (it + step < total) Wn = a.work[it + step];
-            for (int kc0 = W.k0; kc0 < W.k1 && ok; kc0 += SPL_DRAIN_KT, ++dchunk) {
-                const int kc1 = min(kc0 + SPL_DRAIN_KT, W.k1);
-                for (int kt = kc0; kt < kc1; ++kt, ++kidx) {
-                    const int s = int(kidx % UM_STAGES);
-                    if (!(ok = mbar_wait(sm, &sm.full[s], uint32_t((kidx / UM_STAGES) & 1), a.status))) break;
-                    tc_fence_after();
-                    if (!(ok = umma_ktile(sm, tmem, su32(sm.L[s]), su32(sm.R[s]), kt == kc0, kt == kc1 - 1, dchunk,
-                                          a.status)))
-                        break;
-                    umma_commit(&sm.empty[s]);
+            // the MMA's N: the tile's valid columns rounded up to 16
+            const int ncols = min(SPL_TN, Gn.N - W.ntile * SPL_TN);
+            const uint32_t idesc = um_idesc((ncols + 15) & ~15);
+            if (it + step < total) {
+                Wn = a.work[it + step];
+                Gn = a.gemms[Wn.gemm];
+            }
+            const int len = W.k1 - W.k0;
+            for (int kt = 0; kt < len; ++kt, ++kidx) {
+                const int s = int(kidx % UM_STAGES);
+                if (!(ok = mbar_wait(sm, &sm.full[s], uint32_t((kidx / UM_STAGES) & 1), a.status))) break;
+                tc_fence_after();
+                const uint32_t a0 = sdesc_lo(su32(sm.L[s])), b0 = sdesc_lo(su32(sm.R[s]));
+                // a chunk's first tile: every accumulator starts over
+                if (kt == 0 || um_drains(kt - 1, len))
+                    ok = issue_tile<SPL_ACCS>(sm, tmem, a0, b0, idesc, nd, a.status);
+                else
+                    ok = issue_tile<-1>(sm, tmem, a0, b0, idesc, nd, a.status);
+                if (!ok) break;
+                umma_commit(&sm.empty[s]);
+                if (um_drains(kt, len)) {
+#pragma unroll
+                    for (int c = SPL_ACCS - 1; c >= 0; --c) {
+                        umma_commit(&sm.tfull[c]);
+                        ++nd[c];
+                    }
                 }
             }
         }
@@ -605,11 +797,234 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
         mbar_wait_final(&sm.done, 0);
     } else if (warp >= 2) {
         // ---- epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (tile rows) and the column
-        // half (w-2)/4 of every accumulator
+        // third (w-2)/4 of every accumulator
         const int q = warp & 3, h = (warp - 2) >> 2;
         const int row = 32 * q + lane, col0 = h * UM_EPI_COLS;
-        const uint32_t lane_addr = uint32_t(32 * q) << 16;
-        int64_t dchunk = 0;
+        const uint32_t tmem_row = tmem + (uint32_t(32 * q) << 16);
+        int nd[SPL_ACCS] = {0, 0, 0, 0, 0};
+        bool ok = true;
+        // the next work item is loaded ahead; its GEMM descriptor is read at the item's
+        // start, while the first drain waits for the MMAs
+        SWork W1{};
+        if (blockIdx.x < total) W1 = a.work[blockIdx.x];
+        for (int64_t it = blockIdx.x; it < total && ok; it += step) {
+            const SWork W = W1;
+            if (it + step < total) W1 = a.work[it + step];
+            const int r = W.mtile * SPL_TM + row;
+            const int cbase = W.ntile * SPL_TN + col0;
+            // stage 1: the exponents of the epilogue, loaded before the drain (the GEMM
+            // descriptor is read again after it, from L1)
+            S1Pre pre{};
+            {
+                const SGemm G0 = a.gemms[W.gemm];
+                if (G0.kind == 0) pre = stage1_prefetch(a, G0, r, cbase, lane);
+            }
+            long long acc[UM_EPI_COLS];
+#pragma unroll
+            for (int j = 0; j < UM_EPI_COLS; ++j) acc[j] = 0;
+            const int len = W.k1 - W.k0;
+            for (int kt = 0; kt < len && ok; ++kt) {
+                if (!um_drains(kt, len)) continue;
+                ok = drain_acc<4>(sm, tmem_row, col0, nd[4], acc, a.status) &&
+                     drain_acc<3>(sm, tmem_row, col0, nd[3], acc, a.status) &&
+                     drain_acc<2>(sm, tmem_row, col0, nd[2], acc, a.status) &&
+                     drain_acc<1>(sm, tmem_row, col0, nd[1], acc, a.status) &&
+                     drain_acc<0>(sm, tmem_row, col0, nd[0], acc, a.status);
+#pragma unroll
+                for (int c = 0; c < SPL_ACCS; ++c) ++nd[c];
+            }
+            if (!ok) break;
+            const SGemm G = a.gemms[W.gemm];
+            if (G.kind == 0) {
+                stage1_store(a, G, r, cbase, pre, acc);
+            } else if (r < G.M) {
+                // F = round(2^fs * sum): exact for fs >= 31 (up to 32 drains of 2^53.01 stay
+                // below 2^58.01; the GEMM's shift keeps F below 2^62); for fs < 31 only the
+                // part below 2^-fs, i.e. of acc 4, is rounded
+                const int fs = G.fshift;
+                unsigned long long* D = reinterpret_cast<unsigned long long*>(a.s2 + G.d_off + int64_t(r) * G.ldd);
+#pragma unroll
+                for (int j = 0; j < UM_EPI_COLS; ++j) {
+                    const long long F = fs >= 31
+                                            ? static_cast<long long>(static_cast<unsigned long long>(acc[j]) << (fs - 31))
+                                            : (acc[j] + (1ll << (30 - fs))) >> (31 - fs);
+                    const int c = cbase + j;
+                    if (c < G.N && F != 0) atomicAdd(D + c, static_cast<unsigned long long>(F));
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UM_TMEM_COLS));
+    }
+}
+
+// ----------------------------------------------------------------------------------
+// estimate pass: the stage-2 vector bounds
+
+constexpr int EST_KT = 4;          // K tiles per stage (slice 0 of each)
+constexpr int EST_STAGES = 6;
+constexpr int EST_DRAIN_KT = 64;   // level-0 sums stay exact integers below 2^24 for 1024 K
+constexpr int EST_TMEM_COLS = 256; // two accumulator slots of SPL_TN columns
+struct EstSmem {
+    uint16_t L[EST_STAGES][EST_KT * SPL_LT];
+    uint16_t R[EST_STAGES][EST_KT * SPL_RT];
+    uint64_t full[EST_STAGES], empty[EST_STAGES], tfull[2], tempty[2], done;
+    uint32_t tmem_base;
+    volatile int abort;
+};
+static_assert(sizeof(EstSmem) <= 232448, "estimate pass shared memory");
+static_assert(2 * SPL_TN <= EST_TMEM_COLS, "estimate accumulators");
+
+struct EstArgs {
+    const SWork* work;
+    int64_t n_work;
+    const SGemm* gemms;
+    const uint16_t* op_sl;
+    const uint16_t* ap_sl;
+    const int32_t* op_ex;
+    int32_t* ap_ex;
+    const int32_t* srow;
+    const float* xs;
+    int* status;
+};
+
+__device__ __forceinline__ bool est_wait(EstSmem& sm, uint64_t* b, uint32_t ph, int* status) {
+    return mbar_wait_limit(b, ph, UM_WAIT_CYCLES, &sm.abort, status);
+}
+
+// Over the stage-1 work list: the top-digit product X~ = sum a~ x~ (slice pair (0, 0),
+// one MMA per 16-K tile, exact integer sums drained every 1024 K into two alternating
+// TMEM slots), then per entry the bound
+//     |X| < 2^(E_a + E_x) f,  f = |X~| 2^-(E_a+E_x) + 1.005 2^-8 (sum|x| 2^-E_x + sum|a~| 2^-E_a)
+// (enlarged by 2^-20 relative and 2^-30 absolute for the rounding of f and of the
+// stage-1 result), and each stage-2 vector's bound exponent is raised to the largest
+// E_a + E_x + ceil(log2 f) of its entries with an integer atomicMax.
+__global__ void __launch_bounds__(UM_THREADS, 1) k_uest(EstArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    EstSmem& sm = *reinterpret_cast<EstSmem*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&sm.tmem_base)),
+                     "r"(EST_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    {
+        uint4* z = reinterpret_cast<uint4*>(&sm.L[0][0]);
+        constexpr int n16 = int((sizeof(sm.L) + sizeof(sm.R)) / 16);
+        static_assert(offsetof(EstSmem, R) == sizeof(EstSmem::L), "stages are contiguous");
+        for (int i = threadIdx.x; i < n16; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < EST_STAGES; ++s) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.empty[s], 1);
+        }
+        for (int c = 0; c < 2; ++c) {
+            mbar_init(&sm.tfull[c], 1);
+            mbar_init(&sm.tempty[c], 32 * UM_EPI_WARPS);
+        }
+        mbar_init(&sm.done, 1);
+        sm.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem_base;
+    const int64_t total = a.n_work;
+    const int64_t step = gridDim.x;
+
+    if (warp == 0 && lane == 0) {
+        // ---- producer: slice 0 of EST_KT K tiles of L and R per stage
+        int64_t sidx = 0;
+        bool ok = true;
+        // descriptors loaded ahead, as in the slice GEMM: no dependent global load at an
+        // item boundary (the items of this pass are short)
+        SWork W1{}, W2{};
+        SGemm G1{};
+        if (blockIdx.x < total) {
+            W1 = a.work[blockIdx.x];
+            G1 = a.gemms[W1.gemm];
+        }
+        if (blockIdx.x + step < total) W2 = a.work[blockIdx.x + step];
+        for (int64_t it = blockIdx.x; it < total && ok; it += step) {
+            const SWork W = W1;
+            const SGemm G = G1;
+            W1 = W2;
+            if (it + step < total) G1 = a.gemms[W1.gemm];
+            if (it + 2 * step < total) W2 = a.work[it + 2 * step];
+            const uint16_t* Lb = (G.l_buf ? a.ap_sl : a.op_sl) + G.l_tiles;
+            const uint16_t* Rb = (G.r_buf ? a.ap_sl : a.op_sl) + G.r_tiles;
+            const int lg = (min(SPL_TM, G.M - W.mtile * SPL_TM) + 7) >> 3;
+            const int rg = (min(SPL_TN, G.N - W.ntile * SPL_TN) + 7) >> 3;
+            for (int kt0 = W.k0; kt0 < W.k1; kt0 += EST_KT, ++sidx) {
+                const int s = int(sidx % EST_STAGES);
+                const int64_t n = sidx / EST_STAGES;
+                if (n > 0 && !(ok = est_wait(sm, &sm.empty[s], uint32_t((n - 1) & 1), a.status))) break;
+                const int nk = min(EST_KT, W.k1 - kt0);
+                mbar_expect_tx(&sm.full[s], uint32_t(nk) * uint32_t(lg + rg) * 256u);
+                for (int j = 0; j < nk; ++j) {
+                    bulk_g2s(sm.L[s] + j * SPL_LT, Lb + (int64_t(W.mtile) * G.kt + kt0 + j) * (SPL_S * SPL_LT),
+                             uint32_t(lg) * 256u, &sm.full[s]);
+                    bulk_g2s(sm.R[s] + j * SPL_RT, Rb + (int64_t(W.ntile) * G.kt + kt0 + j) * (SPL_S * SPL_RT),
+                             uint32_t(rg) * 256u, &sm.full[s]);
+                }
+            }
+        }
+        for (int64_t q = sidx - EST_STAGES; q < sidx; ++q)
+            if (q >= 0) mbar_wait_final(&sm.full[q % EST_STAGES], uint32_t((q / EST_STAGES) & 1));
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer: one MMA per K tile into the slot of the current drain chunk
+        int64_t sidx = 0, chunk = 0;
+        bool ok = true;
+        SWork Wn{};
+        int Nn = 0;
+        if (blockIdx.x < total) {
+            Wn = a.work[blockIdx.x];
+            Nn = a.gemms[Wn.gemm].N;
+        }
+        for (int64_t it = blockIdx.x; it < total && ok; it += step) {
+            const SWork W = Wn;
+            const int ncols = min(SPL_TN, Nn - W.ntile * SPL_TN);
+            if (it + step < total) {
+                Wn = a.work[it + step];
+                Nn = a.gemms[Wn.gemm].N;
+            }
+            const uint32_t idesc = um_idesc((ncols + 15) & ~15);
+            for (int kc0 = W.k0; kc0 < W.k1 && ok; kc0 += EST_DRAIN_KT, ++chunk) {
+                const int kc1 = min(kc0 + EST_DRAIN_KT, W.k1);
+                const int slot = int(chunk & 1);
+                if (chunk >= 2) {   // the slot's previous chunk has been read
+                    if (!(ok = est_wait(sm, &sm.tempty[slot], uint32_t(((chunk >> 1) - 1) & 1), a.status))) break;
+                    tc_fence_after();
+                }
+                for (int kt0 = kc0; kt0 < kc1; kt0 += EST_KT, ++sidx) {
+                    const int s = int(sidx % EST_STAGES);
+                    if (!(ok = est_wait(sm, &sm.full[s], uint32_t((sidx / EST_STAGES) & 1), a.status))) break;
+                    tc_fence_after();
+                    const int nk = min(EST_KT, kc1 - kt0);
+                    const uint32_t a0 = sdesc_lo(su32(sm.L[s])), b0 = sdesc_lo(su32(sm.R[s]));
+                    for (int j = 0; j < nk; ++j)
+                        umma(tmem + uint32_t(slot * SPL_TN), a0 + uint32_t(j * SPL_LT * 2) / 16,
+                             b0 + uint32_t(j * SPL_RT * 2) / 16, (kt0 == kc0 && j == 0) ? 0u : 1u, idesc);
+                    umma_commit(&sm.empty[s]);
+                }
+                if (ok) umma_commit(&sm.tfull[slot]);
+            }
+        }
+        umma_commit(&sm.done);
+        mbar_wait_final(&sm.done, 0);
+    } else if (warp >= 2) {
+        // ---- epilogue
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int row = 32 * q + lane, col0 = h * UM_EPI_COLS;
+        const uint32_t tmem_row = tmem + (uint32_t(32 * q) << 16);
+        int64_t chunk = 0;
         bool ok = true;
         SWork W1{}, W2{};
         SGemm G1{};
@@ -624,127 +1039,64 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
             W1 = W2;
             if (it + step < total) G1 = a.gemms[W1.gemm];
             if (it + 2 * step < total) W2 = a.work[it + 2 * step];
-            const int fs = G.fshift;
             const int r = W.mtile * SPL_TM + row;
             const int cbase = W.ntile * SPL_TN + col0;
-            // stage 1: the exponents its epilogue needs, loaded before the drain (both
-            // arrays are read-only while stage 1 runs): column cbase + lane, this row
-            const bool rv = r < G.M;
-            int cex_l = 0, erow = 0;
-            if (G.kind == 0) {
-                if (cbase + lane < G.N) cex_l = a.ap_ex[G.ec_off + cbase + lane];
-                if (rv) erow = a.op_ex[G.er_off + r];
+            // every load of the bound is issued before the drain wait
+            int ex_lane = SPL_EXP_NONE;
+            float xs_lane = 0.0f;
+            if (cbase + lane < G.N) {
+                ex_lane = a.ap_ex[G.ec_off + cbase + lane];
+                xs_lane = a.xs[G.ec_off + cbase + lane];
             }
-            long long acc[UM_EPI_COLS];   // slice sums of the item in units of 2^-31
+            const bool rv_ok = r < G.M;
+            const int ea = rv_ok ? a.op_ex[G.er_off + r] : SPL_EXP_NONE;
+            const int sa_i = rv_ok ? a.srow[G.er_off + r] : 0;
+            int acc[UM_EPI_COLS];
 #pragma unroll
             for (int j = 0; j < UM_EPI_COLS; ++j) acc[j] = 0;
-            for (int kc0 = W.k0; kc0 < W.k1 && ok; kc0 += SPL_DRAIN_KT, ++dchunk) {
-                // 32-bit conversions only (the 64-bit one is an FP64-rate operation): acc c
-                // holds the exact level sum in units of 2^(-8c) for c < 4 (|sum| <=
-                // (c+1) 2^22 in those units), acc 4 the rest, rounded to units of 2^-31
-                // (< 2^24 of them); each is added in units of 2^-31, the chunk's total
-                // staying below 2^53.01.  An accumulator is handed back to the MMA issuer
-                // as soon as it is in registers.
+            for (int kc0 = W.k0; kc0 < W.k1 && ok; kc0 += EST_DRAIN_KT, ++chunk) {
+                const int slot = int(chunk & 1);
+                ok = __all_sync(0xffffffffu, est_wait(sm, &sm.tfull[slot], uint32_t((chunk >> 1) & 1), a.status));
+                if (!ok) break;
+                tc_fence_after();
+                uint32_t rv[UM_EPI_COLS];
+                tmem_ld32(tmem_row + uint32_t(slot * SPL_TN + col0), rv);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                tc_fence_before();
+                mbar_arrive(&sm.tempty[slot]);
 #pragma unroll
-                for (int c = 0; c < SPL_ACCS; ++c) {
-                    // warp-uniform outcome: the TMEM loads below are .sync.aligned
-                    const int slot = um_slot(c, dchunk);
-                    ok = __all_sync(0xffffffffu, mbar_wait(sm, &sm.tfull[slot], um_use(c, dchunk) & 1, a.status));
-                    if (!ok) break;
-                    tc_fence_after();
-                    const uint32_t base = tmem + lane_addr + uint32_t(slot) * SPL_TN + col0;
-                    uint32_t rv[UM_EPI_COLS];
-#pragma unroll
-                    for (int c0 = 0; c0 < UM_EPI_COLS; c0 += 8)
-                        tmem_ld8(base + c0, *reinterpret_cast<uint32_t(*)[8]>(rv + c0));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    tc_fence_before();
-                    mbar_arrive(&sm.tempty[slot]);
-                    const float scale = c == 0 ? 1.0f : c == 1 ? 256.0f : c == 2 ? 65536.0f : c == 3 ? 16777216.0f : 2147483648.0f;
-#pragma unroll
-                    for (int j = 0; j < UM_EPI_COLS; ++j) {
-                        const int iv = __float2int_rn(__uint_as_float(rv[j]) * scale);
-                        if (c == 0)
-                            acc[j] += static_cast<long long>(iv) * (1ll << 31);
-                        else if (c < SPL_ACCS - 1)
-                            acc[j] += static_cast<long long>(iv) * (1 << (31 - 8 * c));
-                        else
-                            acc[j] += iv;
-                    }
-                }
+                for (int j = 0; j < UM_EPI_COLS; ++j) acc[j] += __float2int_rn(__uint_as_float(rv[j]));
             }
             if (!ok) break;
-            // F = round(2^fs * sum): exact for fs >= 31 (up to 32 drains of 2^53.01 stay
-            // below 2^58.01; the GEMM's shift keeps F below 2^62); for fs < 31 only the
-            // part below 2^-fs, i.e. of i4, is rounded
+            const int i = rv_ok ? r % G.per : 0;
+            const float sa = float(sa_i) * (1.005f / 32768.0f);
+            int vprev = -1, Emax = SPL_EXP_NONE;
 #pragma unroll
-            for (int j = 0; j < UM_EPI_COLS; ++j)
-                acc[j] = fs >= 31 ? static_cast<long long>(static_cast<unsigned long long>(acc[j]) << (fs - 31))
-                                  : (acc[j] + (1ll << (30 - fs))) >> (31 - fs);
-            if (G.kind == 0) {
-                // exponents of the stage-2 vectors fed by this row: the column exponents
-                // come with one load per warp (lane l holds column cbase + l) and a
-                // broadcast per column, so no global load sits between the atomics
-                const int rs = rv ? r : 0;
-                // stage-2 vector of entry (r, c): (c / colgroup) * period + r % period
-                int32_t* x2 = a.ap_ex + G.x2_exp + rs % G.x2_period;
-                const int eoff = erow - (14 + G.fshift);
-                int emax = INT_MIN, grp = cbase / G.x2_colgroup;
-                int next = (grp + 1) * G.x2_colgroup;   // first column of the next group
-#pragma unroll
-                for (int j = 0; j < UM_EPI_COLS; ++j) {
-                    const int c = cbase + j;   // the same for every lane
-                    const int ce = __shfl_sync(0xffffffffu, cex_l, j);
-                    if (c < G.N) {
-                        if (c >= next) {
-                            if (rv && emax != INT_MIN) atomicMax(x2 + grp * G.x2_period, emax + eoff);
-                            emax = INT_MIN;
-                            ++grp;
-                            next += G.x2_colgroup;
-                        }
-                        if (acc[j] != 0) {
-                            const unsigned long long u = acc[j] < 0 ? static_cast<unsigned long long>(-acc[j])
-                                                                    : static_cast<unsigned long long>(acc[j]);
-                            emax = max(emax, (64 - __clzll(u)) + ce);
-                        }
-                    }
+            for (int j = 0; j < UM_EPI_COLS; ++j) {
+                const int ex = __shfl_sync(0xffffffffu, ex_lane, j);
+                const float xsj = __shfl_sync(0xffffffffu, xs_lane, j);
+                const int col = cbase + j;
+                if (!rv_ok || col >= G.N || ex < SPL_EXP_NONE / 2 || ea < -(1 << 28)) continue;
+                const int v = col / G.cp;
+                if (v != vprev) {
+                    if (vprev >= 0 && Emax > SPL_EXP_NONE) atomicMax(a.ap_ex + G.dst_exp + vprev * G.per + i, Emax);
+                    vprev = v;
+                    Emax = SPL_EXP_NONE;
                 }
-                if (rv && emax != INT_MIN) atomicMax(x2 + grp * G.x2_period, emax + eoff);
-                // row-major store through the warp's shared-memory patch: each pass moves
-                // 4 columns of the warp's 32 rows, written as 8 rows x 32 contiguous bytes
-                // per instruction instead of 32 rows x 8 bytes
-                long long* tp = sm.tr[warp - 2];
-                int64_t* D = a.s1 + G.d_off;
-                const int rbase = W.mtile * SPL_TM + 32 * q;
-#pragma unroll
-                for (int c4 = 0; c4 < UM_EPI_COLS; c4 += 4) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) tp[lane * UM_TR_LD + j] = G.sign > 0 ? acc[c4 + j] : -acc[c4 + j];
-                    __syncwarp();
-                    const int cc = lane & 3, c = cbase + c4 + cc;
-#pragma unroll
-                    for (int rep = 0; rep < 4; ++rep) {
-                        const int rr = 8 * rep + (lane >> 2), gr = rbase + rr;
-                        if (gr < G.M && c < G.N) D[int64_t(gr) * G.ldd + c] = tp[rr * UM_TR_LD + cc];
-                    }
-                    __syncwarp();
-                }
-            } else if (r < G.M) {
-                unsigned long long* D = reinterpret_cast<unsigned long long*>(a.s2 +
-                                                                              G.d_off + int64_t(r) * G.ldd);
-#pragma unroll
-                for (int j = 0; j < UM_EPI_COLS; ++j) {
-                    const int c = cbase + j;
-                    if (c < G.N && acc[j] != 0) atomicAdd(D + c, static_cast<unsigned long long>(acc[j]));
-                }
+                const float f = (float(abs(acc[j])) * (1.0f / 16384.0f) + xsj + sa) * (1.0f + 1.0f / 1048576.0f) +
+                                (1.0f / 1073741824.0f);
+                // f is a positive normal float: f < 2^(biased exponent - 126)
+                const int e = int((__float_as_uint(f) >> 23) & 255u) - 126;
+                Emax = max(Emax, ea + ex + e);
             }
+            if (vprev >= 0 && Emax > SPL_EXP_NONE) atomicMax(a.ap_ex + G.dst_exp + vprev * G.per + i, Emax);
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UM_TMEM_COLS));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(EST_TMEM_COLS));
     }
 }
 
@@ -765,22 +1117,20 @@ __global__ void k_wait_selftest(int* status, long long limit) {
 // stage-2 sums -> FP64 wave function
 
 __global__ void k_finalize(const SBlock* __restrict__ blocks, const SPart* __restrict__ parts,
-                           const int64_t* __restrict__ s2, int64_t s2_vs, const int32_t* __restrict__ op_ex,
-                           const int32_t* __restrict__ ap_ex, int64_t ap_ex_vs, double* __restrict__ y, int64_t dim) {
+                           const int64_t* __restrict__ s2, const int32_t* __restrict__ op_ex,
+                           const int32_t* __restrict__ ap_ex, double* __restrict__ y, int64_t dim) {
     const SBlock B = blocks[blockIdx.x];
     const int v = blockIdx.y;
-    const int32_t* aex = ap_ex + int64_t(v) * ap_ex_vs;
-    const int64_t* S2 = s2 + int64_t(v) * s2_vs;
     for (int e = threadIdx.x; e < B.rows * B.cols; e += blockDim.x) {
         const int i = e / B.cols, j = e % B.cols;
         double sum = 0.0;
         for (int p = B.p0; p < B.p0 + B.np; ++p) {
             const SPart P = parts[p];
             const int ri = v * P.rstack + i, cj = v * P.cstack + j;
-            const long long F = S2[P.acc_off + int64_t(ri) * P.ld + cj];
+            const long long F = s2[P.acc_off + int64_t(ri) * P.ld + cj];
             if (F == 0) continue;
-            const int er = (P.er_buf ? aex : op_ex)[P.er_off + ri];
-            const int ec = (P.ec_buf ? aex : op_ex)[P.ec_off + cj];
+            const int er = (P.er_buf ? ap_ex : op_ex)[P.er_off + ri];
+            const int ec = (P.ec_buf ? ap_ex : op_ex)[P.ec_off + cj];
             sum += scalbn(static_cast<double>(F), er + ec - P.e_off);
         }
         y[int64_t(v) * dim + B.y_off + e] = sum;
@@ -802,92 +1152,121 @@ int32_t fshift_for(int64_t K) {
 // ----------------------------------------------------------------------------------
 // host side
 
-// Host-side bounds proof of a split plan: every bulk-copy source range, slicer write,
-// exponent read/write, stage-1 store and stage-2 sum lies inside its buffer.
+namespace {
+int64_t job_tile_elems(int rows_tile) { return int64_t(SPL_S) * rows_tile * SPL_TK; }
+}  // namespace
+
+// Host-side bounds proof of a split plan: every slicer read and write, bulk-copy source
+// range, exponent and bound-table access, stage-1 epilogue store, stage-2 sum and
+// finalize read lies inside its buffer.
 int validate_split_plan(const Plan& P, const SplitHost& H, std::string* err) {
     auto bad = [&](const char* what) {
         *err = std::string("split plan out of bounds: ") + what;
         return DMRG_ERR_BOUNDS;
     };
+    const int64_t n_jobs = int64_t(H.jobs.size());
+    auto job_ok = [&](int64_t j) { return j >= 0 && j < n_jobs; };
     for (const SJob& J : H.jobs) {
-        const int64_t tiles = int64_t(J.npad / J.rows_tile) * J.kt * SPL_S * J.rows_tile * SPL_TK;
+        if (J.rows_tile != SPL_TM && J.rows_tile != SPL_TN) return bad("job tile height");
+        const int64_t tiles = int64_t(J.npad / J.rows_tile) * J.kt * job_tile_elems(J.rows_tile);
         const int64_t sl = J.out_buf ? H.ap_sl_vs : H.op_sl;
         const int64_t ex = J.out_buf ? H.ap_ex_vs : H.op_ex;
-        if (J.npad % J.rows_tile || J.npad < J.nvalid || J.kt * SPL_TK < J.K) return bad("job shape");
+        if (J.npad % J.rows_tile || J.npad < J.nvalid || J.nvalid < 0 || int64_t(J.kt) * SPL_TK < J.K || J.K < 0)
+            return bad("job shape");
         if (J.out_tiles < 0 || J.out_tiles % 8 || J.out_tiles + tiles > sl) return bad("slice tiles");
         if (J.out_exp < 0 || J.out_exp + J.npad > ex) return bad("exponents");
+        if (J.top_sums && (J.out_buf || J.nseg != 1)) return bad("row sums");
+        if (J.out_buf) continue;
         int64_t K = 0;
         for (int s = J.seg0; s < J.seg0 + J.nseg; ++s) {
+            if (s < 0 || s >= int32_t(H.segs.size())) return bad("segment index");
             const SSeg& g = H.segs[s];
-            if (g.kbase != K) return bad("segment K base");
-            K += int64_t(g.kc) * g.nt;
-            if (J.nvalid == 0 || g.kc <= 0 || g.nt <= 0) continue;
-            if (g.vper < 1) return bad("vector grouping");
+            if (g.kbase != K || g.kc < 1 || g.kcp < g.kc || g.nt < 1 || g.vper < 1) return bad("segment shape");
+            if (J.top_sums && g.nt != 1) return bad("row-sum segment");
+            K += int64_t(g.kcp) * g.nt;
+            if (J.nvalid == 0) continue;
             const int ngrp = (J.nvalid - 1) / g.vper, rmax = std::min(J.nvalid, g.vper) - 1;
             const int64_t last = g.off + (g.nt - 1) * g.ts + ngrp * g.vgs + int64_t(rmax) * g.vs + int64_t(g.kc - 1) * g.ks;
-            const int64_t lim = g.space == SP_OPS ? P.ops_len
-                                                  : (g.space == SP_X ? P.dim * H.nv : P.scratch_len * H.nv);
-            if (g.off < 0 || last >= lim) return bad("slice source");
-            if (g.is_i64) {
-                if (g.space != SP_SCR) return bad("int64 source space");
-                if (g.er_off < 0 || g.er_off + int64_t(g.nt - 1) * g.er_ts + rmax + 1 > H.op_ex) return bad("row exps");
-                if (g.ec_off < 0 || g.ec_off + int64_t(ngrp) * g.ec_vgs + g.kc > H.ap_ex_vs) return bad("col exps");
-            }
+            if (g.off < 0 || g.ts < 0 || g.vgs < 0 || g.vs < 0 || g.ks < 0 || last >= P.ops_len)
+                return bad("slice source");
         }
         if (K != J.K) return bad("job K");
     }
-    for (const STile& T : H.tiles) {   // the digit pass starts its segment search at T.seg
-        if (T.job < 0 || T.job >= int32_t(H.jobs.size())) return bad("tile job");
-        const SJob& J = H.jobs[size_t(T.job)];
-        if (T.seg < J.seg0 || T.seg >= J.seg0 + J.nseg || T.k0 < 0 || T.k0 >= J.K || 8 * T.vg >= J.nvalid ||
-            H.segs[size_t(T.seg)].kbase > T.k0)
-            return bad("tile segment");
+    for (const SXJob& X : H.xjobs) {
+        if (!job_ok(X.job)) return bad("psi job index");
+        const SJob& J = H.jobs[size_t(X.job)];
+        if (!J.out_buf || J.rows_tile != SPL_TN || X.cp % SPL_KPAD || X.cp < X.nk || X.nk < 1 ||
+            J.nvalid != H.nv * X.cp || J.K != X.K || X.K < 1)
+            return bad("psi job shape");
+        const int64_t last = int64_t(H.nv - 1) * P.dim + X.off + int64_t(X.K - 1) * X.ks + int64_t(X.nk - 1) * X.vs;
+        if (X.off < 0 || X.ks < 0 || X.vs < 0 || last >= P.dim * H.nv) return bad("psi source");
     }
-    auto check_work = [&](const std::vector<SWork>& w) {
+    if (H.ap_ex_mid0 < 0 || H.ap_ex_mid0 > H.ap_ex_mid1 || H.ap_ex_mid1 > H.ap_ex_vs) return bad("bound range");
+    auto check_work = [&](const std::vector<SWork>& w) -> const char* {
         for (const SWork& x : w) {
-            const SGemm& G = H.gemms[x.gemm];
-            if (x.k0 < 0 || x.k1 > G.kt || x.k0 >= x.k1) return false;
-            if (cdiv(x.k1 - x.k0, SPL_DRAIN_KT) > SPL_MAX_DRAINS) return false;   // epilogue sum bound
+            if (x.gemm < 0 || x.gemm >= int32_t(H.gemms.size())) return "work gemm index";
+            const SGemm& G = H.gemms[size_t(x.gemm)];
+            if (x.k0 < 0 || x.k1 > G.kt || x.k0 >= x.k1) return "work K range";
+            if (cdiv(x.k1 - x.k0, SPL_DRAIN_KT) > SPL_MAX_DRAINS) return "work drains";   // epilogue sum bound
             const int64_t lsz = G.l_buf ? H.ap_sl_vs : H.op_sl, rsz = G.r_buf ? H.ap_sl_vs : H.op_sl;
             const int64_t lend = G.l_tiles + (int64_t(x.mtile) * G.kt + x.k1) * (SPL_S * SPL_LT);
             const int64_t rend = G.r_tiles + (int64_t(x.ntile) * G.kt + x.k1) * (SPL_S * SPL_RT);
-            if (G.l_tiles % 8 || G.r_tiles % 8 || lend > lsz || rend > rsz) return false;
-            if (int64_t(x.mtile) * SPL_TM >= G.M || int64_t(x.ntile) * SPL_TN >= G.N) return false;
-            const int64_t dend = G.d_off + int64_t(G.M - 1) * G.ldd + G.N;
-            if (G.ldd < G.N || dend > (G.kind == 0 ? H.s1_vs : H.s2_vs)) return false;
-            if (G.kind == 0) {   // stage-1 epilogue exponent reads and raises
-                const int64_t ngrp = G.x2_colgroup > 0 ? (G.N - 1) / G.x2_colgroup : -1;
-                if (G.x2_exp < 0 || G.x2_period <= 0 || ngrp < 0 ||
-                    G.x2_exp + (ngrp + 1) * G.x2_period > H.ap_ex_vs)
-                    return false;
-                if (G.er_off < 0 || G.er_off + G.M > H.op_ex || G.ec_off < 0 || G.ec_off + G.N > H.ap_ex_vs)
-                    return false;
+            if (G.l_tiles < 0 || G.r_tiles < 0 || G.l_tiles % 8 || G.r_tiles % 8 || lend > lsz || rend > rsz)
+                return "work operand tiles";
+            if (x.mtile < 0 || x.ntile < 0 || int64_t(x.mtile) * SPL_TM >= G.M || int64_t(x.ntile) * SPL_TN >= G.N)
+                return "work output tile";
+            if (G.kind == 1) {
+                const int64_t dend = G.d_off + int64_t(G.M - 1) * G.ldd + G.N;
+                if (G.d_off < 0 || G.ldd < G.N || dend > H.s2_vs) return "stage-2 sums";
+                continue;
             }
+            // stage-1 epilogue: row r = t*per + i, column v*cp + k -> vector v*per + i,
+            // K = kbase + t*cp + k of the destination job (written in groups of 8 K)
+            if (G.per < 1 || G.cp < 1 || G.cp % SPL_KPAD || G.kbase % SPL_KPAD || G.M % G.per || G.N % G.cp)
+                return "stage-1 shape";
+            const int64_t nt = G.M / G.per, nvv = G.N / G.cp;
+            if (nvv != H.nv) return "stage-1 vectors";
+            bool dst_ok = false;
+            for (const SJob& J : H.jobs)
+                if (J.out_buf && J.out_tiles == G.d_off && J.out_exp == G.dst_exp && J.rows_tile == G.dst_rows_tile &&
+                    J.kt == G.dst_kt) {
+                    dst_ok = int64_t(H.nv) * G.per <= J.nvalid && G.kbase + nt * G.cp <= J.K;
+                    break;
+                }
+            if (!dst_ok) return "stage-1 destination";
+            if (G.er_off < 0 || G.er_off + G.M > H.op_ex || G.ec_off < 0 || G.ec_off + G.N > H.ap_ex_vs) return "stage-1 exponents";
+            // the bounds the stage-1 epilogue reads and the estimate pass raises
+            if (G.dst_exp < H.ap_ex_mid0 || G.dst_exp + int64_t(H.nv) * G.per > H.ap_ex_mid1) return "stage-1 bounds";
         }
-        return true;
+        return nullptr;
     };
-    if (!check_work(H.w1) || !check_work(H.w2)) return bad("gemm work");
-    for (const STile& T : H.tiles) {
-        if (T.job < 0 || T.job >= int32_t(H.jobs.size())) return bad("slice tile job");
-        const SJob& J = H.jobs[T.job];
-        if (T.vg < 0 || 8 * T.vg >= J.nvalid || 8 * T.vg + 8 > J.npad || J.rows_tile % 8) return bad("slice tile rows");
+    if (const char* why = check_work(H.w1)) return bad(why);
+    if (const char* why = check_work(H.w2)) return bad(why);
+    for (const STile& T : H.tiles) {   // the digit pass starts its segment search at T.seg
+        if (!job_ok(T.job)) return bad("slice tile job");
+        const SJob& J = H.jobs[size_t(T.job)];
+        if (J.out_buf || T.vg < 0 || 8 * T.vg >= J.nvalid || 8 * T.vg + 8 > J.npad) return bad("slice tile rows");
         if (T.k0 < 0 || T.k0 >= J.K || T.k0 % SPL_TILE_K) return bad("slice tile K");
+        if (T.seg < J.seg0 || T.seg >= J.seg0 + J.nseg || H.segs[size_t(T.seg)].kbase > T.k0) return bad("tile segment");
     }
     for (const SItem& I : H.items) {
         if (I.slab < 0 || I.slab >= int32_t(H.slabs.size())) return bad("slice item");
-        const SSlab& Sl = H.slabs[I.slab];
+        const SSlab& Sl = H.slabs[size_t(I.slab)];
         if (I.r0 < 0 || I.nrows <= 0 || I.r0 + I.nrows > Sl.rows) return bad("slice item rows");
-        const SJob& J = H.jobs[Sl.job];
-        if (Sl.seg < J.seg0 || Sl.seg >= J.seg0 + J.nseg || Sl.rows != int64_t(H.segs[Sl.seg].nt) * J.nvalid)
+        if (!job_ok(Sl.job)) return bad("slice slab job");
+        const SJob& J = H.jobs[size_t(Sl.job)];
+        if (J.out_buf || Sl.seg < J.seg0 || Sl.seg >= J.seg0 + J.nseg ||
+            Sl.rows != int64_t(H.segs[size_t(Sl.seg)].nt) * J.nvalid)
             return bad("slice slab");
     }
     for (const SBlock& B : H.blocks)
         for (int p = B.p0; p < B.p0 + B.np; ++p) {
-            const SPart& Q = H.parts[p];
+            if (p < 0 || p >= int32_t(H.parts.size())) return bad("finalize part");
+            const SPart& Q = H.parts[size_t(p)];
             const int64_t rmax = int64_t(H.nv - 1) * Q.rstack + B.rows, cmax = int64_t(H.nv - 1) * Q.cstack + B.cols;
-            if (Q.ld < cmax || Q.acc_off + (rmax - 1) * Q.ld + cmax > H.s2_vs) return bad("finalize sums");
-            if (Q.er_off + rmax > (Q.er_buf ? H.ap_ex_vs : H.op_ex)) return bad("finalize row exps");
-            if (Q.ec_off + cmax > (Q.ec_buf ? H.ap_ex_vs : H.op_ex)) return bad("finalize col exps");
+            if (Q.ld < cmax || Q.acc_off < 0 || Q.acc_off + (rmax - 1) * Q.ld + cmax > H.s2_vs) return bad("finalize sums");
+            if (Q.er_off < 0 || Q.er_off + rmax > (Q.er_buf ? H.ap_ex_vs : H.op_ex)) return bad("finalize row exps");
+            if (Q.ec_off < 0 || Q.ec_off + cmax > (Q.ec_buf ? H.ap_ex_vs : H.op_ex)) return bad("finalize col exps");
         }
     return DMRG_OK;
 }
@@ -905,7 +1284,7 @@ void build_split_work(SplitHost& H, const Schedule& S) {
     }
     // stage 2: output tiles x K chunks.  A shape class with no scheduled chunk takes the
     // adaptive one: the longest multiple of the drain length up to SPL_S2_KCHUNK K tiles
-    // that leaves >= 4 items per SM.
+    // that leaves >= 4 items per SM.  Scheduled chunks are given in units of 32 K.
     int64_t tile_kt = 0;
     for (const SGemm& m : H.gemms)
         if (m.kind == 1) tile_kt += cdiv(m.M, SPL_TM) * cdiv(m.N, SPL_TN) * int64_t(m.kt);
@@ -917,7 +1296,7 @@ void build_split_work(SplitHost& H, const Schedule& S) {
         const SGemm& m = H.gemms[gi];
         if (m.kind != 1) continue;
         const int sc = S.split_kchunk[kclass(int64_t(m.kt) * SPL_TK)];
-        const int chunk = sc > 0 ? sc : adaptive;
+        const int chunk = sc > 0 ? sc * (32 / SPL_TK) : adaptive;
         for (int k0 = 0; k0 < m.kt; k0 += chunk)
             for (int mt = 0; mt < cdiv(m.M, SPL_TM); ++mt)
                 for (int nt = 0; nt < cdiv(m.N, SPL_TN); ++nt)
@@ -946,21 +1325,25 @@ void build_split_work(SplitHost& H, const Schedule& S) {
 }
 
 int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err, const Schedule& S) {
-    std::vector<SGemm>& gemms = H.gemms;
-    std::vector<SSeg>& segs = H.segs;
+    H = SplitHost{};
+    H.nv = nv;
+    if (nv < 1 || nv > 64) {
+        *err = "nvec out of range";
+        return DMRG_ERR_INVALID_ARG;
+    }
+    if (int64_t(P.groups.size()) > (int64_t(1) << 28) || P.dim * nv > (int64_t(1) << 40)) {
+        *err = "too many groups";
+        return DMRG_ERR_INVALID_ARG;
+    }
     std::vector<SJob>& jobs = H.jobs;
-    std::vector<int32_t> op_jobs, x_jobs, mid_jobs;
-    std::vector<SBlock>& blocks = H.blocks;
-    blocks.assign(P.blocks.size(), SBlock{});
-    std::vector<SPart>& parts = H.parts;
+    std::vector<SSeg>& segs = H.segs;
+    std::vector<int32_t> op_jobs;
     int64_t op_sl = 0, op_ex = 0, ap_sl = 0, ap_ex = 0, s2 = 0;
-
-    auto add_job = [&](int out_buf, int rows_tile, int nvalid, int64_t K, const std::vector<SSeg>& js,
-                       int64_t* tiles_off, int64_t* exp_off) {
+    auto add_job = [&](int out_buf, int rows_tile, int64_t nvalid, int64_t K, const std::vector<SSeg>& js) {
         SJob J{};
         J.out_buf = out_buf;
         J.rows_tile = rows_tile;
-        J.nvalid = nvalid;
+        J.nvalid = int32_t(nvalid);
         J.npad = int32_t(cdiv(nvalid, rows_tile) * rows_tile);
         J.K = int32_t(K);
         J.kt = int32_t(cdiv(K, SPL_TK));
@@ -969,189 +1352,187 @@ int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err, cons
         int32_t kb = 0;
         for (SSeg g : js) {
             g.kbase = kb;
-            kb += g.kc * g.nt;
+            kb += g.kcp * g.nt;
             segs.push_back(g);
         }
         int64_t& sl = out_buf ? ap_sl : op_sl;
         int64_t& ex = out_buf ? ap_ex : op_ex;
         J.out_tiles = sl;
         J.out_exp = ex;
-        sl += int64_t(J.npad) * J.kt * SPL_TK * SPL_S;
+        sl += int64_t(J.npad / rows_tile) * J.kt * job_tile_elems(rows_tile);
         ex += J.npad;
-        *tiles_off = J.out_tiles;
-        *exp_off = J.out_exp;
         jobs.push_back(J);
+        if (!out_buf) op_jobs.push_back(int32_t(jobs.size() - 1));
         return int32_t(jobs.size() - 1);
     };
-    auto seg = [](int space, int64_t off, int64_t ts, int64_t vs, int64_t ks, int kc, int nt) {
+    // operator run: nt sub-blocks (terms) of kc entries padded to kcp
+    auto seg = [](int64_t off, int64_t ts, int64_t vs, int kc, int kcp, int nt) {
         SSeg s{};
-        s.space = space; s.off = off; s.ts = ts; s.vs = vs; s.ks = ks; s.kc = kc; s.nt = nt;
-        s.vper = 1 << 30;   // one vector group unless stacked
+        s.off = off; s.ts = ts; s.vs = vs; s.ks = 1; s.kc = kc; s.kcp = kcp; s.nt = nt;
+        s.vper = 1 << 30;
         return s;
     };
-    // the same entries for nv stacked Davidson vectors: vector v*per + r of vector v
-    auto stacked = [](SSeg s, int per, int64_t vgs, int32_t ec_vgs) {
-        s.vper = per; s.vgs = vgs; s.ec_vgs = ec_vgs;
-        return s;
-    };
-    if (nv < 1 || nv > 64) {
-        *err = "nvec out of range";
-        return DMRG_ERR_INVALID_ARG;
-    }
-    if (int64_t(P.groups.size()) > (int64_t(1) << 30)) {
-        *err = "too many groups";
-        return DMRG_ERR_INVALID_ARG;
-    }
-
-    // stage 1: one GEMM per group; L = stacked operator (operator slices), R = x block
-    std::vector<int64_t> s1_lexp(P.groups.size()), s1_rexp(P.groups.size());
-    std::vector<int32_t> s1_eoff(P.groups.size());
-    for (size_t g = 0; g < P.groups.size(); ++g) {
-        const Group& G = P.groups[g];
-        const PsiBlock& B = P.blocks[G.in_block];
-        const int n = int(G.terms.size());
-        SGemm m{};
-        int64_t lt, le, rt, re;
-        // the nv Davidson vectors stack along N: column v*c + j is column j of vector v
-        if (G.order == 0) {   // X_g = A_stack (n a x b) * [x_q^(v)] (b x nv c)
-            m.M = n * G.a; m.N = nv * G.c;
-            op_jobs.push_back(add_job(0, SPL_TM, m.M, G.b, {seg(SP_OPS, G.a_stack, 0, G.b, 1, G.b, 1)}, &lt, &le));
-            x_jobs.push_back(add_job(1, SPL_TN, m.N, G.b,
-                                     {stacked(seg(SP_X, B.off, 0, 1, G.c, G.b, 1), G.c, P.dim, 0)}, &rt, &re));
-        } else {              // Z_g^T = B_stack (n d x c) * [x_q^(v)T] (c x nv b)
-            m.M = n * G.d; m.N = nv * G.b;
-            op_jobs.push_back(add_job(0, SPL_TM, m.M, G.c, {seg(SP_OPS, G.b_stack, 0, G.c, 1, G.c, 1)}, &lt, &le));
-            x_jobs.push_back(add_job(1, SPL_TN, m.N, G.c,
-                                     {stacked(seg(SP_X, B.off, 0, G.c, 1, G.c, 1), G.b, P.dim, 0)}, &rt, &re));
-        }
-        m.l_tiles = lt; m.r_tiles = rt; m.l_buf = 0; m.r_buf = 1;
-        m.kt = int32_t(cdiv(G.order == 0 ? G.b : G.c, SPL_TK));
-        if (m.kt > SPL_MAX_DRAINS * SPL_DRAIN_KT) {   // one stage-1 item spans the whole contraction
+    for (const Group& G : P.groups) {
+        const int64_t kmax = int64_t(std::max({G.a, G.b, G.c, G.d}));
+        if (kmax > SPL_MAX_DRAINS * SPL_DRAIN_KT * SPL_TK) {   // one stage-1 item spans the whole contraction
             *err = "split path: a sector dimension above 8192";
             return DMRG_ERR_INVALID_ARG;
         }
-        m.d_off = int64_t(nv) * G.scratch; m.ldd = m.N; m.kind = 0; m.sign = G.sign < 0 ? -1 : 1;
-        m.fshift = fshift_for(G.order == 0 ? G.b : G.c);
-        m.er_off = le; m.ec_off = re; m.x2_exp = -1;
-        m.x2_period = G.order == 0 ? G.a : G.d;
-        m.x2_colgroup = G.order == 0 ? G.c : G.b;
-        s1_lexp[g] = le; s1_rexp[g] = re; s1_eoff[g] = 14 + m.fshift;
-        gemms.push_back(m);
     }
-    // stage 2: per output block, one GEMM over its A-first groups and one over its B-first groups
+
+    // psi jobs: one per (input block, contraction side), shared by the groups that use it
+    std::vector<int32_t> xjob_of(P.blocks.size() * 2, -1);
+    auto xjob = [&](int32_t q, int side) {
+        int32_t& x = xjob_of[size_t(q) * 2 + size_t(side)];
+        if (x >= 0) return x;
+        const PsiBlock& B = P.blocks[size_t(q)];
+        SXJob X{};
+        X.off = B.off;
+        if (side == 0) {   // vectors = columns (K over the block's rows)
+            X.K = B.rows; X.nk = B.cols; X.ks = B.cols; X.vs = 1;
+        } else {           // vectors = rows (K over the block's columns)
+            X.K = B.cols; X.nk = B.rows; X.ks = 1; X.vs = B.cols;
+        }
+        X.cp = kpad(X.nk);
+        X.job = add_job(1, SPL_TN, int64_t(nv) * X.cp, X.K, {});
+        H.xjobs.push_back(X);
+        x = int32_t(H.xjobs.size() - 1);
+        return x;
+    };
+
+    // every psi job first, so that the exponents of the stage-2 intermediate vectors
+    // (reset per apply) form one range after them
+    for (const Group& G : P.groups) xjob(G.in_block, G.order);
+    H.ap_ex_mid0 = ap_ex;
+    // stage 2 next (the stage-1 epilogues need their destination jobs): per output block
+    // one GEMM over its A-first groups and one over its B-first groups
+    std::vector<int32_t> dst_of(P.groups.size(), -1);
+    std::vector<int32_t> kbase_of(P.groups.size(), 0);
     std::vector<std::vector<int32_t>> by_out(P.blocks.size());
-    for (int32_t g = 0; g < int32_t(P.groups.size()); ++g) by_out[P.groups[g].out_block].push_back(g);
+    for (int32_t g = 0; g < int32_t(P.groups.size()); ++g) by_out[size_t(P.groups[size_t(g)].out_block)].push_back(g);
+    std::vector<SGemm> s2g;
+    H.blocks.assign(P.blocks.size(), SBlock{});
     for (size_t o = 0; o < P.blocks.size(); ++o) {
         const PsiBlock& O = P.blocks[o];
-        blocks[o] = {O.off, O.rows, O.cols, int32_t(parts.size()), 0};
+        H.blocks[o] = {O.off, O.rows, O.cols, int32_t(H.parts.size()), 0};
         for (int order = 0; order < 2; ++order) {
-            std::vector<SSeg> lseg, rseg;
+            std::vector<SSeg> opseg;
+            std::vector<int32_t> gs;
             int64_t K = 0;
             for (int32_t g : by_out[o]) {
-                const Group& G = P.groups[g];
+                const Group& G = P.groups[size_t(g)];
                 if (G.order != order) continue;
                 const int n = int(G.terms.size());
-                const int64_t sc = int64_t(nv) * G.scratch;
-                if (order == 0) {  // L = X_g rows (int64), vectors stacked along M; R = B_t rows
-                    // vector v*a + i, entry (t, k) = X_g[t a + i][v c + k]  (X_g is n a x nv c)
-                    SSeg s = stacked(seg(SP_SCR, sc, int64_t(G.a) * nv * G.c, int64_t(nv) * G.c, 1, G.c, n),
-                                     G.a, G.c, G.c);
-                    s.is_i64 = 1; s.er_off = s1_lexp[g]; s.er_ts = G.a; s.ec_off = s1_rexp[g]; s.e_off = s1_eoff[g];
-                    lseg.push_back(s);
-                    rseg.push_back(seg(SP_OPS, G.b_stack, int64_t(G.d) * G.c, G.c, 1, G.c, n));
-                    K += int64_t(G.c) * n;
-                } else {           // L = c_t A_t rows; R = Z_g^T rows (int64), vectors stacked along N
-                    // vector v*d + j, entry (t, k) = Z_g^T[t d + j][v b + k]  (Z_g^T is n d x nv b)
-                    lseg.push_back(seg(SP_OPS, G.a_stack, int64_t(G.a) * G.b, G.b, 1, G.b, n));
-                    SSeg s = stacked(seg(SP_SCR, sc, int64_t(G.d) * nv * G.b, int64_t(nv) * G.b, 1, G.b, n),
-                                     G.d, G.b, G.b);
-                    s.is_i64 = 1; s.er_off = s1_lexp[g]; s.er_ts = G.d; s.ec_off = s1_rexp[g]; s.e_off = s1_eoff[g];
-                    rseg.push_back(s);
-                    K += int64_t(G.b) * n;
+                kbase_of[size_t(g)] = int32_t(K);
+                if (order == 0) {   // K = (t, k < c): R = B_t rows (output columns)
+                    opseg.push_back(seg(G.b_stack, int64_t(G.d) * G.c, G.c, G.c, kpad(G.c), n));
+                    K += int64_t(kpad(G.c)) * n;
+                } else {            // K = (t, k < b): L = c_t A_t rows (output rows)
+                    opseg.push_back(seg(G.a_stack, int64_t(G.a) * G.b, G.b, G.b, kpad(G.b), n));
+                    K += int64_t(kpad(G.b)) * n;
                 }
+                gs.push_back(g);
             }
-            if (lseg.empty()) continue;
-            if (K > SPL_MAX_K) {
+            if (gs.empty()) continue;
+            if (K > SPL_MAX_K || K > INT32_MAX / 2) {
                 *err = "stage-2 contraction longer than 2^23";
                 return DMRG_ERR_INVALID_ARG;
             }
+            // the intermediate side: vectors v*rows + i (A-first, L) or v*cols + j (B-first, R)
+            const int32_t ij = order == 0 ? add_job(1, SPL_TM, int64_t(nv) * O.rows, K, {})
+                                          : add_job(1, SPL_TN, int64_t(nv) * O.cols, K, {});
+            const int32_t oj = order == 0 ? add_job(0, SPL_TN, O.cols, K, opseg) : add_job(0, SPL_TM, O.rows, K, opseg);
+            for (int32_t g : gs) dst_of[size_t(g)] = ij;
+            const SJob IJ = jobs[size_t(ij)];
+            const SJob OJ = jobs[size_t(oj)];
             SGemm m{};
+            m.kind = 1; m.sign = 1;
             m.M = order == 0 ? nv * O.rows : O.rows;
             m.N = order == 0 ? O.cols : nv * O.cols;
             m.kt = int32_t(cdiv(K, SPL_TK));
-            int64_t lt, le, rt, re;
-            const int lbuf = order == 0 ? 1 : 0, rbuf = order == 0 ? 0 : 1;
-            int32_t lj = add_job(lbuf, SPL_TM, m.M, K, lseg, &lt, &le);
-            int32_t rj = add_job(rbuf, SPL_TN, m.N, K, rseg, &rt, &re);
-            for (int32_t g : by_out[o])   // stage-1 GEMMs whose rows feed this job's vectors
-                if (P.groups[g].order == order) gemms[g].x2_exp = order == 0 ? le : re;
-            (lbuf ? mid_jobs : op_jobs).push_back(lj);
-            (rbuf ? mid_jobs : op_jobs).push_back(rj);
-            m.l_tiles = lt; m.r_tiles = rt; m.l_buf = lbuf; m.r_buf = rbuf;
-            m.d_off = s2; m.ldd = m.N; m.kind = 1; m.sign = 1;
+            m.l_buf = order == 0 ? 1 : 0; m.r_buf = order == 0 ? 0 : 1;
+            m.l_tiles = order == 0 ? IJ.out_tiles : OJ.out_tiles;
+            m.r_tiles = order == 0 ? OJ.out_tiles : IJ.out_tiles;
+            m.d_off = s2; m.ldd = m.N;
             m.fshift = fshift_for(K);
             SPart part{};
-            part.acc_off = s2; part.er_off = le; part.ec_off = re; part.er_buf = lbuf; part.ec_buf = rbuf;
+            part.acc_off = s2;
+            part.er_off = order == 0 ? IJ.out_exp : OJ.out_exp;
+            part.ec_off = order == 0 ? OJ.out_exp : IJ.out_exp;
+            part.er_buf = order == 0 ? 1 : 0;
+            part.ec_buf = order == 0 ? 0 : 1;
             part.e_off = 14 + m.fshift; part.ld = m.N;
             part.rstack = order == 0 ? O.rows : 0;
             part.cstack = order == 0 ? 0 : O.cols;
-            parts.push_back(part);
-            blocks[o].np += 1;
+            H.parts.push_back(part);
+            H.blocks[o].np += 1;
             s2 += int64_t(m.M) * m.N;
-            gemms.push_back(m);
+            s2g.push_back(m);
         }
     }
+    H.ap_ex_mid1 = ap_ex;
+    // stage 1: one GEMM per group; L = stacked operator rows (c_t A_t or B_t), R = psi
+    for (size_t g = 0; g < P.groups.size(); ++g) {
+        const Group& G = P.groups[g];
+        const int n = int(G.terms.size());
+        const int32_t xi = xjob(G.in_block, G.order);
+        const SXJob X = H.xjobs[size_t(xi)];
+        const SJob XJ = jobs[size_t(X.job)];   // copies: add_job below may reallocate
+        const int per = G.order == 0 ? G.a : G.d;
+        int32_t lj;
+        if (G.order == 0)   // X_g = A_stack (n a x b) * [x_q^(v)] (b x nv c)
+            lj = add_job(0, SPL_TM, int64_t(n) * G.a, G.b, {seg(G.a_stack, 0, G.b, G.b, G.b, 1)});
+        else                // Z_g^T = B_stack (n d x c) * [x_q^(v)T] (c x nv b)
+            lj = add_job(0, SPL_TM, int64_t(n) * G.d, G.c, {seg(G.b_stack, 0, G.c, G.c, G.c, 1)});
+        jobs[size_t(lj)].top_sums = 1;
+        const SJob LJ = jobs[size_t(lj)];
+        if (dst_of[g] < 0) {
+            *err = "split plan: a group without its output block";
+            return DMRG_ERR_INVALID_ARG;
+        }
+        const SJob DJ = jobs[size_t(dst_of[g])];
+        SGemm m{};
+        m.kind = 0;
+        m.M = n * per; m.N = nv * X.cp; m.kt = LJ.kt;
+        m.l_buf = 0; m.r_buf = 1; m.l_tiles = LJ.out_tiles; m.r_tiles = XJ.out_tiles;
+        m.sign = G.sign < 0 ? -1 : 1;
+        m.fshift = fshift_for(X.K);
+        m.per = per; m.cp = X.cp; m.kbase = kbase_of[g];
+        m.d_off = DJ.out_tiles; m.dst_rows_tile = DJ.rows_tile; m.dst_kt = DJ.kt; m.dst_exp = int32_t(DJ.out_exp);
+        m.er_off = int32_t(LJ.out_exp); m.ec_off = int32_t(XJ.out_exp);
+        H.gemms.push_back(m);
+    }
+    for (const SGemm& m : s2g) H.gemms.push_back(m);
+    if (op_ex > INT32_MAX || ap_ex > INT32_MAX) {
+        *err = "split plan: exponent tables beyond 2^31 entries";
+        return DMRG_ERR_INVALID_ARG;
+    }
     build_split_work(H, S);
-    std::vector<SSlab>& slabs = H.slabs;
-    std::vector<SItem>& items = H.items;
-    auto add_items = [&](const std::vector<int32_t>& js) {
-        for (int32_t j : js) {
-            int32_t kb = 0;
-            for (int sg = jobs[j].seg0; sg < jobs[j].seg0 + jobs[j].nseg; ++sg) {
-                const int64_t n = int64_t(segs[sg].nt) * jobs[j].nvalid;
-                if (n > 0) {
-                    const int32_t sl = int32_t(slabs.size());
-                    slabs.push_back({n, j, sg, kb, 0});
-                    for (int64_t r0 = 0; r0 < n; r0 += SPL_ROWS_PER_ITEM)
-                        items.push_back({r0, sl, int32_t(std::min<int64_t>(SPL_ROWS_PER_ITEM, n - r0))});
-                }
-                kb += segs[sg].kc * segs[sg].nt;
+    // operator slicing work: exponent items (rows of every segment) and digit tiles
+    for (int32_t j : op_jobs) {
+        const SJob& J = jobs[size_t(j)];
+        for (int sg = J.seg0; sg < J.seg0 + J.nseg; ++sg) {
+            const int64_t rows = int64_t(segs[size_t(sg)].nt) * J.nvalid;
+            if (rows == 0) continue;
+            const int32_t sl = int32_t(H.slabs.size());
+            H.slabs.push_back({rows, j, sg, segs[size_t(sg)].kbase, 0});
+            for (int64_t r0 = 0; r0 < rows; r0 += SPL_ROWS_PER_ITEM)
+                H.items.push_back({r0, sl, int32_t(std::min<int64_t>(SPL_ROWS_PER_ITEM, rows - r0))});
+        }
+        for (int vg = 0; 8 * vg < J.nvalid; ++vg) {
+            int32_t sg = J.seg0;
+            for (int k0 = 0; k0 < J.K; k0 += SPL_TILE_K) {
+                while (sg < J.seg0 + J.nseg - 1 && k0 >= segs[size_t(sg)].kbase + segs[size_t(sg)].kcp * segs[size_t(sg)].nt)
+                    ++sg;
+                H.tiles.push_back({j, vg, k0, sg});
             }
         }
-    };
-    H.it_op0 = 0;
-    add_items(op_jobs);
-    H.it_x0 = int64_t(items.size());
-    add_items(x_jobs);
-    H.it_mid0 = int64_t(items.size());
-    add_items(mid_jobs);
-    H.it_end = int64_t(items.size());
-    std::vector<STile>& tiles = H.tiles;
-    auto add_tiles = [&](const std::vector<int32_t>& js) {
-        for (int32_t j : js)
-            for (int vg = 0; 8 * vg < jobs[j].nvalid; ++vg) {
-                int32_t sg = jobs[j].seg0;
-                for (int k0 = 0; k0 < jobs[j].K; k0 += SPL_TILE_K) {
-                    while (sg < jobs[j].seg0 + jobs[j].nseg - 1 && k0 >= segs[sg].kbase + segs[sg].kc * segs[sg].nt)
-                        ++sg;
-                    tiles.push_back({j, vg, k0, sg});
-                }
-            }
-    };
-    H.tl_op0 = 0;
-    add_tiles(op_jobs);
-    H.tl_x0 = int64_t(tiles.size());
-    add_tiles(x_jobs);
-    H.tl_mid0 = int64_t(tiles.size());
-    add_tiles(mid_jobs);
-    H.tl_end = int64_t(tiles.size());
+    }
     H.op_sl = op_sl;
     H.op_ex = op_ex + 1;
     H.ap_sl_vs = cdiv(ap_sl, 64) * 64;
     H.ap_ex_vs = cdiv(ap_ex, 4) * 4 + 4;
-    H.s1_vs = P.scratch_len * nv;
     H.s2_vs = s2;
-    H.nv = nv;
     return validate_split_plan(P, H, err);
 }
 
@@ -1162,7 +1543,7 @@ int Handle::init_split() {
     std::string err;
     // one plan per number of stacked vectors; operator slices are identical in all of them
     std::vector<SplitHost> hosts(static_cast<size_t>(max_nvec));
-    int64_t ap_sl = 0, ap_ex = 0, s1 = 0, s2 = 0;
+    int64_t ap_sl = 0, ap_ex = 0, s2 = 0;
     for (int nv = 1; nv <= max_nvec; ++nv) {
         SplitHost& H = hosts[size_t(nv - 1)];
         const int rc0 = build_split_plan(P, nv, H, &err);
@@ -1171,7 +1552,6 @@ int Handle::init_split() {
             return fail(DMRG_ERR_BOUNDS, "operator slice layout differs between plans");
         ap_sl = std::max(ap_sl, H.ap_sl_vs);
         ap_ex = std::max(ap_ex, H.ap_ex_vs);
-        s1 = std::max(s1, H.s1_vs);
         s2 = std::max(s2, H.s2_vs);
     }
     const int64_t op_sl = hosts[0].op_sl, op_ex = hosts[0].op_ex;
@@ -1190,9 +1570,10 @@ int Handle::init_split() {
     int rc;
     if ((rc = al((void**)&S->op_sl, sizeof(uint16_t) * op_sl, "operator slices")) ||
         (rc = al((void**)&S->op_ex, sizeof(int32_t) * op_ex, "operator exponents")) ||
+        (rc = al((void**)&S->srow, sizeof(int32_t) * op_ex, "operator top-digit sums")) ||
         (rc = al((void**)&S->ap_sl, sizeof(uint16_t) * ap_sl, "apply slices")) ||
         (rc = al((void**)&S->ap_ex, sizeof(int32_t) * ap_ex, "apply exponents")) ||
-        (rc = al((void**)&S->s1, sizeof(int64_t) * s1, "stage-1 int64 results")) ||
+        (rc = al((void**)&S->xs, sizeof(float) * ap_ex, "psi sums")) ||
         (rc = al((void**)&S->s2, sizeof(int64_t) * s2, "stage-2 int64 sums")) ||
         (rc = al((void**)&S->status, sizeof(int32_t), "status")))
         return rc;
@@ -1205,6 +1586,7 @@ int Handle::init_split() {
             (rc = up((void**)&D.work2, H.w2.data(), sizeof(SWork) * H.w2.size(), "split work")) ||
             (rc = up((void**)&D.segs, H.segs.data(), sizeof(SSeg) * H.segs.size(), "slice segments")) ||
             (rc = up((void**)&D.jobs, H.jobs.data(), sizeof(SJob) * H.jobs.size(), "slice jobs")) ||
+            (rc = up((void**)&D.xjobs, H.xjobs.data(), sizeof(SXJob) * H.xjobs.size(), "psi jobs")) ||
             (rc = up((void**)&D.slabs, H.slabs.data(), sizeof(SSlab) * H.slabs.size(), "slice slabs")) ||
             (rc = up((void**)&D.items, H.items.data(), sizeof(SItem) * H.items.size(), "slice items")) ||
             (rc = up((void**)&D.tiles, H.tiles.data(), sizeof(STile) * H.tiles.size(), "slice tiles")) ||
@@ -1216,17 +1598,25 @@ int Handle::init_split() {
         D.r1 = H.r1;
         D.r2 = H.r2;
         D.n_blocks = int64_t(H.blocks.size());
-        D.it_op0 = H.it_op0; D.it_x0 = H.it_x0; D.it_mid0 = H.it_mid0; D.it_end = H.it_end;
-        D.tl_op0 = H.tl_op0; D.tl_x0 = H.tl_x0; D.tl_mid0 = H.tl_mid0; D.tl_end = H.tl_end;
-        D.ap_ex_len = H.ap_ex_vs;
+        D.n_xjobs = int64_t(H.xjobs.size());
+        D.n_items = int64_t(H.items.size());
+        D.n_tiles = int64_t(H.tiles.size());
         D.s2_len = H.s2_vs;
-        // algorithmic DRAM bytes of the two slice-GEMM launches: slice tiles read once
-        // (12 B per entry) plus the int64 results written (stage 1) or added (stage 2)
-        for (size_t gi = 0; gi < H.gemms.size(); ++gi) {
-            const SGemm& m = H.gemms[gi];
-            const double bytes = 12.0 * (double(m.M) + m.N) * m.kt * SPL_TK + 8.0 * double(m.M) * m.N;
-            (m.kind == 0 ? D.s1_bytes : D.s2_bytes) += bytes;
+        D.mid0 = H.ap_ex_mid0;
+        D.mid1 = H.ap_ex_mid1;
+        // algorithmic DRAM bytes: slice tiles read once (12 B per entry), stage-1 digit
+        // slices written (12 B per entry), stage-2 int64 sums added (8 B per entry); the
+        // psi pass reads psi and writes its slices
+        for (const SGemm& m : H.gemms) {
+            const double rd = 12.0 * (double(m.M) + m.N) * m.kt * SPL_TK;
+            if (m.kind == 0) {
+                D.s1_bytes += rd + 12.0 * double(m.M) * m.N;
+                D.e_bytes += rd / SPL_S;   // the estimate pass reads slice 0 only
+            } else {
+                D.s2_bytes += rd + 8.0 * double(m.M) * m.N;
+            }
         }
+        for (const SXJob& X : H.xjobs) D.x_bytes += double(nv) * (8.0 * X.K * X.nk + 12.0 * X.K * X.cp);
     }
     for (const SplitHost& H : hosts) {
         S->cap_w1.push_back(H.w1.size());
@@ -1237,25 +1627,28 @@ int Handle::init_split() {
     if (e != cudaSuccess) return cuda_fail(e, "status");
     e = cudaFuncSetAttribute(k_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(UmmaSmem)));
     if (e != cudaSuccess) return cuda_fail(e, "umma shared memory");
-    S->kid_x = prof.kernel_id("split_slice/x");
+    e = cudaFuncSetAttribute(k_uest, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(EstSmem)));
+    if (e != cudaSuccess) return cuda_fail(e, "estimate shared memory");
+    S->kid_x = prof.kernel_id("split_xprep");
+    S->kid_e = prof.kernel_id("split_estimate");
     S->kid_s1 = prof.kernel_id("umma_slices/stage1");
-    S->kid_mid = prof.kernel_id("split_slice/intermediate");
     S->kid_s2 = prof.kernel_id("umma_slices/stage2");
     S->kid_fin = prof.kernel_id("split_finalize");
     // slice buffers start at zero (padding is never written again), exponents at "none"
     if (op_sl > 0 && (e = cudaMemset(S->op_sl, 0, sizeof(uint16_t) * op_sl)) != cudaSuccess) return cuda_fail(e, "zero slices");
     if (ap_sl > 0 && (e = cudaMemset(S->ap_sl, 0, sizeof(uint16_t) * ap_sl)) != cudaSuccess) return cuda_fail(e, "zero slices");
     if ((e = cudaMemset(S->op_ex, 0xC0, sizeof(int32_t) * op_ex)) != cudaSuccess) return cuda_fail(e, "exponents");
+    if ((e = cudaMemset(S->srow, 0, sizeof(int32_t) * op_ex)) != cudaSuccess) return cuda_fail(e, "top-digit sums");
+    if (ap_ex > 0 && (e = cudaMemset(S->ap_ex, 0xE0, sizeof(int32_t) * ap_ex)) != cudaSuccess) return cuda_fail(e, "exponents");
     // operator slices, once (from the first plan; every plan has the same operator jobs)
     const SplitDevPlan& D0 = S->plans[0];
-    if (D0.it_x0 > D0.it_op0) {
-        SliceArgs sa{D0.items + D0.it_op0, D0.it_x0 - D0.it_op0, D0.slabs, D0.jobs, D0.segs, d_ops, nullptr, 0,
-                     nullptr, 0, S->op_sl, S->ap_sl, 0, S->op_ex, S->ap_ex, 0, 1};
-        TileArgs ta{D0.tiles + D0.tl_op0, D0.tl_x0 - D0.tl_op0, D0.jobs, D0.segs, d_ops, nullptr, 0, nullptr, 0,
-                    S->op_sl, S->ap_sl, 0, S->op_ex, S->ap_ex, 0, 1};
-        k_slice_max<<<unsigned(std::min<int64_t>(D0.it_x0 - D0.it_op0, int64_t(n_sm) * 16)), 256>>>(sa);
-        k_slice_digits<<<unsigned(std::min<int64_t>(cdiv(D0.tl_x0 - D0.tl_op0, DIG_WARPS), int64_t(n_sm) * 16)),
-                         32 * DIG_WARPS>>>(ta);
+    if (D0.n_items > 0) {
+        SliceArgs sa{D0.items, D0.n_items, D0.slabs, D0.jobs, D0.segs, d_ops, S->op_ex};
+        TileArgs ta{D0.tiles, D0.n_tiles, D0.jobs, D0.segs, d_ops, S->op_sl, S->op_ex, S->srow};
+        k_slice_max<<<unsigned(std::min<int64_t>(D0.n_items, int64_t(n_sm) * 16)), 256>>>(sa);
+        if (D0.n_tiles > 0)
+            k_slice_digits<<<unsigned(std::min<int64_t>(cdiv(D0.n_tiles, DIG_WARPS), int64_t(n_sm) * 16)),
+                             32 * DIG_WARPS>>>(ta);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return cuda_fail(e, "operator slicing");
@@ -1263,35 +1656,21 @@ int Handle::init_split() {
     return DMRG_OK;
 }
 
-// One split H_eff*psi for nvec stacked vectors: slice x, stage-1 slice GEMM (int64 results,
-// stage-2 exponents raised), slice intermediates, stage-2 slice GEMM (int64 sums), finalize.
+// One split H_eff*psi for nvec stacked vectors: psi pass (exponents, bounds, slices;
+// stage-2 sums cleared), stage-1 slice GEMM (its epilogue writes the stage-2 slices),
+// stage-2 slice GEMM (int64 sums), finalize.
 int Handle::apply_split(const double* x, double* y, int32_t nvec, cudaStream_t st) {
     SplitState* S = split;
     const SplitDevPlan& D = S->plans[size_t(nvec - 1)];
     Profiler::Pending pe;
     cudaError_t e;
-    const int64_t slice_grid_cap = int64_t(n_sm) * 16;
-    auto slice = [&](int64_t i0, int64_t i1, int64_t t0, int64_t t1, bool with_max, int kid) {
-        if (t1 == t0) return cudaSuccess;
-        SliceArgs sa{D.items + i0, i1 - i0, D.slabs, D.jobs, D.segs, d_ops, x, 0, S->s1, 0,
-                     S->op_sl, S->ap_sl, 0, S->op_ex, S->ap_ex, 0, 1};
-        TileArgs ta{D.tiles + t0, t1 - t0, D.jobs, D.segs, d_ops, x, 0, S->s1, 0, S->op_sl,
-                    S->ap_sl, 0, S->op_ex, S->ap_ex, 0, 1};
-        prof.begin(kid, st, 0.0, 0.0, &pe);
-        if (with_max && i1 > i0)
-            k_slice_max<<<unsigned(std::min<int64_t>(i1 - i0, slice_grid_cap)), 256, 0, st>>>(sa);
-        k_slice_digits<<<unsigned(std::min<int64_t>(cdiv(t1 - t0, DIG_WARPS), slice_grid_cap)), 32 * DIG_WARPS, 0,
-                         st>>>(ta);
-        prof.end(pe, st);
-        return cudaGetLastError();
-    };
     // one stage: a single persistent launch over its work list, or (per_gemm) one launch
     // per GEMM over that GEMM's contiguous range
     auto gemm = [&](const SWork* w, int64_t nw, const std::vector<std::pair<int32_t, int32_t>>& rg, int kid,
                     double flops, double bytes) {
         if (nw == 0) return cudaSuccess;
         auto launch = [&](const SWork* w0, int64_t n) {
-            UmmaArgs ua{w0, n, D.gemms, S->op_sl, S->ap_sl, S->s1, S->s2, S->op_ex, S->ap_ex, S->status};
+            UmmaArgs ua{w0, n, D.gemms, S->op_sl, S->ap_sl, S->s2, S->op_ex, S->ap_ex, S->status};
             k_umma<<<unsigned(std::min<int64_t>(n, n_sm)), UM_THREADS, sizeof(UmmaSmem), st>>>(ua);
             return cudaGetLastError();
         };
@@ -1305,22 +1684,28 @@ int Handle::apply_split(const double* x, double* y, int32_t nvec, cudaStream_t s
         prof.end(pe, st);
         return le;
     };
-    if ((e = cudaMemsetAsync(S->ap_ex, 0xC0, sizeof(int32_t) * D.ap_ex_len, st)) != cudaSuccess)
-        return cuda_fail(e, "reset exponents");
-    if ((e = slice(D.it_x0, D.it_mid0, D.tl_x0, D.tl_mid0, true, S->kid_x)) != cudaSuccess)
-        return cuda_fail(e, "slice x");
+    if (D.n_xjobs > 0) {
+        XArgs xa{D.xjobs, D.jobs, x, plan.dim, S->ap_sl, S->ap_ex, S->xs, S->s2, D.s2_len, D.mid0, D.mid1};
+        prof.begin(S->kid_x, st, 0.0, D.x_bytes, &pe);
+        k_xprep<<<dim3(unsigned(D.n_xjobs), unsigned(nvec)), 256, 0, st>>>(xa);
+        prof.end(pe, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "psi slices");
+    }
+    if (D.n_work1 > 0) {   // the stage-2 vector bounds, over the stage-1 work list
+        EstArgs ea{D.work1, D.n_work1, D.gemms, S->op_sl, S->ap_sl, S->op_ex, S->ap_ex, S->srow, S->xs, S->status};
+        prof.begin(S->kid_e, st, 0.0, D.e_bytes, &pe);
+        k_uest<<<unsigned(std::min<int64_t>(D.n_work1, n_sm)), UM_THREADS, sizeof(EstSmem), st>>>(ea);
+        prof.end(pe, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "estimate pass");
+    }
     if ((e = gemm(D.work1, D.n_work1, D.r1, S->kid_s1, s1_flops * nvec, D.s1_bytes)) != cudaSuccess)
         return cuda_fail(e, "stage-1 slice gemm");
-    if ((e = slice(D.it_mid0, D.it_end, D.tl_mid0, D.tl_end, false, S->kid_mid)) != cudaSuccess)
-        return cuda_fail(e, "slice intermediates");
-    if (D.s2_len > 0 && (e = cudaMemsetAsync(S->s2, 0, sizeof(int64_t) * D.s2_len, st)) != cudaSuccess)
-        return cuda_fail(e, "zero stage-2 sums");
     if ((e = gemm(D.work2, D.n_work2, D.r2, S->kid_s2, s2_flops * nvec, D.s2_bytes)) != cudaSuccess)
         return cuda_fail(e, "stage-2 slice gemm");
     if (D.n_blocks > 0) {
         prof.begin(S->kid_fin, st, 0.0, 0.0, &pe);
-        k_finalize<<<dim3(unsigned(D.n_blocks), unsigned(nvec)), 256, 0, st>>>(D.blocks, D.parts, S->s2, 0, S->op_ex,
-                                                                              S->ap_ex, 0, y, plan.dim);
+        k_finalize<<<dim3(unsigned(D.n_blocks), unsigned(nvec)), 256, 0, st>>>(D.blocks, D.parts, S->s2, S->op_ex,
+                                                                              S->ap_ex, y, plan.dim);
         prof.end(pe, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "finalize");
     }
