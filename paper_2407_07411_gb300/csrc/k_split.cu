@@ -1070,26 +1070,29 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_uest(EstArgs a) {
             if (!ok) break;
             const int i = rv_ok ? r % G.per : 0;
             const float sa = float(sa_i) * (1.005f / 32768.0f);
-            int vprev = -1, Emax = SPL_EXP_NONE;
+            // the Davidson vector of the columns changes at multiples of cp (>= 8), the
+            // same for every lane: no division per column
+            int v = cbase / G.cp, vend = (v + 1) * G.cp, Emax = SPL_EXP_NONE;
+            const bool row_ok = rv_ok && ea > -(1 << 28);
+            int32_t* dst = a.ap_ex + G.dst_exp + i;
 #pragma unroll
             for (int j = 0; j < UM_EPI_COLS; ++j) {
                 const int ex = __shfl_sync(0xffffffffu, ex_lane, j);
                 const float xsj = __shfl_sync(0xffffffffu, xs_lane, j);
                 const int col = cbase + j;
-                if (!rv_ok || col >= G.N || ex < SPL_EXP_NONE / 2 || ea < -(1 << 28)) continue;
-                const int v = col / G.cp;
-                if (v != vprev) {
-                    if (vprev >= 0 && Emax > SPL_EXP_NONE) atomicMax(a.ap_ex + G.dst_exp + vprev * G.per + i, Emax);
-                    vprev = v;
+                if (col >= vend) {
+                    if (row_ok && Emax > SPL_EXP_NONE) atomicMax(dst + v * G.per, Emax);
+                    ++v;
+                    vend += G.cp;
                     Emax = SPL_EXP_NONE;
                 }
                 const float f = (float(abs(acc[j])) * (1.0f / 16384.0f) + xsj + sa) * (1.0f + 1.0f / 1048576.0f) +
                                 (1.0f / 1073741824.0f);
                 // f is a positive normal float: f < 2^(biased exponent - 126)
                 const int e = int((__float_as_uint(f) >> 23) & 255u) - 126;
-                Emax = max(Emax, ea + ex + e);
+                if (col < G.N && ex > SPL_EXP_NONE / 2) Emax = max(Emax, ea + ex + e);
             }
-            if (vprev >= 0 && Emax > SPL_EXP_NONE) atomicMax(a.ap_ex + G.dst_exp + vprev * G.per + i, Emax);
+            if (row_ok && Emax > SPL_EXP_NONE) atomicMax(dst + v * G.per, Emax);
         }
     }
     tc_fence_before();
