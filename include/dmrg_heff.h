@@ -63,13 +63,19 @@ typedef struct dmrg_heff* dmrg_heff_t;
 
 typedef struct {
     int32_t precision;  /* DMRG_PREC_*                                               */
-    int32_t n_slices;   /* split path: digit slices per operand (0 = default)        */
+    int32_t n_slices;   /* split path: digit slices per operand, 0 or 6 (the only
+                           count built; others give DMRG_ERR_UNSUPPORTED)            */
     int32_t max_nvec;   /* largest nvec passed to apply (sizes the scratch), >= 1   */
     int32_t flags;      /* DMRG_FLAG_* bits                                           */
+    int64_t split_mid_bytes;  /* split path: device bytes of stage-2 intermediate
+                           slices per output chunk (0 = 64 GiB).  An apply takes the
+                           output blocks in chunks whose intermediates fit under it and
+                           reuses one buffer for them; results do not depend on it.  */
 } dmrg_heff_opts;
 
 /* Build only the host-side plan: no device memory is touched, so the handle works
- * without a GPU; only dmrg_heff_dim, _flops, _plan_dump and _destroy may be called. */
+ * without a GPU; only dmrg_heff_dim, _flops, _memory, _plan_dump and _destroy may be
+ * called. */
 #define DMRG_FLAG_PLAN_ONLY 1
 /* Launch every apply kernel directly instead of replaying a CUDA graph.  By default
  * each apply is captured once per (x, y, nvec) into a graph (up to 64 per handle) and
@@ -148,6 +154,22 @@ int64_t dmrg_heff_dim(dmrg_heff_t h);
 /* Algorithmic flops of one H_eff*psi for one vector: the sum over the plan of the
  * cheaper order's 2abc + 2acd or 2bcd + 2abd. */
 int dmrg_heff_flops(dmrg_heff_t h, int64_t* flops);
+
+/* Device memory of a handle, in bytes (for a plan-only handle: what a full handle with
+ * the same options would hold).
+ *   operators        the FP64 operator copy in the grouped layout (FP64 handles; a split
+ *                    handle keeps none after set-up)
+ *   operator_slices  split handles: the operators' digit slices, exponents and row sums
+ *   apply_buffers    per-apply buffers for max_nvec vectors: FP64 stage-1 scratch and
+ *                    split-K partials, or the split path's psi and intermediate slices,
+ *                    exponents and stage-2 sums
+ *   setup_peak       the largest transient buffer of set-up (split: the operator staging
+ *                    buffer the FP64 operators are streamed through, block by block)
+ *   total            operators + operator_slices + apply_buffers */
+typedef struct {
+    int64_t operators, operator_slices, apply_buffers, setup_peak, total;
+} dmrg_memory;
+int dmrg_heff_memory(dmrg_heff_t h, dmrg_memory* m);
 
 /* Canonical plan: rows (out_block, term, in_block, order 0=A-first 1=B-first, flops),
  * int64, sorted by (out_block, term, in_block).  Call with buf = NULL to get *n_rows;

@@ -33,12 +33,18 @@ SYMBOLS = ("dmrg_heff_create", "dmrg_heff_dim", "dmrg_heff_flops", "dmrg_heff_pl
            "dmrg_heff_profile_read", "dmrg_probe_fp64_peak", "dmrg_heff_apply_noalloc",
            "dmrg_selftest_wait_timeout", "dmrg_heff_schedule_get", "dmrg_heff_schedule_set",
            "dmrg_heff_autotune", "dmrg_heff_gemm_count", "dmrg_lanczos", "dmrg_renormalise",
-           "dmrg_heff_psi_blocks", "dmrg_svd_truncate", "dmrg_heff_create_su2", "dmrg_su2_recoupling")
+           "dmrg_heff_psi_blocks", "dmrg_svd_truncate", "dmrg_heff_create_su2", "dmrg_su2_recoupling",
+           "dmrg_heff_memory")
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("n_slices", ctypes.c_int32),
-                ("max_nvec", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("max_nvec", ctypes.c_int32), ("flags", ctypes.c_int32), ("split_mid_bytes", ctypes.c_int64)]
+
+
+class Memory(ctypes.Structure):
+    _fields_ = [("operators", ctypes.c_int64), ("operator_slices", ctypes.c_int64),
+                ("apply_buffers", ctypes.c_int64), ("setup_peak", ctypes.c_int64), ("total", ctypes.c_int64)]
 
 
 class DavidsonInfo(ctypes.Structure):
@@ -91,6 +97,7 @@ _lib.dmrg_su2_recoupling.argtypes = [_i32, _i32, _i32, _i32, _i32, _i32, ctypes.
 _lib.dmrg_heff_dim.argtypes = [_P]
 _lib.dmrg_heff_dim.restype = _i64
 _lib.dmrg_heff_flops.argtypes = [_P, ctypes.POINTER(_i64)]
+_lib.dmrg_heff_memory.argtypes = [_P, ctypes.POINTER(Memory)]
 _lib.dmrg_heff_plan_dump.argtypes = [_P, _P, ctypes.POINTER(_i64)]
 _lib.dmrg_heff_apply.argtypes = [_P, _P, _P, _i32, _P]
 _lib.dmrg_heff_apply_host.argtypes = [_P, _P, _P, _i32]
@@ -165,7 +172,7 @@ class HEff:
 
     def __init__(self, left, right, target, coef, delta, parity, a_off, b_off, op_data,
                  precision: str = "fp64", max_nvec: int = 1, n_slices: int = 0, plan_only: bool = False,
-                 graphs: bool = True):
+                 graphs: bool = True, split_mid_bytes: int = 0):
         self._h = None
         arr = lambda a, dt: np.ascontiguousarray(np.asarray(a, dtype=dt))
         self._left = arr(left, np.int32).reshape(-1, 3)
@@ -177,7 +184,7 @@ class HEff:
         b_off = arr(b_off, np.int64).reshape(T, len(self._right))
         op_data = arr(op_data, np.float64)
         opts = Opts(_PREC[precision] if isinstance(precision, str) else int(precision), n_slices, max_nvec,
-                    (FLAG_PLAN_ONLY if plan_only else 0) | (0 if graphs else FLAG_NO_GRAPH))
+                    (FLAG_PLAN_ONLY if plan_only else 0) | (0 if graphs else FLAG_NO_GRAPH), int(split_mid_bytes))
         h = ctypes.c_void_p()
         _check(_lib.dmrg_heff_create(_ptr(self._left), len(self._left), _ptr(self._right), len(self._right),
                                      int(target[0]), int(target[1]), _ptr(coef), _ptr(delta), _ptr(parity),
@@ -198,7 +205,7 @@ class HEff:
 
     @classmethod
     def from_su2(cls, p, precision: str = "fp64", max_nvec: int = 1, n_slices: int = 0, plan_only: bool = False,
-                 graphs: bool = True) -> "HEff":
+                 graphs: bool = True, split_mid_bytes: int = 0) -> "HEff":
         """Spin-adapted handle (dmrg_heff_create_su2) from an object with the fields
         left, right, target, coef, rank2, dn, parity, a_blocks, b_blocks, op_data."""
         self = cls.__new__(cls)
@@ -212,7 +219,7 @@ class HEff:
         bb = arr(p.b_blocks, np.int64).reshape(-1, 4)
         op_data = arr(p.op_data, np.float64)
         opts = Opts(_PREC[precision] if isinstance(precision, str) else int(precision), n_slices, max_nvec,
-                    (FLAG_PLAN_ONLY if plan_only else 0) | (0 if graphs else FLAG_NO_GRAPH))
+                    (FLAG_PLAN_ONLY if plan_only else 0) | (0 if graphs else FLAG_NO_GRAPH), int(split_mid_bytes))
         h = ctypes.c_void_p()
         _check(_lib.dmrg_heff_create_su2(_ptr(self._left), len(self._left), _ptr(self._right), len(self._right),
                                          int(p.target[0]), int(p.target[1]), _ptr(coef), _ptr(rank2), _ptr(dn),
@@ -243,6 +250,13 @@ class HEff:
         f = _i64()
         _check(_lib.dmrg_heff_flops(self._h, ctypes.byref(f)))
         return int(f.value)
+
+    def memory(self) -> dict:
+        """Device bytes of the handle (dmrg_heff_memory): operators, operator_slices,
+        apply_buffers, setup_peak, total."""
+        m = Memory()
+        _check(_lib.dmrg_heff_memory(self._h, ctypes.byref(m)))
+        return {k: int(getattr(m, k)) for k, _ in Memory._fields_}
 
     def plan_dump(self) -> np.ndarray:
         n = _i64(0)

@@ -71,7 +71,8 @@ struct Handle : dmrg_heff {
     int precision = 0, max_nvec = 1, n_slices = 0;
     int device = 0, n_sm = 152, tiles_per_sm = 8;
     bool plan_only = false;
-    int64_t split_host_bytes = 0;   // plan-only split handles: device bytes the plan needs
+    dmrg_memory mem{};              // device bytes (plan-only handles: what they would hold)
+    int64_t split_mid_cap = 0;      // split path: intermediate bytes per output chunk (0: default)
     double* d_ops = nullptr;
     double* d_scr = nullptr;
     double* d_part = nullptr;
@@ -94,6 +95,7 @@ struct Handle : dmrg_heff {
     double* d_ystage = nullptr;
     DiagJob* d_diag_jobs = nullptr;
     int32_t n_diag_jobs = 0;
+    double* d_diag = nullptr;       // split handles: the diagonal, formed at set-up
     SplitState* split = nullptr;
     DavidsonState* dav = nullptr;
     Profiler prof;
@@ -113,8 +115,13 @@ struct Handle : dmrg_heff {
     int apply_fp64(const double* x, double* y, int32_t nvec, cudaStream_t st);
     int init_diag();
     int diagonal(double* diag, cudaStream_t st);
-    // split-precision path (k_split.cu)
-    int init_split();   // slices the device operator copy
+    // forms the diagonal blocks whose stacks lie in layout entries [lo, hi) from the
+    // layout entries held in ops (entry ops_lo first)
+    cudaError_t launch_diag(const double* ops, int64_t ops_lo, int64_t lo, int64_t hi, double* diag,
+                            cudaStream_t st);
+    // split-precision path (k_split.cu): streams the operators window by window through
+    // a device staging buffer into the slicer and the diagonal (no resident FP64 copy)
+    int init_split(const double* op_data);
     int apply_split(const double* x, double* y, int32_t nvec, cudaStream_t st);
     void release_split();
     // reads and clears the device status word of the split kernels (synchronises)
@@ -123,7 +130,5 @@ struct Handle : dmrg_heff {
     void release_davidson();
 };
 
-cudaError_t launch_diag(const DiagJob* jobs, int32_t n_jobs, const double* ops, double* diag,
-                        int64_t dim, cudaStream_t st);
 
 }  // namespace dmrg

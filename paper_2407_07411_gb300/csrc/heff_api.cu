@@ -240,7 +240,7 @@ int Handle::apply_graph(const double* x, double* y, int32_t nvec, cudaStream_t s
 
 Handle::~Handle() {
     void* ptrs[] = {d_ops, d_scr, d_part, d_tiles1, d_tiles2, d_gemms, d_segs, d_red, d_counters,
-                    d_xstage, d_ystage, d_diag_jobs};
+                    d_xstage, d_ystage, d_diag_jobs, d_diag};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     release_split();
@@ -259,12 +259,15 @@ int check_opts(const dmrg_heff_opts* opts, const double* op_data, int64_t op_len
                dmrg_heff_t* out) {
     if (!out) return dmrg::fail(DMRG_ERR_INVALID_ARG, "null output handle");
     *out = nullptr;
-    *o = dmrg_heff_opts{DMRG_PREC_FP64, 0, 1, 0};
+    *o = dmrg_heff_opts{DMRG_PREC_FP64, 0, 1, 0, 0};
     if (opts) *o = *opts;
     if (o->precision != DMRG_PREC_FP64 && o->precision != DMRG_PREC_SPLIT_BF16)
         return dmrg::fail(DMRG_ERR_INVALID_ARG, "unknown precision");
     if (o->max_nvec < 1 || o->max_nvec > 64 || (o->flags & ~(DMRG_FLAG_PLAN_ONLY | DMRG_FLAG_NO_GRAPH)) != 0)
         return dmrg::fail(DMRG_ERR_INVALID_ARG, "max_nvec must be in [1, 64], unknown flags must be 0");
+    if (o->n_slices != 0 && o->n_slices != 6)
+        return dmrg::fail(DMRG_ERR_UNSUPPORTED, "the split path takes 6 digit slices (n_slices 0 or 6)");
+    if (o->split_mid_bytes < 0) return dmrg::fail(DMRG_ERR_INVALID_ARG, "split_mid_bytes must be >= 0");
     if (op_len > 0 && !op_data) return dmrg::fail(DMRG_ERR_INVALID_ARG, "null op_data");
     return DMRG_OK;
 }
@@ -277,18 +280,24 @@ int create_from_plan(Handle* h, const dmrg_heff_opts& o, const double* op_data, 
     h->precision = o.precision;
     h->max_nvec = o.max_nvec;
     h->n_slices = o.n_slices;
+    h->split_mid_cap = o.split_mid_bytes;
     h->plan_only = (o.flags & DMRG_FLAG_PLAN_ONLY) != 0;
     h->use_graphs = (o.flags & DMRG_FLAG_NO_GRAPH) == 0;
+    if (o.precision == DMRG_PREC_FP64) {
+        const dmrg::Plan& P = h->plan;
+        dmrg_memory& m = h->mem;
+        m.operators = 8 * P.ops_len;
+        m.apply_buffers = 8 * int64_t(o.max_nvec) * (P.scratch_len + P.n_slots * dmrg::FP64_BM * dmrg::FP64_BN);
+        m.total = m.operators + m.apply_buffers;
+    }
     if (h->plan_only) {
-        if (o.precision == DMRG_PREC_SPLIT_BF16) {   // host-side split plan and its bounds proof
-            for (int nv = 1; nv <= h->max_nvec; ++nv) {
-                dmrg::SplitHost sh;
-                rc = dmrg::build_split_plan(h->plan, nv, sh, &err);
-                if (rc != DMRG_OK) {
-                    delete h;
-                    return dmrg::fail(rc, err);
-                }
-                h->split_host_bytes = sh.op_sl * 2 + sh.ap_sl_vs * 2 + sh.s2_vs * 8;
+        if (o.precision == DMRG_PREC_SPLIT_BF16) {   // host-side split plans, bounds proof, windows
+            std::vector<dmrg::SplitHost> hosts;
+            std::vector<dmrg::SWindow> win;
+            rc = dmrg::build_split_hosts(h->plan, h->max_nvec, h->split_mid_cap, hosts, win, &h->mem, &err);
+            if (rc != DMRG_OK) {
+                delete h;
+                return dmrg::fail(rc, err);
             }
         }
         *out = h;
@@ -329,9 +338,10 @@ int create_from_plan(Handle* h, const dmrg_heff_opts& o, const double* op_data, 
         delete h;
         return code;
     };
-    // Operators in the grouped device layout, streamed through a bounded host buffer (the
-    // host never holds a second copy of the operator data).
-    if (P.ops_len > 0) {
+    // FP64 handles: the operators in the grouped device layout, streamed through a
+    // bounded host buffer (the host never holds a second copy of the operator data).
+    // Split handles stream them through the slicer instead and keep only the slices.
+    if (P.ops_len > 0 && o.precision == DMRG_PREC_FP64) {
         if ((rc = dmrg::dalloc(reinterpret_cast<void**>(&h->d_ops), sizeof(double) * size_t(P.ops_len),
                                "operators")) != DMRG_OK)
             return bail(rc);
@@ -368,10 +378,11 @@ int create_from_plan(Handle* h, const dmrg_heff_opts& o, const double* op_data, 
         if ((rc = dmrg::dalloc(reinterpret_cast<void**>(&h->d_scr), sizeof(double) * P.scratch_len * nv,
                                "stage-1 scratch")) != DMRG_OK)
             return bail(rc);
+        if ((rc = h->init_diag()) != DMRG_OK) return bail(rc);
     } else {
-        if ((rc = h->init_split()) != DMRG_OK) return bail(rc);
+        if ((rc = h->init_diag()) != DMRG_OK) return bail(rc);
+        if ((rc = h->init_split(op_data)) != DMRG_OK) return bail(rc);
     }
-    if ((rc = h->init_diag()) != DMRG_OK) return bail(rc);
     *out = h;
     return DMRG_OK;
 }
@@ -436,6 +447,12 @@ int64_t dmrg_heff_dim(dmrg_heff_t h) { return h ? static_cast<Handle*>(h)->plan.
 int dmrg_heff_flops(dmrg_heff_t h, int64_t* flops) {
     if (!h || !flops) return dmrg::fail(DMRG_ERR_INVALID_ARG, "null argument");
     *flops = static_cast<Handle*>(h)->plan.flops;
+    return DMRG_OK;
+}
+
+int dmrg_heff_memory(dmrg_heff_t h, dmrg_memory* m) {
+    if (!h || !m) return dmrg::fail(DMRG_ERR_INVALID_ARG, "null argument");
+    *m = static_cast<Handle*>(h)->mem;
     return DMRG_OK;
 }
 

@@ -1,6 +1,7 @@
 // Diagonal of H_eff, the Davidson preconditioner's input: only groups whose output
 // block is their input block (Delta = 0 in U(1); Delta n = 0 and unchanged spins in
 // SU(2)) have diagonal entries, diag[(l, r)] = sum_t (scaled A_t)[l, l] B_t[r, r].
+#include <cstdint>
 #include <vector>
 
 #include "../../include/dmrg_heff.h"
@@ -9,13 +10,16 @@
 namespace dmrg {
 namespace {
 
-// One CTA per diagonal job; jobs of one block are accumulated in job order by the
-// same CTA (jobs are grouped per block and a block is owned by one CTA).
+// One CTA per block; the block's jobs are accumulated in job order by that CTA.  ops
+// holds the layout entries from ops_lo on; only blocks whose first job's A stack lies
+// in [lo, hi) are formed (a block's stacks lie in one window of the layout).
 __global__ void k_diag(const DiagJob* __restrict__ jobs, const int32_t* __restrict__ first,
-                       const double* __restrict__ ops, double* __restrict__ diag) {
+                       const double* __restrict__ ops, int64_t ops_lo, int64_t lo, int64_t hi,
+                       double* __restrict__ diag) {
     const int32_t j0 = first[blockIdx.x], j1 = first[blockIdx.x + 1];
     if (j0 == j1) return;
     const DiagJob J0 = jobs[j0];
+    if (J0.a_stack < lo || J0.a_stack >= hi) return;
     for (int64_t e = threadIdx.x; e < int64_t(J0.rows) * J0.cols; e += blockDim.x) {
         const int i = int(e / J0.cols), j = int(e % J0.cols);
         double s = 0.0;
@@ -23,8 +27,8 @@ __global__ void k_diag(const DiagJob* __restrict__ jobs, const int32_t* __restri
             const DiagJob J = jobs[q];
             double g = 0.0;
             for (int t = 0; t < J.n; ++t)
-                g += ops[J.a_stack + int64_t(t) * J.rows * J.rows + int64_t(i) * J.rows + i] *
-                     ops[J.b_stack + int64_t(t) * J.cols * J.cols + int64_t(j) * J.cols + j];
+                g += ops[J.a_stack - ops_lo + int64_t(t) * J.rows * J.rows + int64_t(i) * J.rows + i] *
+                     ops[J.b_stack - ops_lo + int64_t(t) * J.cols * J.cols + int64_t(j) * J.cols + j];
             s += J.sign * g;
         }
         diag[J0.off + e] = s;
@@ -32,6 +36,15 @@ __global__ void k_diag(const DiagJob* __restrict__ jobs, const int32_t* __restri
 }
 
 }  // namespace
+
+cudaError_t Handle::launch_diag(const double* ops, int64_t ops_lo, int64_t lo, int64_t hi, double* diag,
+                                cudaStream_t st) {
+    if (plan.blocks.empty()) return cudaSuccess;
+    const int32_t* first = reinterpret_cast<const int32_t*>(
+        reinterpret_cast<const char*>(d_diag_jobs) + sizeof(DiagJob) * n_diag_jobs);
+    k_diag<<<int(plan.blocks.size()), 256, 0, st>>>(d_diag_jobs, first, ops, ops_lo, lo, hi, diag);
+    return cudaGetLastError();
+}
 
 int Handle::init_diag() {
     std::vector<DiagJob> jobs;
@@ -65,13 +78,14 @@ int Handle::diagonal(double* diag, cudaStream_t st) {
     if (plan_only) return fail(DMRG_ERR_INVALID_ARG, "plan-only handle");
     if (plan.dim == 0) return DMRG_OK;
     if (!diag) return fail(DMRG_ERR_INVALID_ARG, "null diag");
-    cudaError_t e = cudaMemsetAsync(diag, 0, sizeof(double) * plan.dim, st);
+    cudaError_t e;
+    if (d_diag) {   // split handles: formed while the operators were streamed in
+        e = cudaMemcpyAsync(diag, d_diag, sizeof(double) * plan.dim, cudaMemcpyDeviceToDevice, st);
+        return e == cudaSuccess ? DMRG_OK : cuda_fail(e, "copy diag");
+    }
+    e = cudaMemsetAsync(diag, 0, sizeof(double) * plan.dim, st);
     if (e != cudaSuccess) return cuda_fail(e, "zero diag");
-    if (plan.blocks.empty()) return DMRG_OK;
-    const int32_t* first = reinterpret_cast<const int32_t*>(
-        reinterpret_cast<const char*>(d_diag_jobs) + sizeof(DiagJob) * n_diag_jobs);
-    k_diag<<<int(plan.blocks.size()), 256, 0, st>>>(d_diag_jobs, first, d_ops, diag);
-    e = cudaGetLastError();
+    e = launch_diag(d_ops, 0, 0, INT64_MAX, diag, st);
     if (e != cudaSuccess) return cuda_fail(e, "diag kernel");
     return DMRG_OK;
 }

@@ -18,7 +18,9 @@
 // Every mbarrier wait is bounded; on timeout the CTA records DMRG_ERR_DEVICE_TIMEOUT in
 // the handle's status word, drains its own copies and MMAs and releases TMEM.
 #include <algorithm>
+#include <array>
 #include <climits>
+#include <map>
 #include <type_traits>
 #include <cstddef>
 #include <cstdint>
@@ -67,8 +69,13 @@ struct SplitDevPlan {
     SPart* parts = nullptr;
     int64_t n_work1 = 0, n_work2 = 0, n_blocks = 0, n_xjobs = 0, n_items = 0, n_tiles = 0;
     std::vector<std::pair<int32_t, int32_t>> r1, r2;   // per-GEMM work ranges (per_gemm)
+    int n_chunks = 1;                                  // output chunks and their work ranges
+    std::vector<int32_t> cw1, cw2, cr1, cr2;
     int64_t s2_len = 0, mid0 = 0, mid1 = 0;
-    double s1_bytes = 0, s2_bytes = 0, x_bytes = 0, e_bytes = 0;    // algorithmic DRAM bytes
+    double x_bytes = 0;                                // algorithmic DRAM bytes of the psi pass
+    // per output chunk: algorithmic DRAM bytes of stage 1, stage 2 and the estimate pass,
+    // and FP64-equivalent flops per vector of the two stages
+    std::vector<double> s1_bytes, s2_bytes, e_bytes, s1_flops, s2_flops;
     void release() {
         void* p[] = {gemms, work1, work2, segs, jobs, xjobs, slabs, items, tiles, blocks, parts};
         for (void* q : p)
@@ -178,7 +185,8 @@ struct SliceArgs {
     const SSlab* slabs;
     const SJob* jobs;
     const SSeg* segs;
-    const double* ops;
+    const double* ops;   // operator layout entries [ops_lo, ...) (a window of it)
+    int64_t ops_lo;
     int32_t* op_ex;
 };
 
@@ -195,7 +203,7 @@ __global__ void __launch_bounds__(256) k_slice_max(SliceArgs a) {
             const int64_t r = I.r0 + rr;
             const int t = int(r / J.nvalid), vec = int(r - int64_t(t) * J.nvalid);
             const int vg = vec / g.vper, vr = vec - vg * g.vper;
-            const int64_t base = g.off + t * g.ts + vg * g.vgs + int64_t(vr) * g.vs;
+            const int64_t base = g.off + t * g.ts + vg * g.vgs + int64_t(vr) * g.vs - a.ops_lo;
             int E = INT_MIN;
             for (int k = lane; k < g.kc; k += 32) E = max(E, exp_f64(a.ops[base + k * g.ks]));
 #pragma unroll
@@ -210,7 +218,8 @@ struct TileArgs {
     int64_t n_tiles;
     const SJob* jobs;
     const SSeg* segs;
-    const double* ops;
+    const double* ops;   // operator layout entries [ops_lo, ...)
+    int64_t ops_lo;
     uint16_t* op_sl;
     const int32_t* op_ex;
     int32_t* srow;
@@ -264,7 +273,7 @@ __global__ void __launch_bounds__(32 * DIG_WARPS) k_slice_digits(TileArgs a) {
                 const SSeg g = a.segs[sg];
                 const int t = (K - g.kbase) / g.kcp, k = (K - g.kbase) - t * g.kcp;
                 if (k < g.kc) {
-                    const int64_t base = g.off + t * g.ts + k * g.ks;
+                    const int64_t base = g.off + t * g.ts + k * g.ks - a.ops_lo;
                     int vg = (8 * T.vg) / g.vper, vr = 8 * T.vg - vg * g.vper;
                     double xv[8];
 #pragma unroll
@@ -1205,6 +1214,13 @@ int validate_split_plan(const Plan& P, const SplitHost& H, std::string* err) {
         if (X.off < 0 || X.ks < 0 || X.vs < 0 || last >= P.dim * H.nv) return bad("psi source");
     }
     if (H.ap_ex_mid0 < 0 || H.ap_ex_mid0 > H.ap_ex_mid1 || H.ap_ex_mid1 > H.ap_ex_vs) return bad("bound range");
+    // per-apply jobs by (first slice entry, output chunk); within a chunk no two share one
+    std::map<std::pair<int64_t, int32_t>, int32_t> mid_jobs;
+    for (int32_t j = 0; j < int32_t(H.jobs.size()); ++j) {
+        const SJob& J = H.jobs[size_t(j)];
+        if (J.out_buf && J.npad > 0 && !mid_jobs.emplace(std::make_pair(J.out_tiles, J.chunk), j).second)
+            return bad("two per-apply jobs share their slices");
+    }
     auto check_work = [&](const std::vector<SWork>& w) -> const char* {
         for (const SWork& x : w) {
             if (x.gemm < 0 || x.gemm >= int32_t(H.gemms.size())) return "work gemm index";
@@ -1221,6 +1237,10 @@ int validate_split_plan(const Plan& P, const SplitHost& H, std::string* err) {
             if (G.kind == 1) {
                 const int64_t dend = G.d_off + int64_t(G.M - 1) * G.ldd + G.N;
                 if (G.d_off < 0 || G.ldd < G.N || dend > H.s2_vs) return "stage-2 sums";
+                // its intermediate operand: a job of the GEMM's own output chunk
+                if (G.l_buf + G.r_buf != 1) return "stage-2 operands";
+                const int64_t mid = G.l_buf ? G.l_tiles : G.r_tiles;
+                if (mid < H.ap_sl_mid0 || !mid_jobs.count({mid, G.chunk})) return "stage-2 intermediate";
                 continue;
             }
             // stage-1 epilogue: row r = t*per + i, column v*cp + k -> vector v*per + i,
@@ -1229,13 +1249,14 @@ int validate_split_plan(const Plan& P, const SplitHost& H, std::string* err) {
                 return "stage-1 shape";
             const int64_t nt = G.M / G.per, nvv = G.N / G.cp;
             if (nvv != H.nv) return "stage-1 vectors";
+            if (G.r_buf != 1 || G.l_buf != 0 || G.r_tiles >= H.ap_sl_mid0) return "stage-1 operands";
             bool dst_ok = false;
-            for (const SJob& J : H.jobs)
-                if (J.out_buf && J.out_tiles == G.d_off && J.out_exp == G.dst_exp && J.rows_tile == G.dst_rows_tile &&
-                    J.kt == G.dst_kt) {
-                    dst_ok = int64_t(H.nv) * G.per <= J.nvalid && G.kbase + nt * G.cp <= J.K;
-                    break;
-                }
+            const auto it = mid_jobs.find({G.d_off, G.chunk});
+            if (it != mid_jobs.end()) {
+                const SJob& J = H.jobs[size_t(it->second)];
+                dst_ok = J.out_exp == G.dst_exp && J.rows_tile == G.dst_rows_tile && J.kt == G.dst_kt &&
+                         int64_t(H.nv) * G.per <= J.nvalid && G.kbase + nt * G.cp <= J.K;
+            }
             if (!dst_ok) return "stage-1 destination";
             if (G.er_off < 0 || G.er_off + G.M > H.op_ex || G.ec_off < 0 || G.ec_off + G.N > H.ap_ex_vs) return "stage-1 exponents";
             // the bounds the stage-1 epilogue reads and the estimate pass raises
@@ -1243,6 +1264,46 @@ int validate_split_plan(const Plan& P, const SplitHost& H, std::string* err) {
         }
         return nullptr;
     };
+    // output chunks: intermediates of one chunk are disjoint and above the psi slices
+    // (which no chunk reuses); every work range holds the items of its chunk only
+    if (H.n_chunks < 1 || H.ap_sl_mid0 < 0 || H.ap_sl_mid0 > H.ap_sl_vs) return bad("output chunks");
+    for (const SGemm& G : H.gemms)
+        if (G.chunk < 0 || G.chunk >= H.n_chunks) return bad("gemm chunk");
+    {
+        std::vector<std::array<int64_t, 3>> mids;
+        for (const SJob& J : H.jobs) {
+            if (!J.out_buf) continue;
+            const int64_t end = J.out_tiles + int64_t(J.npad / J.rows_tile) * J.kt * job_tile_elems(J.rows_tile);
+            if (J.out_tiles < H.ap_sl_mid0) {
+                if (end > H.ap_sl_mid0) return bad("psi slices reach the intermediates");
+                continue;
+            }
+            if (J.chunk < 0 || J.chunk >= H.n_chunks) return bad("job chunk");
+            mids.push_back({J.chunk, J.out_tiles, end});
+        }
+        std::sort(mids.begin(), mids.end());
+        for (size_t i = 1; i < mids.size(); ++i)
+            if (mids[i][0] == mids[i - 1][0] && mids[i][1] < mids[i - 1][2]) return bad("intermediates of a chunk overlap");
+    }
+    auto check_ranges = [&](const std::vector<SWork>& w, const std::vector<int32_t>& cw,
+                            const std::vector<std::pair<int32_t, int32_t>>& R, const std::vector<int32_t>& cr) {
+        if (cw.size() != size_t(H.n_chunks) + 1 || cr.size() != cw.size() || cw[0] != 0 || cr[0] != 0 ||
+            cw.back() != int32_t(w.size()) || cr.back() != int32_t(R.size()))
+            return false;
+        for (int c = 0; c < H.n_chunks; ++c) {
+            if (cw[size_t(c)] > cw[size_t(c) + 1] || cr[size_t(c)] > cr[size_t(c) + 1]) return false;
+            for (int32_t i = cw[size_t(c)]; i < cw[size_t(c) + 1]; ++i) {
+                const int32_t g = w[size_t(i)].gemm;
+                if (g < 0 || g >= int32_t(H.gemms.size()) || H.gemms[size_t(g)].chunk != c) return false;
+            }
+            for (int32_t r = cr[size_t(c)]; r < cr[size_t(c) + 1]; ++r)
+                if (R[size_t(r)].first < cw[size_t(c)] || R[size_t(r)].second > cw[size_t(c) + 1] ||
+                    R[size_t(r)].first >= R[size_t(r)].second)
+                    return false;
+        }
+        return true;
+    };
+    if (!check_ranges(H.w1, H.cw1, H.r1, H.cr1) || !check_ranges(H.w2, H.cw2, H.r2, H.cr2)) return bad("chunk work ranges");
     if (const char* why = check_work(H.w1)) return bad(why);
     if (const char* why = check_work(H.w2)) return bad(why);
     for (const STile& T : H.tiles) {   // the digit pass starts its segment search at T.seg
@@ -1305,31 +1366,47 @@ void build_split_work(SplitHost& H, const Schedule& S) {
                 for (int nt = 0; nt < cdiv(m.N, SPL_TN); ++nt)
                     w2.push_back({int32_t(gi), mt, nt, k0, std::min(m.kt, k0 + chunk), 0});
     }
-    // longest items first; one launch per GEMM keeps each GEMM's items contiguous
-    auto by_cost = [](const SWork& x, const SWork& y) { return (x.k1 - x.k0) > (y.k1 - y.k0); };
-    auto by_gemm = [](const SWork& x, const SWork& y) {
+    // output chunk first; then longest items first, or (one launch per GEMM) each GEMM's
+    // items contiguous
+    auto ck = [&](const SWork& x) { return H.gemms[size_t(x.gemm)].chunk; };
+    auto by_cost = [&](const SWork& x, const SWork& y) {
+        return ck(x) != ck(y) ? ck(x) < ck(y) : (x.k1 - x.k0) > (y.k1 - y.k0);
+    };
+    auto by_gemm = [&](const SWork& x, const SWork& y) {
+        if (ck(x) != ck(y)) return ck(x) < ck(y);
         return x.gemm != y.gemm ? x.gemm < y.gemm : (x.k1 - x.k0) > (y.k1 - y.k0);
     };
     for (int st = 0; st < 2; ++st) {
         std::vector<SWork>& w = st == 0 ? w1 : w2;
-        if (!S.per_gemm) {
-            std::stable_sort(w.begin(), w.end(), by_cost);
-            continue;
-        }
-        std::stable_sort(w.begin(), w.end(), by_gemm);
+        std::vector<int32_t>& cw = st == 0 ? H.cw1 : H.cw2;
+        std::vector<int32_t>& cr = st == 0 ? H.cr1 : H.cr2;
         auto& R = st == 0 ? H.r1 : H.r2;
-        for (int32_t i = 0; i < int32_t(w.size());) {
-            int32_t j = i;
-            while (j < int32_t(w.size()) && w[j].gemm == w[i].gemm) ++j;
-            R.push_back({i, j});
-            i = j;
+        std::stable_sort(w.begin(), w.end(), [&](const SWork& x, const SWork& y) {
+            return S.per_gemm ? by_gemm(x, y) : by_cost(x, y);
+        });
+        if (S.per_gemm)
+            for (int32_t i = 0; i < int32_t(w.size());) {
+                int32_t j = i;
+                while (j < int32_t(w.size()) && w[j].gemm == w[i].gemm) ++j;
+                R.push_back({i, j});
+                i = j;
+            }
+        cw.assign(size_t(H.n_chunks) + 1, 0);
+        cr.assign(size_t(H.n_chunks) + 1, 0);
+        size_t i = 0, r = 0;
+        for (int c = 0; c < H.n_chunks; ++c) {
+            while (i < w.size() && ck(w[i]) == c) ++i;
+            while (r < R.size() && ck(w[size_t(R[r].first)]) == c) ++r;
+            cw[size_t(c) + 1] = int32_t(i);
+            cr[size_t(c) + 1] = int32_t(r);
         }
     }
 }
 
-int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err, const Schedule& S) {
+int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err, const Schedule& S, int64_t mid_cap) {
     H = SplitHost{};
     H.nv = nv;
+    if (mid_cap <= 0) mid_cap = SPL_MID_CAP;
     if (nv < 1 || nv > 64) {
         *err = "nvec out of range";
         return DMRG_ERR_INVALID_ARG;
@@ -1407,6 +1484,7 @@ int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err, cons
     // (reset per apply) form one range after them
     for (const Group& G : P.groups) xjob(G.in_block, G.order);
     H.ap_ex_mid0 = ap_ex;
+    H.ap_sl_mid0 = ap_sl;
     // stage 2 next (the stage-1 epilogues need their destination jobs): per output block
     // one GEMM over its A-first groups and one over its B-first groups
     std::vector<int32_t> dst_of(P.groups.size(), -1);
@@ -1415,9 +1493,31 @@ int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err, cons
     for (int32_t g = 0; g < int32_t(P.groups.size()); ++g) by_out[size_t(P.groups[size_t(g)].out_block)].push_back(g);
     std::vector<SGemm> s2g;
     H.blocks.assign(P.blocks.size(), SBlock{});
+    // output chunks: the intermediates of the blocks of one chunk take the apply space
+    // from ap_sl_mid0 on; a block that would take a chunk beyond mid_cap bytes opens the
+    // next chunk (whose intermediates reuse the space)
+    std::vector<int32_t> chunk_of(P.blocks.size(), 0);
+    int32_t chunk = 0;
+    int64_t mid_end = ap_sl;
     for (size_t o = 0; o < P.blocks.size(); ++o) {
         const PsiBlock& O = P.blocks[o];
         H.blocks[o] = {O.off, O.rows, O.cols, int32_t(H.parts.size()), 0};
+        int64_t need = 0;   // this block's intermediate slice entries
+        for (int order = 0; order < 2; ++order) {
+            int64_t K = 0;
+            for (int32_t g : by_out[o]) {
+                const Group& G = P.groups[size_t(g)];
+                if (G.order == order) K += int64_t(kpad(order == 0 ? G.c : G.b)) * int64_t(G.terms.size());
+            }
+            if (K == 0) continue;
+            const int rt = order == 0 ? SPL_TM : SPL_TN;
+            need += cdiv(int64_t(nv) * (order == 0 ? O.rows : O.cols), rt) * cdiv(K, SPL_TK) * job_tile_elems(rt);
+        }
+        if (ap_sl > H.ap_sl_mid0 && 2 * (ap_sl - H.ap_sl_mid0 + need) > mid_cap) {
+            ++chunk;
+            ap_sl = H.ap_sl_mid0;
+        }
+        chunk_of[o] = chunk;
         for (int order = 0; order < 2; ++order) {
             std::vector<SSeg> opseg;
             std::vector<int32_t> gs;
@@ -1444,12 +1544,13 @@ int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err, cons
             // the intermediate side: vectors v*rows + i (A-first, L) or v*cols + j (B-first, R)
             const int32_t ij = order == 0 ? add_job(1, SPL_TM, int64_t(nv) * O.rows, K, {})
                                           : add_job(1, SPL_TN, int64_t(nv) * O.cols, K, {});
+            jobs[size_t(ij)].chunk = chunk;
             const int32_t oj = order == 0 ? add_job(0, SPL_TN, O.cols, K, opseg) : add_job(0, SPL_TM, O.rows, K, opseg);
             for (int32_t g : gs) dst_of[size_t(g)] = ij;
             const SJob IJ = jobs[size_t(ij)];
             const SJob OJ = jobs[size_t(oj)];
             SGemm m{};
-            m.kind = 1; m.sign = 1;
+            m.kind = 1; m.sign = 1; m.chunk = chunk;
             m.M = order == 0 ? nv * O.rows : O.rows;
             m.N = order == 0 ? O.cols : nv * O.cols;
             m.kt = int32_t(cdiv(K, SPL_TK));
@@ -1472,7 +1573,11 @@ int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err, cons
             s2 += int64_t(m.M) * m.N;
             s2g.push_back(m);
         }
+        mid_end = std::max(mid_end, ap_sl);
     }
+    ap_sl = mid_end;
+    H.n_chunks = chunk + 1;
+    H.block_chunk = chunk_of;
     H.ap_ex_mid1 = ap_ex;
     // stage 1: one GEMM per group; L = stacked operator rows (c_t A_t or B_t), R = psi
     for (size_t g = 0; g < P.groups.size(); ++g) {
@@ -1496,6 +1601,7 @@ int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err, cons
         const SJob DJ = jobs[size_t(dst_of[g])];
         SGemm m{};
         m.kind = 0;
+        m.chunk = chunk_of[size_t(G.out_block)];
         m.M = n * per; m.N = nv * X.cp; m.kt = LJ.kt;
         m.l_buf = 0; m.r_buf = 1; m.l_tiles = LJ.out_tiles; m.r_tiles = XJ.out_tiles;
         m.sign = G.sign < 0 ? -1 : 1;
@@ -1539,20 +1645,18 @@ int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err, cons
     return validate_split_plan(P, H, err);
 }
 
-int Handle::init_split() {
+int Handle::init_split(const double* op_data) {
     const Plan& P = plan;
     SplitState* S = new SplitState();
     split = S;
     std::string err;
     // one plan per number of stacked vectors; operator slices are identical in all of them
-    std::vector<SplitHost> hosts(static_cast<size_t>(max_nvec));
+    std::vector<SplitHost> hosts;
+    std::vector<SWindow> win;
+    int rc0 = build_split_hosts(P, max_nvec, split_mid_cap, hosts, win, &mem, &err);
+    if (rc0 != DMRG_OK) return fail(rc0, err);
     int64_t ap_sl = 0, ap_ex = 0, s2 = 0;
-    for (int nv = 1; nv <= max_nvec; ++nv) {
-        SplitHost& H = hosts[size_t(nv - 1)];
-        const int rc0 = build_split_plan(P, nv, H, &err);
-        if (rc0 != DMRG_OK) return fail(rc0, err);
-        if (H.op_sl != hosts[0].op_sl || H.op_ex != hosts[0].op_ex)
-            return fail(DMRG_ERR_BOUNDS, "operator slice layout differs between plans");
+    for (const SplitHost& H : hosts) {
         ap_sl = std::max(ap_sl, H.ap_sl_vs);
         ap_ex = std::max(ap_ex, H.ap_ex_vs);
         s2 = std::max(s2, H.s2_vs);
@@ -1600,6 +1704,8 @@ int Handle::init_split() {
         D.n_work2 = int64_t(H.w2.size());
         D.r1 = H.r1;
         D.r2 = H.r2;
+        D.n_chunks = H.n_chunks;
+        D.cw1 = H.cw1; D.cw2 = H.cw2; D.cr1 = H.cr1; D.cr2 = H.cr2;
         D.n_blocks = int64_t(H.blocks.size());
         D.n_xjobs = int64_t(H.xjobs.size());
         D.n_items = int64_t(H.items.size());
@@ -1610,14 +1716,24 @@ int Handle::init_split() {
         // algorithmic DRAM bytes: slice tiles read once (12 B per entry), stage-1 digit
         // slices written (12 B per entry), stage-2 int64 sums added (8 B per entry); the
         // psi pass reads psi and writes its slices
+        const size_t nc = size_t(H.n_chunks);
+        D.s1_bytes.assign(nc, 0.0); D.s2_bytes.assign(nc, 0.0); D.e_bytes.assign(nc, 0.0);
+        D.s1_flops.assign(nc, 0.0); D.s2_flops.assign(nc, 0.0);
         for (const SGemm& m : H.gemms) {
             const double rd = 12.0 * (double(m.M) + m.N) * m.kt * SPL_TK;
+            const size_t c = size_t(m.chunk);
             if (m.kind == 0) {
-                D.s1_bytes += rd + 12.0 * double(m.M) * m.N;
-                D.e_bytes += rd / SPL_S;   // the estimate pass reads slice 0 only
+                D.s1_bytes[c] += rd + 12.0 * double(m.M) * m.N;
+                D.e_bytes[c] += rd / SPL_S;   // the estimate pass reads slice 0 only
             } else {
-                D.s2_bytes += rd + 8.0 * double(m.M) * m.N;
+                D.s2_bytes[c] += rd + 8.0 * double(m.M) * m.N;
             }
+        }
+        for (const Group& G : P.groups) {   // the planned order's flops, as for the handle totals
+            const size_t c = size_t(H.block_chunk[size_t(G.out_block)]);
+            const double n = double(G.terms.size()), a = G.a, b = G.b, cc = G.c, d = G.d;
+            D.s1_flops[c] += G.order == 0 ? n * 2 * a * b * cc : n * 2 * b * cc * d;
+            D.s2_flops[c] += G.order == 0 ? n * 2 * a * cc * d : n * 2 * a * b * d;
         }
         for (const SXJob& X : H.xjobs) D.x_bytes += double(nv) * (8.0 * X.K * X.nk + 12.0 * X.K * X.cp);
     }
@@ -1643,47 +1759,96 @@ int Handle::init_split() {
     if ((e = cudaMemset(S->op_ex, 0xC0, sizeof(int32_t) * op_ex)) != cudaSuccess) return cuda_fail(e, "exponents");
     if ((e = cudaMemset(S->srow, 0, sizeof(int32_t) * op_ex)) != cudaSuccess) return cuda_fail(e, "top-digit sums");
     if (ap_ex > 0 && (e = cudaMemset(S->ap_ex, 0xE0, sizeof(int32_t) * ap_ex)) != cudaSuccess) return cuda_fail(e, "exponents");
-    // operator slices, once (from the first plan; every plan has the same operator jobs)
+    // operator slices and the diagonal, once (from the first plan; every plan has the same
+    // operator jobs): the FP64 layout is scaled on the host through a bounded buffer and
+    // staged on the device one window at a time
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&d_diag), sizeof(double) * std::max<int64_t>(P.dim, 1))) !=
+        cudaSuccess)
+        return cuda_fail(e, "diagonal");
+    if (P.dim > 0 && (e = cudaMemset(d_diag, 0, sizeof(double) * P.dim)) != cudaSuccess) return cuda_fail(e, "zero diagonal");
+    if (win.empty()) return DMRG_OK;
     const SplitDevPlan& D0 = S->plans[0];
-    if (D0.n_items > 0) {
-        SliceArgs sa{D0.items, D0.n_items, D0.slabs, D0.jobs, D0.segs, d_ops, S->op_ex};
-        TileArgs ta{D0.tiles, D0.n_tiles, D0.jobs, D0.segs, d_ops, S->op_sl, S->op_ex, S->srow};
-        k_slice_max<<<unsigned(std::min<int64_t>(D0.n_items, int64_t(n_sm) * 16)), 256>>>(sa);
-        if (D0.n_tiles > 0)
-            k_slice_digits<<<unsigned(std::min<int64_t>(cdiv(D0.n_tiles, DIG_WARPS), int64_t(n_sm) * 16)),
+    int64_t wmax = 0;
+    for (const SWindow& w : win) wmax = std::max(wmax, w.hi - w.lo);
+    double* d_stage = nullptr;
+    if ((rc = al((void**)&d_stage, sizeof(double) * wmax, "operator staging")) != DMRG_OK) return rc;
+    const size_t cap = size_t(std::min<int64_t>(wmax, int64_t(1) << 25));   // 256 MB host buffer
+    std::vector<double> hbuf(cap);
+    size_t wi = 0, fill = 0;
+    int64_t pos = 0, fill_lo = 0;   // layout position of the next entry, of hbuf[0]
+    cudaError_t ce = cudaSuccess;
+    auto flush = [&]() {
+        if (fill > 0 && ce == cudaSuccess)
+            ce = cudaMemcpy(d_stage + (fill_lo - win[wi].lo), hbuf.data(), sizeof(double) * fill,
+                            cudaMemcpyHostToDevice);
+        fill_lo += int64_t(fill);
+        fill = 0;
+    };
+    auto slice_window = [&]() {
+        const SWindow& w = win[wi];
+        if (ce != cudaSuccess) return;
+        if (w.item1 > w.item0) {
+            SliceArgs sa{D0.items + w.item0, w.item1 - w.item0, D0.slabs, D0.jobs, D0.segs, d_stage, w.lo, S->op_ex};
+            k_slice_max<<<unsigned(std::min<int64_t>(w.item1 - w.item0, int64_t(n_sm) * 16)), 256>>>(sa);
+        }
+        if (w.tile1 > w.tile0) {
+            TileArgs ta{D0.tiles + w.tile0, w.tile1 - w.tile0, D0.jobs, D0.segs, d_stage, w.lo,
+                        S->op_sl, S->op_ex, S->srow};
+            k_slice_digits<<<unsigned(std::min<int64_t>(cdiv(w.tile1 - w.tile0, DIG_WARPS), int64_t(n_sm) * 16)),
                              32 * DIG_WARPS>>>(ta);
-        e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaDeviceSynchronize();
-        if (e != cudaSuccess) return cuda_fail(e, "operator slicing");
-    }
+        }
+        ce = cudaGetLastError();
+        if (ce == cudaSuccess) ce = launch_diag(d_stage, w.lo, w.lo, w.hi, d_diag, nullptr);
+        if (ce == cudaSuccess) ce = cudaDeviceSynchronize();   // the staging buffer is reused
+    };
+    stream_ops(P, op_data, [&](const double* src, int64_t n, double scale) {
+        while (n > 0 && wi < win.size()) {
+            const int64_t k = std::min({n, int64_t(cap - fill), win[wi].hi - pos});
+            for (int64_t i = 0; i < k; ++i) hbuf[fill + size_t(i)] = scale * src[i];
+            fill += size_t(k);
+            pos += k;
+            src += k;
+            n -= k;
+            if (fill == cap) flush();
+            if (pos == win[wi].hi) {
+                flush();
+                slice_window();
+                ++wi;
+            }
+        }
+    });
+    cudaFree(d_stage);
+    if (ce != cudaSuccess) return cuda_fail(ce, "operator slicing");
+    if (wi != win.size() || pos != P.ops_len) return fail(DMRG_ERR_BOUNDS, "operator layout size");
     return DMRG_OK;
 }
 
 // One split H_eff*psi for nvec stacked vectors: psi pass (exponents, bounds, slices;
-// stage-2 sums cleared), stage-1 slice GEMM (its epilogue writes the stage-2 slices),
-// stage-2 slice GEMM (int64 sums), finalize.
+// stage-2 sums cleared); per output chunk the estimate pass, the stage-1 slice GEMM (its
+// epilogue writes the chunk's stage-2 slices) and the stage-2 slice GEMM (int64 sums);
+// finalize.
 int Handle::apply_split(const double* x, double* y, int32_t nvec, cudaStream_t st) {
     SplitState* S = split;
     const SplitDevPlan& D = S->plans[size_t(nvec - 1)];
     Profiler::Pending pe;
     cudaError_t e;
-    // one stage: a single persistent launch over its work list, or (per_gemm) one launch
-    // per GEMM over that GEMM's contiguous range
-    auto gemm = [&](const SWork* w, int64_t nw, const std::vector<std::pair<int32_t, int32_t>>& rg, int kid,
-                    double flops, double bytes) {
-        if (nw == 0) return cudaSuccess;
-        auto launch = [&](const SWork* w0, int64_t n) {
-            UmmaArgs ua{w0, n, D.gemms, S->op_sl, S->ap_sl, S->s2, S->op_ex, S->ap_ex, S->status};
+    // one stage of one chunk: a single persistent launch over the chunk's work items
+    // [w0, w1), or (per_gemm) one launch per GEMM over its ranges rg[r0, r1)
+    auto gemm = [&](const SWork* w, int32_t w0, int32_t w1, const std::vector<std::pair<int32_t, int32_t>>& rg,
+                    int32_t r0, int32_t r1, int kid, double flops, double bytes) {
+        if (w1 <= w0) return cudaSuccess;
+        auto launch = [&](const SWork* wp, int64_t n) {
+            UmmaArgs ua{wp, n, D.gemms, S->op_sl, S->ap_sl, S->s2, S->op_ex, S->ap_ex, S->status};
             k_umma<<<unsigned(std::min<int64_t>(n, n_sm)), UM_THREADS, sizeof(UmmaSmem), st>>>(ua);
             return cudaGetLastError();
         };
         prof.begin(kid, st, flops, bytes, &pe);
         cudaError_t le = cudaSuccess;
         if (!sched.per_gemm)
-            le = launch(w, nw);
+            le = launch(w + w0, w1 - w0);
         else
-            for (size_t r = 0; r < rg.size() && le == cudaSuccess; ++r)
-                le = launch(w + rg[r].first, rg[r].second - rg[r].first);
+            for (int32_t r = r0; r < r1 && le == cudaSuccess; ++r)
+                le = launch(w + rg[size_t(r)].first, rg[size_t(r)].second - rg[size_t(r)].first);
         prof.end(pe, st);
         return le;
     };
@@ -1694,17 +1859,23 @@ int Handle::apply_split(const double* x, double* y, int32_t nvec, cudaStream_t s
         prof.end(pe, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "psi slices");
     }
-    if (D.n_work1 > 0) {   // the stage-2 vector bounds, over the stage-1 work list
-        EstArgs ea{D.work1, D.n_work1, D.gemms, S->op_sl, S->ap_sl, S->op_ex, S->ap_ex, S->srow, S->xs, S->status};
-        prof.begin(S->kid_e, st, 0.0, D.e_bytes, &pe);
-        k_uest<<<unsigned(std::min<int64_t>(D.n_work1, n_sm)), UM_THREADS, sizeof(EstSmem), st>>>(ea);
-        prof.end(pe, st);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "estimate pass");
+    for (int c = 0; c < D.n_chunks; ++c) {
+        const int32_t a0 = D.cw1[size_t(c)], a1 = D.cw1[size_t(c) + 1];
+        if (a1 > a0) {   // the stage-2 vector bounds of the chunk, over its stage-1 work
+            EstArgs ea{D.work1 + a0, a1 - a0, D.gemms, S->op_sl, S->ap_sl, S->op_ex, S->ap_ex, S->srow, S->xs,
+                       S->status};
+            prof.begin(S->kid_e, st, 0.0, D.e_bytes[size_t(c)], &pe);
+            k_uest<<<unsigned(std::min<int64_t>(a1 - a0, n_sm)), UM_THREADS, sizeof(EstSmem), st>>>(ea);
+            prof.end(pe, st);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "estimate pass");
+        }
+        if ((e = gemm(D.work1, a0, a1, D.r1, D.cr1[size_t(c)], D.cr1[size_t(c) + 1], S->kid_s1,
+                      D.s1_flops[size_t(c)] * nvec, D.s1_bytes[size_t(c)])) != cudaSuccess)
+            return cuda_fail(e, "stage-1 slice gemm");
+        if ((e = gemm(D.work2, D.cw2[size_t(c)], D.cw2[size_t(c) + 1], D.r2, D.cr2[size_t(c)], D.cr2[size_t(c) + 1],
+                      S->kid_s2, D.s2_flops[size_t(c)] * nvec, D.s2_bytes[size_t(c)])) != cudaSuccess)
+            return cuda_fail(e, "stage-2 slice gemm");
     }
-    if ((e = gemm(D.work1, D.n_work1, D.r1, S->kid_s1, s1_flops * nvec, D.s1_bytes)) != cudaSuccess)
-        return cuda_fail(e, "stage-1 slice gemm");
-    if ((e = gemm(D.work2, D.n_work2, D.r2, S->kid_s2, s2_flops * nvec, D.s2_bytes)) != cudaSuccess)
-        return cuda_fail(e, "stage-2 slice gemm");
     if (D.n_blocks > 0) {
         prof.begin(S->kid_fin, st, 0.0, 0.0, &pe);
         k_finalize<<<dim3(unsigned(D.n_blocks), unsigned(nvec)), 256, 0, st>>>(D.blocks, D.parts, S->s2, S->op_ex,
@@ -1757,7 +1928,7 @@ int Handle::split_set_schedule(const Schedule& s) {
     if (!split) {
         for (int nv = 1; nv <= max_nvec; ++nv) {
             SplitHost H;
-            const int rc = build_split_plan(plan, nv, H, &err, s);
+            const int rc = build_split_plan(plan, nv, H, &err, s, split_mid_cap);
             if (rc != DMRG_OK) return fail(rc, err);
         }
         return DMRG_OK;
@@ -1788,6 +1959,7 @@ int Handle::split_set_schedule(const Schedule& s) {
         D.n_work2 = int64_t(H.w2.size());
         D.r1 = H.r1;
         D.r2 = H.r2;
+        D.cw1 = H.cw1; D.cw2 = H.cw2; D.cr1 = H.cr1; D.cr2 = H.cr2;
     }
     return DMRG_OK;
 }

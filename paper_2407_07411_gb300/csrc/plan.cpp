@@ -178,12 +178,20 @@ int finish_plan(Plan& P, std::vector<std::array<int64_t, 5>>& items, std::string
         P.flops += items[i][4];
     }
 
-    // Device operator layout and per-vector scratch.
+    // Device operator layout (output block by output block) and per-vector scratch.
+    P.layout.resize(P.groups.size());
+    for (size_t g = 0; g < P.groups.size(); ++g) P.layout[g] = int32_t(g);
+    std::stable_sort(P.layout.begin(), P.layout.end(),
+                     [&](int32_t x, int32_t y) { return P.groups[x].out_block < P.groups[y].out_block; });
     int64_t pos = 0, scr = 0;
-    for (Group& G : P.groups) {
+    for (int32_t g : P.layout) {
+        Group& G = P.groups[g];
         const int64_t n = int64_t(G.terms.size());
         G.a_stack = pos; pos += n * G.a * G.b;
         G.b_stack = pos; pos += n * G.d * G.c;
+    }
+    for (Group& G : P.groups) {
+        const int64_t n = int64_t(G.terms.size());
         G.scratch = scr;
         scr += G.order == 0 ? n * G.a * G.c : n * G.d * G.b;
         if (G.in_block == G.out_block) P.diag_terms += n;
@@ -328,7 +336,8 @@ int build_fp64_work(Plan& P, const Schedule& S, std::string* err) {
 
 void stream_ops(const Plan& P, const double* op_data,
                 const std::function<void(const double*, int64_t, double)>& sink) {
-    for (const Group& G : P.groups) {
+    for (int32_t g : P.layout) {
+        const Group& G = P.groups[size_t(g)];
         const int64_t na = int64_t(G.a) * G.b, nb = int64_t(G.d) * G.c;
         for (size_t i = 0; i < G.terms.size(); ++i) sink(op_data + G.a_src[i], na, G.a_scale[i]);
         for (size_t i = 0; i < G.terms.size(); ++i) sink(op_data + G.b_src[i], nb, 1.0);

@@ -76,8 +76,8 @@ struct Group {
     std::vector<int32_t> terms;
     std::vector<int64_t> a_src, b_src;  // per term: op_data offsets of its A and B blocks
     std::vector<double> a_scale;        // per term: factor of its stacked A copy
-    int64_t a_stack, b_stack;  // offsets of the stacked operator copies (device ops)
-    int64_t scratch;           // offset of X_g or Z_g^T in the per-vector scratch
+    int64_t a_stack = 0, b_stack = 0;   // offsets of the stacked operator copies (device ops)
+    int64_t scratch = 0;                // offset of X_g or Z_g^T in the per-vector scratch
 };
 
 struct Plan {
@@ -88,6 +88,7 @@ struct Plan {
     std::vector<int64_t> canon;         // 5 int64 per item, canonical order
     int64_t flops = 0;                  // algorithmic flops per vector
     std::vector<Group> groups;
+    std::vector<int32_t> layout;        // groups in operator-layout order (by output block)
     int64_t ops_len = 0;                // doubles in the device operator copy
     int64_t scratch_len = 0;            // doubles of stage-1 intermediates per vector
     // FP64 grouped-GEMM work lists
@@ -130,7 +131,10 @@ double su2_recoupling(int sl_out, int sr_out, int sl_in, int sr_in, int k2, int 
 constexpr int SU2_MAX_TWO_S = 40;   // spins up to 20 (factorials stay far inside the double range)
 
 // Sorts the items, fills the canonical dump and flop total, lays out the stacked
-// operator copies and scratch of P.groups and builds the FP64 work lists.
+// operator copies and scratch of P.groups and builds the FP64 work lists.  The stacks
+// are laid out output block by output block (groups of one output block in their
+// order), so that everything one output block's GEMMs and diagonal read is one
+// contiguous range of the layout.
 int finish_plan(Plan& P, std::vector<std::array<int64_t, 5>>& items, std::string* err);
 
 // (Re)builds the FP64 tile lists of P for schedule S; returns 0 or DMRG_ERR_INVALID_ARG.
@@ -138,8 +142,9 @@ int build_fp64_work(Plan& P, const Schedule& S, std::string* err);
 // Checks the ranges of a schedule (not its fit to a plan).
 int check_schedule(const Schedule& S, std::string* err);
 
-// Visits the device operator layout in memory order: per group its stacked scaled A
-// blocks, then its B blocks; sink(src, n, scale) receives n doubles to be scaled.
+// Visits the device operator layout in memory order: per group (in P.layout order) its
+// stacked scaled A blocks, then its B blocks; sink(src, n, scale) receives n doubles
+// to be scaled.
 void stream_ops(const Plan& P, const double* op_data,
                 const std::function<void(const double*, int64_t, double)>& sink);
 

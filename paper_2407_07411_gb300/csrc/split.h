@@ -51,6 +51,7 @@
 #include <string>
 #include <vector>
 
+#include "../../include/dmrg_heff.h"
 #include "plan.h"
 
 namespace dmrg {
@@ -72,6 +73,7 @@ constexpr int32_t SPL_EXP_NONE = -0x1F1F1F20;     // "no exponent" (an all-zero 
                                                   // sum of two stays far above INT_MIN
 constexpr int SPL_ROWS_PER_ITEM = 64;
 constexpr int SPL_TILE_K = 256;           // K of one work item of the operator digit pass
+constexpr int64_t SPL_MID_CAP = int64_t(64) << 30;   // default intermediate bytes per output chunk
 
 inline int32_t kpad(int32_t k) { return (k + SPL_KPAD - 1) / SPL_KPAD * SPL_KPAD; }
 
@@ -95,6 +97,7 @@ struct SGemm {
     int32_t per, cp, kbase;
     int32_t dst_rows_tile, dst_kt, dst_exp;
     int32_t er_off, ec_off;     // operator row exponents (op_ex), psi vector exponents (ap_ex)
+    int32_t chunk;              // output chunk (host-side: the launch it belongs to)
 };
 
 struct SWork { int32_t gemm, mtile, ntile, k0, k1, pad; };
@@ -122,7 +125,8 @@ struct SJob {
     int32_t out_buf, rows_tile;
     int32_t nvalid, npad, K, kt;
     int32_t seg0, nseg;
-    int32_t top_sums, pad;
+    int32_t top_sums;
+    int32_t chunk;       // stage-2 intermediate jobs: their output chunk (host-side)
 };
 
 // psi operand of the stage-1 GEMMs of one (psi block, contraction side): vector
@@ -169,12 +173,40 @@ struct SplitHost {
     int64_t op_sl = 0, op_ex = 0;                       // operator buffers (the same in every plan)
     int64_t ap_sl_vs = 0, ap_ex_vs = 0, s2_vs = 0;      // per-apply buffers of this plan
     int64_t ap_ex_mid0 = 0, ap_ex_mid1 = 0;             // exponents of the stage-2 intermediate vectors
+    int64_t ap_sl_mid0 = 0;                             // first slice entry of the intermediates
     int nv = 1;   // Davidson vectors stacked in this plan
+    // Output chunks: runs of output blocks whose stage-2 intermediate slices share one
+    // apply space [ap_sl_mid0, ap_sl_vs); an apply runs estimate, stage 1 and stage 2 of
+    // one chunk before the next.  Chunk c owns w1[cw1[c], cw1[c+1]), w2[cw2[c],
+    // cw2[c+1]) and (per_gemm) the GEMM ranges r1[cr1[c], cr1[c+1]), r2[cr2[c], cr2[c+1]).
+    int n_chunks = 1;
+    std::vector<int32_t> cw1, cw2, cr1, cr2;
+    std::vector<int32_t> block_chunk;   // output chunk of each wave-function block
 };
 
+// A range [lo, hi) of the operator layout staged on the device at once while the
+// operators are sliced, and the slicer work (items [item0, item1), tiles [tile0,
+// tile1) of the first plan) that reads only inside it.
+struct SWindow { int64_t lo, hi, item0, item1, tile0, tile1; };
+
 int64_t cdiv(int64_t a, int64_t b);
+// Cuts the operator layout [0, P.ops_len) into windows of at most `target` entries
+// (longer where one run of overlapping read ranges is longer), never inside a range
+// that one operator job of H or one block's diagonal reads, and orders H.items and
+// H.tiles window by window.  Returns the longest window, or DMRG_ERR_BOUNDS (negative)
+// with *err.
+int64_t build_split_windows(const Plan& P, SplitHost& H, int64_t target, std::vector<SWindow>& W,
+                            std::string* err);
+constexpr int64_t SPL_STAGE_TARGET = int64_t(1) << 28;   // entries per operator window (2 GB)
+// The plans for 1 .. max_nvec stacked vectors (hosts[nv - 1]; their operator slices are
+// the same), the operator windows of the first, and the device bytes of the split state
+// (the staging buffer of one window as the set-up peak).
+int build_split_hosts(const Plan& P, int max_nvec, int64_t mid_cap, std::vector<SplitHost>& hosts,
+                      std::vector<SWindow>& W, dmrg_memory* mem, std::string* err);
 int32_t fshift_for(int64_t K);
-int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err, const Schedule& S = Schedule{});
+// mid_cap: bytes of stage-2 intermediate slices per output chunk (0: SPL_MID_CAP).
+int build_split_plan(const Plan& P, int nv, SplitHost& H, std::string* err, const Schedule& S = Schedule{},
+                     int64_t mid_cap = 0);
 // (Re)builds the work lists w1, w2 (and their per-GEMM ranges) of H from its GEMMs.
 void build_split_work(SplitHost& H, const Schedule& S);
 int validate_split_plan(const Plan& P, const SplitHost& H, std::string* err);

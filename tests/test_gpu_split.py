@@ -35,6 +35,35 @@ def test_mid_full_and_deterministic():
     assert np.array_equal(gpu_apply(h, x), y)
 
 
+@pytest.mark.parametrize("nvec", [1, 3])
+def test_output_chunks_bit_identical(nvec):
+    # the output blocks in chunks that reuse one intermediate buffer (a 1-byte cap puts
+    # every block in a chunk of its own; 2 MB groups a few): the same bits as one chunk,
+    # under the default schedule and one launch per GEMM; the streamed diagonal equals
+    # the FP64 handle's bit for bit
+    import torch
+    p = S.generate("mid")
+    X = p.random_vectors(nvec)
+    one = split_handle(p, nvec)
+    ref = gpu_apply(one, X)
+    assert rel_fro(ref[0], heff.apply(p, X[0])) <= TOL_SPLIT
+    d_split = torch.empty(p.dim, dtype=torch.float64, device="cuda")
+    one.diagonal(d_split)
+    one.close()
+    h64 = lib.HEff.from_problem(p, precision="fp64")
+    d_fp64 = torch.empty_like(d_split)
+    h64.diagonal(d_fp64)
+    torch.cuda.synchronize()
+    h64.close()
+    assert torch.equal(d_split, d_fp64)
+    for cap in (1, 2 << 20):
+        h = lib.HEff.from_problem(p, precision="split", max_nvec=nvec, split_mid_bytes=cap)
+        assert np.array_equal(gpu_apply(h, X), ref)
+        h.schedule = dict(h.schedule, per_gemm=1)
+        assert np.array_equal(gpu_apply(h, X), ref)
+        h.close()
+
+
 @pytest.mark.parametrize("name,n_terms,nvec", [("mid", 300, 8), ("heavy", 120, 8), ("tiny", None, 5)])
 def test_stacked_vectors(name, n_terms, nvec):
     # nvec vectors stacked inside every slice GEMM; every call size up to max_nvec
