@@ -506,56 +506,75 @@ struct UmmaArgs {
 // Issue order of the 21 slice pairs (i, j) of a 16-K tile: accumulator c (pair level c
 // for c < 4, levels 4 and 5 for c = 4) alternates with the others, so that consecutive
 // MMAs never feed the same accumulator (a run into one accumulator stalls on its own
-// sum), and the first use of each accumulator follows the order 4, 3, 2, 1, 0 in which
-// the epilogue empties them.
+// sum).  The first tile of a chunk ("open" tile) uses a second order in which the first
+// uses of the accumulators come as late as the alternation allows, in the order 4, 3,
+// 2, 1, 0 in which the epilogue empties them (accumulator 0 at the 20th MMA), so the
+// issuer waits as little as possible for the drains; both orders take the pairs of
+// accumulator 4 in the same sequence (its inexact FP32 sums do not depend on which
+// order a tile uses).
 #define UM_ORDER_C {4, 3, 4, 2, 4, 3, 4, 1, 4, 2, 4, 3, 4, 0, 4, 1, 4, 2, 4, 3, 4}
 #define UM_ORDER_I {0, 0, 1, 0, 2, 1, 3, 0, 4, 1, 0, 2, 1, 0, 2, 1, 3, 2, 4, 3, 5}
 #define UM_ORDER_J {4, 3, 3, 2, 2, 2, 1, 1, 0, 1, 5, 1, 4, 0, 3, 0, 2, 0, 1, 0, 0}
+#define UM_OPEN_C {4, 3, 4, 3, 4, 3, 4, 3, 4, 2, 4, 2, 4, 2, 4, 1, 4, 1, 4, 0, 4}
+#define UM_OPEN_I {0, 0, 1, 1, 2, 2, 3, 3, 4, 0, 0, 1, 1, 2, 2, 0, 3, 1, 4, 0, 5}
+#define UM_OPEN_J {4, 3, 3, 2, 2, 1, 1, 0, 0, 2, 5, 1, 4, 0, 3, 1, 2, 0, 1, 0, 0}
 
-// Drain schedule: every accumulator is emptied after item-relative K tile kt when the
-// tile closes a chunk of 16 tiles (256 K, the limit of the exact levels) or the work
-// item.  Stage-2 items start at multiples of 16 tiles, so the rounding points of the
-// inexact accumulator 4 (and hence the result) do not depend on how a stage-2 GEMM is cut
-// into items.  (Staggering the five accumulators' chunk ends was measured slower: the
-// MMAs of the accumulator whose chunk starts had to run back to back, and consecutive
-// MMAs into one accumulator stall on its sum.)
+// Drain schedule: after item-relative K tile kt, when the tile closes a chunk d = kt / 16
+// of 16 tiles (256 K) or the work item, the accumulators of mask um_drain_mask are
+// emptied.  Accumulators 2, 3 (exact up to 341 and 256 K) and 4 are emptied after every
+// chunk; accumulator 1 (exact up to 512 K: |sum| <= 2 * 512 * 2^14 = 2^24 units) after
+// every second, accumulator 0 (up to 1024 K) after every fourth, and all of them at the
+// item's end.  Exact sums do not depend on where they are cut, and accumulator 4's
+// rounding points are the chunk ends; stage-2 items start at multiples of 16 tiles, so
+// the result does not depend on how a stage-2 GEMM is cut into items.  (Staggering the
+// chunk ends of the five accumulators was measured slower: the MMAs of the accumulator
+// whose chunk starts had to run back to back.)
 __host__ __device__ __forceinline__ bool um_drains(int kt, int len) {
     return kt == len - 1 || kt % SPL_DRAIN_KT == SPL_DRAIN_KT - 1;
 }
+__host__ __device__ __forceinline__ int um_drain_mask(int kt, int len) {
+    if (kt == len - 1) return 0x1F;
+    const int d = kt / SPL_DRAIN_KT;
+    return 0x1C | ((d & 1) ? 0x2 : 0) | ((d & 3) == 3 ? 0x1 : 0);
+}
 
-// The 21 MMAs of one 16-K tile, fully unrolled.  OPEN < 0: every accumulator keeps
-// accumulating.  OPEN = 5: the tile starts a chunk, and each accumulator waits for its
-// own drain (tempty) before its first pair, which overwrites it; the issue order makes
-// these waits follow the order 4, 3, 2, 1, 0 of the epilogue.  nd[c] counts the drains of
-// accumulator c so far in this CTA.
-template <int OPEN>
+// The 21 MMAs of one 16-K tile, fully unrolled.  OPEN = false: every accumulator keeps
+// accumulating.  OPEN = true: the tile starts a chunk; each accumulator of open_mask
+// (the ones emptied at the end of the previous chunk, or all at an item's start) waits
+// for its own drain (tempty) before its first pair, which overwrites it; the others keep
+// accumulating.  nd[c] counts the drains of accumulator c so far in this CTA.
+template <bool OPEN>
 __device__ __forceinline__ bool issue_tile(UmmaSmem& sm, uint32_t tmem, uint32_t a0, uint32_t b0, uint32_t idesc,
-                                           const int (&nd)[SPL_ACCS], int* status) {
-    constexpr int oc[SPL_PAIRS] = UM_ORDER_C, oi[SPL_PAIRS] = UM_ORDER_I, oj[SPL_PAIRS] = UM_ORDER_J;
+                                           const int (&nd)[SPL_ACCS], int open_mask, int* status) {
+    constexpr int sc[SPL_PAIRS] = UM_ORDER_C, si[SPL_PAIRS] = UM_ORDER_I, sj[SPL_PAIRS] = UM_ORDER_J;
+    constexpr int pc[SPL_PAIRS] = UM_OPEN_C, pi[SPL_PAIRS] = UM_OPEN_I, pj[SPL_PAIRS] = UM_OPEN_J;
 #pragma unroll
     for (int p = 0; p < SPL_PAIRS; ++p) {
-        const int c = oc[p];
-        bool first = OPEN == SPL_ACCS;
+        const int c = OPEN ? pc[p] : sc[p];
+        const int i = OPEN ? pi[p] : si[p], j = OPEN ? pj[p] : sj[p];
+        bool first = OPEN;
 #pragma unroll
         for (int p2 = 0; p2 < p; ++p2)
-            if (oc[p2] == c) first = false;
+            if ((OPEN ? pc[p2] : sc[p2]) == c) first = false;
+        first = first && ((open_mask >> c) & 1);
         if (first && nd[c] > 0) {
             if (!mbar_wait(sm, &sm.tempty[c], uint32_t((nd[c] - 1) & 1), status)) return false;
             tc_fence_after();
         }
-        umma(tmem + uint32_t(c * SPL_TN), a0 + uint32_t(oi[p] * (SPL_LT * 2)) / 16,
-             b0 + uint32_t(oj[p] * (SPL_RT * 2)) / 16, first ? 0u : 1u, idesc);
+        umma(tmem + uint32_t(c * SPL_TN), a0 + uint32_t(i * (SPL_LT * 2)) / 16, b0 + uint32_t(j * (SPL_RT * 2)) / 16,
+             first ? 0u : 1u, idesc);
     }
     return true;
 }
 
 // Drain of accumulator c into the int64 sums acc (units of 2^-31 of the digit-product
 // unit).  32-bit conversions only (the 64-bit one is an FP64-rate operation): acc c holds
-// the exact level sum in units of 2^(-8c) for c < 4 (|sum| <= (c+1) 2^22 in those units),
-// acc 4 the rest, rounded to units of 2^-31 (< 2^24 of them); each is added in units of
-// 2^-31, a chunk's total staying below 2^53.01 and a work item's (at most 8192 K) below
-// 2^58.01.  The accumulator is handed back to the MMA issuer as soon as it is in
-// registers.  n: the drains of accumulator c before this one.
+// the exact level sum in units of 2^(-8c) for c < 4 (|sum| <= 2^24 in those units, acc 0
+// over up to four chunks and acc 1 over two), acc 4 the rest, rounded to units of 2^-31
+// (< 2^24 of them); each is added in units of 2^-31, and the running sum of a work item
+// (at most 8192 K, a partial sum of its digit products) stays below 2^58.01.  The
+// accumulator is handed back to the MMA issuer as soon as it is in registers.  n: the
+// drains of accumulator c before this one.
 template <int c>
 __device__ __forceinline__ bool drain_acc(UmmaSmem& sm, uint32_t tmem_row, int col0, int n,
                                           long long (&acc)[UM_EPI_COLS], int* status) {
@@ -786,19 +805,23 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
                 if (!(ok = mbar_wait(sm, &sm.full[s], uint32_t((kidx / UM_STAGES) & 1), a.status))) break;
                 tc_fence_after();
                 const uint32_t a0 = sdesc_lo(su32(sm.L[s])), b0 = sdesc_lo(su32(sm.R[s]));
-                // a chunk's first tile: every accumulator starts over
+                // a chunk's first tile: the accumulators emptied at the end of the previous
+                // chunk (all at an item's start) start over
                 if (kt == 0 || um_drains(kt - 1, len))
-                    ok = issue_tile<SPL_ACCS>(sm, tmem, a0, b0, idesc, nd, a.status);
+                    ok = issue_tile<true>(sm, tmem, a0, b0, idesc, nd, kt == 0 ? 0x1F : um_drain_mask(kt - 1, len),
+                                          a.status);
                 else
-                    ok = issue_tile<-1>(sm, tmem, a0, b0, idesc, nd, a.status);
+                    ok = issue_tile<false>(sm, tmem, a0, b0, idesc, nd, 0, a.status);
                 if (!ok) break;
                 umma_commit(&sm.empty[s]);
                 if (um_drains(kt, len)) {
+                    const int m = um_drain_mask(kt, len);
 #pragma unroll
-                    for (int c = SPL_ACCS - 1; c >= 0; --c) {
-                        umma_commit(&sm.tfull[c]);
-                        ++nd[c];
-                    }
+                    for (int c = SPL_ACCS - 1; c >= 0; --c)
+                        if ((m >> c) & 1) {
+                            umma_commit(&sm.tfull[c]);
+                            ++nd[c];
+                        }
                 }
             }
         }
@@ -834,13 +857,14 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_umma(UmmaArgs a) {
             const int len = W.k1 - W.k0;
             for (int kt = 0; kt < len && ok; ++kt) {
                 if (!um_drains(kt, len)) continue;
+                const int m = um_drain_mask(kt, len);
                 ok = drain_acc<4>(sm, tmem_row, col0, nd[4], acc, a.status) &&
                      drain_acc<3>(sm, tmem_row, col0, nd[3], acc, a.status) &&
                      drain_acc<2>(sm, tmem_row, col0, nd[2], acc, a.status) &&
-                     drain_acc<1>(sm, tmem_row, col0, nd[1], acc, a.status) &&
-                     drain_acc<0>(sm, tmem_row, col0, nd[0], acc, a.status);
+                     (!(m & 2) || drain_acc<1>(sm, tmem_row, col0, nd[1], acc, a.status)) &&
+                     (!(m & 1) || drain_acc<0>(sm, tmem_row, col0, nd[0], acc, a.status));
 #pragma unroll
-                for (int c = 0; c < SPL_ACCS; ++c) ++nd[c];
+                for (int c = 0; c < SPL_ACCS; ++c) nd[c] += (m >> c) & 1;
             }
             if (!ok) break;
             const SGemm G = a.gemms[W.gemm];
