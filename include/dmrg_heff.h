@@ -322,12 +322,28 @@ int dmrg_heff_gemm_count(dmrg_heff_t h, int32_t nvec, int64_t counts[2]);
  *              offset of the row-major d_p x d_q block in op
  *   op       : device, op_len doubles;  out: device, out_len doubles >= sum d'_p d'_q
  *   out_off  : host, n_blocks offsets of the d'_p x d'_q results in out (block order)
- * Runs on `stream` and returns when the results are written (it allocates and frees
- * its scratch).  DMRG_ERR_INVALID_ARG for out-of-range sectors, dims or offsets,
- * checked on the host before any device work. */
+ * Runs on `stream` and returns when the results are written; it allocates and frees
+ * its scratch (dmrg_renorm_create / _run below keep it across calls).
+ * DMRG_ERR_INVALID_ARG for out-of-range sectors, dims or offsets, checked on the host
+ * before any device work. */
 int dmrg_renormalise(int32_t nsec, const int32_t* dims, const int32_t* dims_new, const double* U,
                      const int64_t* blocks, int64_t n_blocks, const double* op, int64_t op_len, double* out,
                      int64_t out_len, int64_t* out_off, void* stream);
+
+/* The same renormalisation split into set-up and run, for a block list that is
+ * renormalised repeatedly (every sweep step with the same sector structure):
+ * dmrg_renorm_create validates the arguments like dmrg_renormalise (same meaning; op_len
+ * and out_len are the sizes the runs will pass), fills out_off, builds the GEMM lists and
+ * allocates and uploads every device buffer the runs need, on the current device.
+ * dmrg_renorm_run copies the bases, then launches the two GEMM stages on `stream` and
+ * returns without synchronising; it allocates nothing.  A plan's scratch is shared by its
+ * runs: runs of one plan that overlap on the GPU (several streams) race.  U, op, out:
+ * device, as above.  dmrg_renorm_destroy frees the plan (after its runs have finished). */
+typedef struct dmrg_renorm* dmrg_renorm_t;
+int dmrg_renorm_create(int32_t nsec, const int32_t* dims, const int32_t* dims_new, const int64_t* blocks,
+                       int64_t n_blocks, int64_t op_len, int64_t out_len, int64_t* out_off, dmrg_renorm_t* plan);
+int dmrg_renorm_run(dmrg_renorm_t plan, const double* U, const double* op, double* out, void* stream);
+void dmrg_renorm_destroy(dmrg_renorm_t plan);
 
 /* Layout of the wave function: n_blocks rows (left sector, right sector, rows, cols,
  * offset) in storage order; with buf NULL only *n_blocks is set, otherwise buf holds

@@ -34,7 +34,7 @@ SYMBOLS = ("dmrg_heff_create", "dmrg_heff_dim", "dmrg_heff_flops", "dmrg_heff_pl
            "dmrg_selftest_wait_timeout", "dmrg_heff_schedule_get", "dmrg_heff_schedule_set",
            "dmrg_heff_autotune", "dmrg_heff_gemm_count", "dmrg_lanczos", "dmrg_renormalise",
            "dmrg_heff_psi_blocks", "dmrg_svd_truncate", "dmrg_heff_create_su2", "dmrg_su2_recoupling",
-           "dmrg_heff_memory")
+           "dmrg_heff_memory", "dmrg_renorm_create", "dmrg_renorm_run", "dmrg_renorm_destroy")
 
 
 class Opts(ctypes.Structure):
@@ -109,6 +109,9 @@ _lib.dmrg_heff_autotune.argtypes = [_P, _i32, _i32, ctypes.POINTER(TuneReport)]
 _lib.dmrg_heff_gemm_count.argtypes = [_P, _i32, _P]
 _lib.dmrg_lanczos.argtypes = [_P, _f64, _i32, _i32, _P, _P, ctypes.POINTER(DavidsonInfo)]
 _lib.dmrg_renormalise.argtypes = [_i32, _P, _P, _P, _P, _i64, _P, _i64, _P, _i64, _P, _P]
+_lib.dmrg_renorm_create.argtypes = [_i32, _P, _P, _P, _i64, _i64, _i64, _P, ctypes.POINTER(_P)]
+_lib.dmrg_renorm_run.argtypes = [_P, _P, _P, _P, _P]
+_lib.dmrg_renorm_destroy.argtypes = [_P]
 _lib.dmrg_heff_psi_blocks.argtypes = [_P, _P, ctypes.POINTER(_i64)]
 _lib.dmrg_svd_truncate.argtypes = [_P, _P, _i32, _P, _P, _P, _i64, _P, ctypes.POINTER(_f64)]
 _lib.dmrg_heff_destroy.argtypes = [_P]
@@ -428,6 +431,40 @@ def renormalise(dims, dims_new, U, blocks, op, out, stream=None) -> np.ndarray:
                                  len(blocks), _dev_ptr(op, 0, "op"), int(op.numel()), _dev_ptr(out, 0, "out"),
                                  int(out.numel()), _ptr(out_off), _stream_ptr(stream)))
     return out_off[:len(blocks)]
+
+
+class Renorm:
+    """A renormalisation plan (dmrg_renorm_create): the block list's GEMM lists and device
+    buffers, built once; run() launches on a stream without allocating or synchronising."""
+
+    def __init__(self, dims, dims_new, blocks, op_len: int, out_len: int):
+        self._p = None
+        self.dims = np.ascontiguousarray(dims, np.int32)
+        self.dims_new = np.ascontiguousarray(dims_new, np.int32)
+        b = np.ascontiguousarray(np.asarray(blocks, np.int64).reshape(-1, 3))
+        out_off = np.zeros(max(len(b), 1), np.int64)
+        p = ctypes.c_void_p()
+        _check(_lib.dmrg_renorm_create(len(self.dims), _ptr(self.dims), _ptr(self.dims_new), _ptr(b), len(b),
+                                       int(op_len), int(out_len), _ptr(out_off), ctypes.byref(p)))
+        self._p = p
+        self.out_off = out_off[:len(b)]
+        self.nu = int((self.dims.astype(np.int64) * self.dims_new).sum())
+
+    def run(self, U, op, out, stream=None):
+        _check(_lib.dmrg_renorm_run(self._p, _dev_ptr(U, self.nu, "U"), _dev_ptr(op, 0, "op"),
+                                    _dev_ptr(out, 0, "out"), _stream_ptr(stream)))
+        return out
+
+    def close(self):
+        if self._p:
+            _lib.dmrg_renorm_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def su2_recoupling(two_sl_out: int, two_sr_out: int, two_sl_in: int, two_sr_in: int, two_k: int,

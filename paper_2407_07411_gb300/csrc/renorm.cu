@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -56,13 +57,37 @@ struct Bufs {
 }  // namespace
 }  // namespace dmrg
 
-extern "C" int dmrg_renormalise(int32_t nsec, const int32_t* dims, const int32_t* dims_new, const double* U,
-                                const int64_t* blocks, int64_t n_blocks, const double* op, int64_t op_len,
-                                double* out, int64_t out_len, int64_t* out_off, void* stream) {
+namespace dmrg {
+
+// A renormalisation plan: the GEMM lists of one block list and the device buffers its
+// launches need, built once and run any number of times.
+struct RenormPlan {
+    Plan P;
+    int32_t nsec = 0;
+    int64_t nu = 0, op_len = 0, out_len = 0;
+    int n_sm = 152;
+    Bufs B;
+    double *uu = nullptr, *X = nullptr, *part = nullptr;
+    Tile *t1 = nullptr, *t2 = nullptr;
+    Gemm* gm = nullptr;
+    Seg* sg = nullptr;
+    Reduce* red = nullptr;
+    int32_t* counters = nullptr;
+    int64_t* d_uoff = nullptr;
+    int32_t *d_d = nullptr, *d_dn = nullptr;
+};
+
+}  // namespace dmrg
+
+extern "C" int dmrg_renorm_create(int32_t nsec, const int32_t* dims, const int32_t* dims_new, const int64_t* blocks,
+                                  int64_t n_blocks, int64_t op_len, int64_t out_len, int64_t* out_off,
+                                  dmrg_renorm_t* plan) {
     using namespace dmrg;
     // ---- validation (host only, before any device work)
+    if (!plan) return fail(DMRG_ERR_INVALID_ARG, "null plan");
+    *plan = nullptr;
     if (nsec < 1 || n_blocks < 0 || op_len < 0 || out_len < 0) return fail(DMRG_ERR_INVALID_ARG, "negative size");
-    if (!dims || !dims_new || (n_blocks > 0 && (!blocks || !out_off || !U || !op || !out)))
+    if (!dims || !dims_new || (n_blocks > 0 && (!blocks || !out_off)))
         return fail(DMRG_ERR_INVALID_ARG, "null argument");
     std::vector<int64_t> u_off(size_t(nsec) + 1, 0);
     for (int32_t q = 0; q < nsec; ++q) {
@@ -79,10 +104,15 @@ extern "C" int dmrg_renormalise(int32_t nsec, const int32_t* dims, const int32_t
         pos += int64_t(dims_new[p]) * dims_new[q];
     }
     if (pos > out_len) return fail(DMRG_ERR_INVALID_ARG, "out too small");
-    if (n_blocks == 0) return DMRG_OK;
 
     // ---- the two-stage GEMM lists
-    Plan P;
+    RenormPlan* R = new (std::nothrow) RenormPlan();
+    if (!R) return fail(DMRG_ERR_OOM, "host allocation");
+    R->nsec = nsec;
+    R->op_len = op_len;
+    R->out_len = out_len;
+    R->nu = u_off[size_t(nsec)];
+    Plan& P = R->P;
     int64_t scr = 0;
     for (int64_t b = 0; b < n_blocks; ++b) {
         const int32_t q = int32_t(blocks[3 * b]), p = int32_t(blocks[3 * b + 1]);
@@ -112,51 +142,83 @@ extern "C" int dmrg_renormalise(int32_t nsec, const int32_t* dims, const int32_t
     }
     std::string err;
     int rc = build_fp64_work(P, Schedule{}, &err);
-    if (rc != DMRG_OK) return fail(rc, err);
+    if (rc != DMRG_OK) {
+        delete R;
+        return fail(rc, err);
+    }
 
-    // ---- device buffers (freed after the launches complete)
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    Bufs B;
-    double *uu = nullptr, *X = nullptr, *part = nullptr;
-    Tile *t1 = nullptr, *t2 = nullptr;
-    Gemm* gm = nullptr;
-    Seg* sg = nullptr;
-    Reduce* red = nullptr;
-    int32_t* counters = nullptr;
-    int64_t* d_uoff = nullptr;
-    int32_t *d_d = nullptr, *d_dn = nullptr;
-    const int64_t nu = u_off[size_t(nsec)];
-    if ((rc = B.alloc(&uu, size_t(2 * nu), "bases")) || (rc = B.alloc(&X, size_t(scr), "renormalisation scratch")) ||
-        (rc = B.alloc(&part, size_t(P.n_slots) * FP64_BM * FP64_BN, "partials")) ||
-        (rc = B.upload(&t1, P.tiles1, "tiles")) || (rc = B.upload(&t2, P.tiles2, "tiles")) ||
-        (rc = B.upload(&gm, P.gemms, "gemms")) || (rc = B.upload(&sg, P.segs, "segments")) ||
-        (rc = B.upload(&red, P.reduces, "reduce jobs")) || (rc = B.alloc(&counters, 2, "counters")) ||
-        (rc = B.upload(&d_uoff, u_off, "basis offsets")) ||
-        (rc = B.upload(&d_d, std::vector<int32_t>(dims, dims + nsec), "dims")) ||
-        (rc = B.upload(&d_dn, std::vector<int32_t>(dims_new, dims_new + nsec), "dims")))
+    if (P.gemms.empty()) {   // no blocks: nothing on the device
+        *plan = reinterpret_cast<dmrg_renorm_t>(R);
+        return DMRG_OK;
+    }
+    // ---- device buffers and tables, once
+    Bufs& B = R->B;
+    if ((rc = B.alloc(&R->uu, size_t(2 * R->nu), "bases")) ||
+        (rc = B.alloc(&R->X, size_t(scr), "renormalisation scratch")) ||
+        (rc = B.alloc(&R->part, size_t(P.n_slots) * FP64_BM * FP64_BN, "partials")) ||
+        (rc = B.upload(&R->t1, P.tiles1, "tiles")) || (rc = B.upload(&R->t2, P.tiles2, "tiles")) ||
+        (rc = B.upload(&R->gm, P.gemms, "gemms")) || (rc = B.upload(&R->sg, P.segs, "segments")) ||
+        (rc = B.upload(&R->red, P.reduces, "reduce jobs")) || (rc = B.alloc(&R->counters, 2, "counters")) ||
+        (rc = B.upload(&R->d_uoff, u_off, "basis offsets")) ||
+        (rc = B.upload(&R->d_d, std::vector<int32_t>(dims, dims + nsec), "dims")) ||
+        (rc = B.upload(&R->d_dn, std::vector<int32_t>(dims_new, dims_new + nsec), "dims"))) {
+        delete R;
         return rc;
-    cudaError_t e = cudaMemcpyAsync(uu, U, sizeof(double) * size_t(nu), cudaMemcpyDeviceToDevice, st);
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&R->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete R;
+        return cuda_fail(e, "device attributes");
+    }
+    *plan = reinterpret_cast<dmrg_renorm_t>(R);
+    return DMRG_OK;
+}
+
+extern "C" int dmrg_renorm_run(dmrg_renorm_t plan, const double* U, const double* op, double* out, void* stream) {
+    using namespace dmrg;
+    if (!plan) return fail(DMRG_ERR_INVALID_ARG, "null plan");
+    RenormPlan* R = reinterpret_cast<RenormPlan*>(plan);
+    const Plan& P = R->P;
+    if (P.gemms.empty()) return DMRG_OK;
+    if (!U || !op || !out) return fail(DMRG_ERR_INVALID_ARG, "null argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(R->uu, U, sizeof(double) * size_t(R->nu), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) {
-        k_transpose_bases<<<unsigned(nsec), 256, 0, st>>>(uu, uu + nu, d_uoff, d_d, d_dn);
+        k_transpose_bases<<<unsigned(R->nsec), 256, 0, st>>>(R->uu, R->uu + R->nu, R->d_uoff, R->d_d, R->d_dn);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, sizeof(int32_t) * 2, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(R->counters, 0, sizeof(int32_t) * 2, st);
     Spaces sp{};
-    sp.ops = op; sp.x = uu; sp.scr = X; sp.y = out; sp.part = part;
-    int dev = 0, n_sm = 152;
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t cap = int64_t(n_sm) * fp64_tiles_per_sm();
+    sp.ops = op; sp.x = R->uu; sp.scr = R->X; sp.y = out; sp.part = R->part;
+    const int64_t cap = int64_t(R->n_sm) * fp64_tiles_per_sm();
     auto grid = [&](size_t n) { return int32_t(std::min<int64_t>(int64_t(n), cap)); };
     if (e == cudaSuccess && !P.tiles1.empty())
-        e = launch_fp64_tiles(t1, int32_t(P.tiles1.size()), gm, sg, sp, 1, counters, grid(P.tiles1.size()), st);
+        e = launch_fp64_tiles(R->t1, int32_t(P.tiles1.size()), R->gm, R->sg, sp, 1, R->counters, grid(P.tiles1.size()),
+                              st);
     if (e == cudaSuccess && !P.tiles2.empty())
-        e = launch_fp64_tiles(t2, int32_t(P.tiles2.size()), gm, sg, sp, 1, counters + 1, grid(P.tiles2.size()), st);
-    if (e == cudaSuccess && !P.reduces.empty())
-        e = launch_fp64_reduce(red, int32_t(P.reduces.size()), gm, sp, 1, st);
-    // the scratch buffers are released only after the launches have run
-    const cudaError_t es = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "renormalisation");
+        e = launch_fp64_tiles(R->t2, int32_t(P.tiles2.size()), R->gm, R->sg, sp, 1, R->counters + 1,
+                              grid(P.tiles2.size()), st);
+    if (e == cudaSuccess && !P.reduces.empty()) e = launch_fp64_reduce(R->red, int32_t(P.reduces.size()), R->gm, sp, 1, st);
+    return e == cudaSuccess ? DMRG_OK : cuda_fail(e, "renormalisation");
+}
+
+extern "C" void dmrg_renorm_destroy(dmrg_renorm_t plan) { delete reinterpret_cast<dmrg::RenormPlan*>(plan); }
+
+extern "C" int dmrg_renormalise(int32_t nsec, const int32_t* dims, const int32_t* dims_new, const double* U,
+                                const int64_t* blocks, int64_t n_blocks, const double* op, int64_t op_len,
+                                double* out, int64_t out_len, int64_t* out_off, void* stream) {
+    using namespace dmrg;
+    if (n_blocks > 0 && (!U || !op || !out)) return fail(DMRG_ERR_INVALID_ARG, "null argument");
+    dmrg_renorm_t plan = nullptr;
+    int rc = dmrg_renorm_create(nsec, dims, dims_new, blocks, n_blocks, op_len, out_len, out_off, &plan);
+    if (rc != DMRG_OK) return rc;
+    rc = dmrg_renorm_run(plan, U, op, out, stream);
+    // the plan's buffers are released only after its launches have run
+    const cudaError_t es = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    dmrg_renorm_destroy(plan);
+    if (rc != DMRG_OK) return rc;
     if (es != cudaSuccess) return cuda_fail(es, "renormalisation");
     return DMRG_OK;
 }

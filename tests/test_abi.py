@@ -106,3 +106,21 @@ def test_split_plan_bounds_proof(name, n_terms, nvec):
     p = S.generate(name, n_terms=n_terms)
     h = lib.HEff.from_problem(p, precision="split", plan_only=True, max_nvec=nvec)
     assert h.dim == p.dim and h.plan_dump().tobytes() == heff.plan(p).tobytes()
+
+
+def test_renorm_plan_argument_checks_on_the_host():
+    # every argument error of the renormalisation plan is reported before any device
+    # work (these run without a GPU); an empty block list needs no device at all
+    d, dn = np.array([3, 4], np.int32), np.array([2, 4], np.int32)
+    good = np.array([[0, 1, 0]], np.int64)
+    for dims, dims_new, blocks, op_len, out_len in [
+            (d, np.array([4, 4], np.int32), good, 100, 100),          # new dim above the dim
+            (d, dn, np.array([[2, 1, 0]], np.int64), 100, 100),       # sector out of range
+            (d, dn, np.array([[0, 1, 95]], np.int64), 100, 100),      # block outside op
+            (d, dn, good, 100, 7)]:                                   # out too small (needs 8)
+        with pytest.raises(lib.DmrgError) as e:
+            lib.Renorm(dims, dims_new, blocks, op_len, out_len)
+        assert e.value.code == -1
+    r = lib.Renorm(d, dn, np.zeros((0, 3), np.int64), 0, 0)
+    assert len(r.out_off) == 0
+    r.close()

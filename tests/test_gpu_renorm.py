@@ -45,3 +45,28 @@ def test_matches_oracle(name, frac):
     assert np.all(np.isfinite(got))
     g = np.concatenate([got[o:o + r.size] for o, r in zip(offs, ref)])
     assert rel_fro(g, np.concatenate([r.ravel() for r in ref])) <= 1e-12
+
+
+def test_plan_runs_match_one_shot_call():
+    # a plan built once and run twice on a non-default stream (new bases for the second
+    # run) gives the one-shot call's results bit for bit
+    import torch
+    p = S.generate("mid")
+    dims, dims_new, U, blocks = _case(p, 0.6, seed=5)
+    _, _, U2, _ = _case(p, 0.6, seed=6)
+    n_out = int(sum(int(dims_new[q]) * int(dims_new[pp]) for q, pp, _ in blocks))
+    opd = torch.from_numpy(p.op_data).cuda()
+    plan = lib.Renorm(dims, dims_new, blocks, opd.numel(), n_out)
+    st = torch.cuda.Stream()
+    for Uh in (U, U2):
+        Ud = torch.from_numpy(Uh).cuda()
+        ref = torch.full((n_out,), float("nan"), dtype=torch.float64, device="cuda")
+        off = lib.renormalise(dims, dims_new, Ud, blocks, opd, ref)
+        out = torch.full_like(ref, float("nan"))
+        st.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(st):
+            plan.run(Ud, opd, out, stream=st)
+        st.synchronize()
+        assert np.array_equal(off, plan.out_off)
+        assert torch.equal(out, ref)
+    plan.close()
