@@ -179,6 +179,44 @@ __global__ void k_diag_set(double* __restrict__ S, int lds, int mmax, const doub
     S[i * lds + j] = (i == j && i < r) ? theta[i] : 0.0;
 }
 
+// Jacobi rotation (c, s) that annihilates apq of the 2 x 2 block [[app, apq], [apq, aqq]],
+// d = aqq - app: t = tan of the angle is the root of smaller magnitude of
+// t^2 + 2 tau t - 1 = 0, tau = d / (2 apq).  Double-precision division and square roots
+// are long dependent chains on this GPU's few FP64 units, so the angle is formed in
+// single precision from d and apq scaled by a power of two (exact), and the pair is then
+// made orthonormal to double precision: with c, s the single-precision cosine and sine,
+// c^2 + s^2 = 1 + delta (|delta| < 2^-20), and c, s are divided by sqrt(1 + delta) =
+// 1 + delta / 2 - delta^2 / 8 + O(delta^3) through the series 1 - delta / 2 +
+// 3 delta^2 / 8 of its reciprocal.  The rotation is exactly orthogonal; the angle's
+// single-precision error leaves |apq| reduced by ~2^-22 of its scale instead of to zero,
+// which the next sweep removes (convergence is judged on the rounding-level threshold).
+__device__ __forceinline__ void rotation(double d, double apq, double* c, double* s) {
+    // scale by 2^-E, E the exponent of the larger magnitude (bit patterns; exact)
+    const long long em = max(__double_as_longlong(d) & 0x7FF0000000000000ll,
+                             __double_as_longlong(apq) & 0x7FF0000000000000ll);
+    const double sc = __longlong_as_double((2046ll << 52) - em);
+    const float df = float(d * sc), af = float(apq * sc);
+    if (!(fabsf(af) > 1e-18f * fabsf(df))) {   // angle below 1e-18: t = apq / d, cos 1 to double
+        *c = 1.0;
+        *s = apq / d;
+        return;
+    }
+    const float tau = df / (2.0f * af);
+    const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+    const float cf = rsqrtf(fmaf(t, t, 1.0f));
+    const double c0 = cf, s0 = double(t * cf);
+    const double delta = fma(c0, c0, fma(s0, s0, -1.0));
+    const double r = fma(delta, fma(delta, 0.375, -0.5), 1.0);
+    *c = c0 * r;
+    *s = s0 * r;
+}
+
+// Integer key whose order is the order of the finite double x.
+__device__ __forceinline__ long long order_key(double x) {
+    const long long b = __double_as_longlong(x);
+    return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFll);
+}
+
 // Cyclic Jacobi eigensolver of the symmetric m x m matrix S (row stride lds) in one CTA:
 // round-robin (circle-method) ordering, the m/2 disjoint rotations of a round applied
 // together.  theta ascending, U[i*ldu + j] = component i of eigenvector j.
@@ -254,11 +292,10 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ S, in
                 // the eigenvalues by < 1e-30 relative, and rotations below rounding level
                 // only regenerate rounding noise and run sweeps up to the limit
                 if (apq * apq > 1e-30 * fabs(app * aqq) + 1e-300) {
-                    const double tau = (aqq - app) / (2.0 * apq);
-                    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                    const double c = 1.0 / sqrt(1.0 + t * t);
+                    double c, s;
+                    rotation(aqq - app, apq, &c, &s);
                     const int slot = atomicAdd(&s_nr, 1);
-                    pp[slot] = p; qq[slot] = q; cs[slot] = c; sn[slot] = t * c;
+                    pp[slot] = p; qq[slot] = q; cs[slot] = c; sn[slot] = s;
                     s_rot = 1;
                 }
             }
@@ -296,14 +333,16 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ S, in
         if (s_rot == 0) break;   // a sweep without rotations: converged to rounding level
         __syncthreads();
     }
-    if (tid == 0) {                      // ascending order of the m real eigenvalues
-        for (int i = 0; i < m; ++i) order[i] = i;
-        for (int i = 0; i < m; ++i) {
-            int best = i;
-            for (int j = i + 1; j < m; ++j)
-                if (A[order[j] * ld + order[j]] < A[order[best] * ld + order[best]]) best = j;
-            const int t = order[i]; order[i] = order[best]; order[best] = t;
+    // ascending order of the m real eigenvalues (ties by index): the rank of eigenvalue
+    // i is the count of those before it, compared as integers (order-preserving keys)
+    for (int i = tid; i < m; i += nt) {
+        const long long ki = order_key(A[i * ld + i]);
+        int rank = 0;
+        for (int j = 0; j < m; ++j) {
+            const long long kj = order_key(A[j * ld + j]);
+            rank += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
         }
+        order[rank] = i;
     }
     __syncthreads();
     for (int j = tid; j < m; j += nt) theta[j] = A[order[j] * ld + order[j]];
