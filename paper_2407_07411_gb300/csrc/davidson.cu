@@ -30,6 +30,7 @@ constexpr int MAX_BASIS = 64;    // m_max limit of the Jacobi kernel
 struct DavidsonState {
     double *V = nullptr, *W = nullptr, *X = nullptr, *R = nullptr, *C = nullptr, *T = nullptr;
     double *diag = nullptr, *S = nullptr, *U = nullptr, *theta = nullptr, *small = nullptr, *partial = nullptr;
+    unsigned* done = nullptr;          // completion count of the dot-product kernel (zero between launches)
     int64_t n_chunks = 0, chunk = 0;   // dot-product partials: count and length
     int mmax = 0, kbmax = 0, block = 0, k_eig = 0;   // sizes the buffers were allocated for
     bool diag_ready = false;
@@ -37,16 +38,22 @@ struct DavidsonState {
         double* p[] = {V, W, X, R, C, T, diag, S, U, theta, small, partial};
         for (double* q : p)
             if (q) cudaFree(q);
+        if (done) cudaFree(done);
     }
 };
 
 namespace {
 
-// partial[(c*np + i)*nq + j] = sum over chunk c of P_i . Q_j   (fixed-order tree)
+// out[i*nq + j] = P_i . Q_j: partial[(c*np + i)*nq + j] = sum over chunk c (fixed-order
+// tree), then the CTA that finishes last (a counter, reset by that CTA for the next
+// launch) adds the chunks' partials in chunk order, so the result does not depend on
+// which CTA runs when.
 __global__ void __launch_bounds__(DOT_NT) k_multidot(const double* __restrict__ P, int64_t ldp, int np,
                                                      const double* __restrict__ Q, int64_t ldq, int nq,
-                                                     int64_t dim, int64_t chunk, double* __restrict__ partial) {
+                                                     int64_t dim, int64_t chunk, double* __restrict__ partial,
+                                                     double* __restrict__ out, unsigned* __restrict__ done) {
     __shared__ double red[DOT_NT];
+    __shared__ bool last;
     const int c = blockIdx.x, i = blockIdx.y;
     const int64_t n0 = int64_t(c) * chunk;
     const int64_t n1 = min(dim, n0 + chunk);
@@ -72,16 +79,20 @@ __global__ void __launch_bounds__(DOT_NT) k_multidot(const double* __restrict__ 
         if (threadIdx.x == 0) partial[(int64_t(c) * np + i) * nq + j] = red[0];
         __syncthreads();
     }
-}
-
-// out[e] = sum over chunks of partial[c*npq + e], chunks in order
-__global__ void k_chunk_reduce(const double* __restrict__ partial, int64_t n_chunks, int npq,
-                               double* __restrict__ out) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= npq) return;
-    double s = 0.0;
-    for (int64_t c = 0; c < n_chunks; ++c) s += partial[c * npq + e];
-    out[e] = s;
+    if (threadIdx.x == 0) {
+        __threadfence();   // this CTA's partials before its count
+        last = atomicAdd(done, 1u) == gridDim.x * gridDim.y - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int npq = np * nq;
+    for (int e = threadIdx.x; e < npq; e += DOT_NT) {
+        double s = 0.0;
+        for (int64_t cc = 0; cc < gridDim.x; ++cc) s += __ldcg(partial + cc * npq + e);
+        out[e] = s;
+    }
+    if (threadIdx.x == 0) *done = 0u;
 }
 
 // out_j = sum_{i<m} coef[i*ldc + col0 + j] * V_i  (j < nj <= MAXQ); sub: out_j -= ...
@@ -376,9 +387,8 @@ struct Run {
     int dots(const double* P, int np, const double* Q, int nq, double* out) {
         if (np == 0 || nq == 0) return DMRG_OK;
         k_multidot<<<dim3(unsigned(s->n_chunks), unsigned(np)), DOT_NT, 0, st>>>(P, dim, np, Q, dim, nq, dim, s->chunk,
-                                                                             s->partial);
-        k_chunk_reduce<<<blocks_for(np * nq), 256, 0, st>>>(s->partial, s->n_chunks, np * nq, out);
-        return check(cudaGetLastError(), "dot kernels");
+                                                                             s->partial, out, s->done);
+        return check(cudaGetLastError(), "dot kernel");
     }
     int lincomb(const double* coef, int ldc, int col0, int nj, int m, const double* V, double* out, int sub) {
         for (int j0 = 0; j0 < nj; j0 += MAXQ) {
@@ -467,6 +477,12 @@ int ensure_state(Handle* h, int mmax, int kbmax, int block, int k_eig) {
         (rc = al(&s->small, 4096, "small")) || (rc = al(&s->partial, s->n_chunks * MAX_BASIS * MAXQ, "partials"))) {
         h->release_davidson();
         return rc;
+    }
+    cudaError_t ce = cudaMalloc(reinterpret_cast<void**>(&s->done), sizeof(unsigned));
+    if (ce == cudaSuccess) ce = cudaMemset(s->done, 0, sizeof(unsigned));
+    if (ce != cudaSuccess) {
+        h->release_davidson();
+        return cuda_fail(ce, "dot counter");
     }
     cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(sizeof(double) * 2 * MAX_BASIS * (MAX_BASIS + 1)));

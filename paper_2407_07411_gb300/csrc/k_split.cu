@@ -69,6 +69,7 @@ struct SplitDevPlan {
     SPart* parts = nullptr;
     int64_t n_work1 = 0, n_work2 = 0, n_blocks = 0, n_xjobs = 0, n_items = 0, n_tiles = 0;
     std::vector<std::pair<int32_t, int32_t>> r1, r2;   // per-GEMM work ranges (per_gemm)
+    int32_t xchunks = 1, fin_chunks = 1;               // CTAs per psi job / per output block
     int n_chunks = 1;                                  // output chunks and their work ranges
     std::vector<int32_t> cw1, cw2, cr1, cr2;
     int64_t s2_len = 0, mid0 = 0, mid1 = 0;
@@ -323,10 +324,13 @@ struct XArgs {
     int64_t* s2;
     int64_t s2_len;
     int64_t mid0, mid1;   // exponents of the stage-2 intermediate vectors (reset to none)
+    int32_t vchunks;      // CTAs per psi job (XP_VCH vectors each)
 };
+constexpr int XP_VCH = 64;   // psi vectors per CTA of the psi pass (a multiple of 8)
 
-// One CTA per (psi job, Davidson vector): pass 1, one warp per vector (a column or a
-// row of the block), the exact exponent E and the estimate pass's term 1.005 2^-8
+// One CTA per (psi job, run of XP_VCH of its vectors, Davidson vector): pass 1, one warp
+// per vector (a column or a row of the block), the exact exponent E and the estimate
+// pass's term 1.005 2^-8
 // sum |x| 2^-E (rounded up); pass 2, the digits of 8 vectors x 32 K per warp item,
 // written as the 16-byte chunks of two 16-K tiles.  The grid also clears the stage-2
 // sums and resets the stage-2 vector bounds to "none".
@@ -339,13 +343,15 @@ __global__ void __launch_bounds__(256) k_xprep(XArgs a) {
         for (int64_t i = t0; i < a.s2_len; i += nthr) a.s2[i] = 0;
         for (int64_t i = a.mid0 + t0; i < a.mid1; i += nthr) a.ap_ex[i] = SPL_EXP_NONE;
     }
-    const SXJob X = a.xjobs[blockIdx.x];
+    const SXJob X = a.xjobs[blockIdx.x / a.vchunks];
+    const int k0 = int(blockIdx.x % a.vchunks) * XP_VCH, k1 = min(X.cp, k0 + XP_VCH);
+    if (k0 >= X.cp) return;
     const SJob J = a.jobs[X.job];
     const int v = blockIdx.y;
     const double* src = a.x + int64_t(v) * a.dim + X.off;
     int32_t* ex = a.ap_ex + J.out_exp + int64_t(v) * X.cp;
     float* xs = a.xs + J.out_exp + int64_t(v) * X.cp;
-    for (int k = warp; k < X.cp; k += 8) {
+    for (int k = k0 + warp; k < k1; k += 8) {
         int E = INT_MIN;
         if (k < X.nk)
             for (int K = lane; K < X.K; K += 32) E = max(E, exp_f64(src[int64_t(K) * X.ks + int64_t(k) * X.vs]));
@@ -365,9 +371,9 @@ __global__ void __launch_bounds__(256) k_xprep(XArgs a) {
     }
     __syncthreads();   // the exponents written above are visible to the whole CTA
     uint16_t (*sd)[8][32] = sd_all[warp];
-    const int ngrp = X.cp / 8, nsub = (X.K + 31) / 32;
+    const int g0 = k0 / 8, ngrp = (k1 - k0) / 8, nsub = (X.K + 31) / 32;
     for (int it = warp; it < ngrp * nsub; it += 8) {
-        const int g8 = it / nsub, sb = it - g8 * nsub;
+        const int g8 = g0 + it / nsub, sb = it - (it / nsub) * nsub;
         const int K = sb * 32 + lane;
 #pragma unroll
         for (int vv = 0; vv < 8; ++vv) {
@@ -1152,12 +1158,14 @@ __global__ void k_wait_selftest(int* status, long long limit) {
 // ----------------------------------------------------------------------------------
 // stage-2 sums -> FP64 wave function
 
+constexpr int FIN_CHUNK = 2048;   // output entries per CTA of the finalize pass
 __global__ void k_finalize(const SBlock* __restrict__ blocks, const SPart* __restrict__ parts,
                            const int64_t* __restrict__ s2, const int32_t* __restrict__ op_ex,
                            const int32_t* __restrict__ ap_ex, double* __restrict__ y, int64_t dim) {
     const SBlock B = blocks[blockIdx.x];
     const int v = blockIdx.y;
-    for (int e = threadIdx.x; e < B.rows * B.cols; e += blockDim.x) {
+    const int e1 = min(B.rows * B.cols, int(blockIdx.z + 1) * FIN_CHUNK);
+    for (int e = int(blockIdx.z) * FIN_CHUNK + threadIdx.x; e < e1; e += blockDim.x) {
         const int i = e / B.cols, j = e % B.cols;
         double sum = 0.0;
         for (int p = B.p0; p < B.p0 + B.np; ++p) {
@@ -1759,7 +1767,12 @@ int Handle::init_split(const double* op_data) {
             D.s1_flops[c] += G.order == 0 ? n * 2 * a * b * cc : n * 2 * b * cc * d;
             D.s2_flops[c] += G.order == 0 ? n * 2 * a * cc * d : n * 2 * a * b * d;
         }
-        for (const SXJob& X : H.xjobs) D.x_bytes += double(nv) * (8.0 * X.K * X.nk + 12.0 * X.K * X.cp);
+        for (const SXJob& X : H.xjobs) {
+            D.x_bytes += double(nv) * (8.0 * X.K * X.nk + 12.0 * X.K * X.cp);
+            D.xchunks = std::max<int32_t>(D.xchunks, int32_t(cdiv(X.cp, XP_VCH)));
+        }
+        for (const SBlock& B : H.blocks)
+            D.fin_chunks = std::max<int32_t>(D.fin_chunks, int32_t(cdiv(int64_t(B.rows) * B.cols, FIN_CHUNK)));
     }
     for (const SplitHost& H : hosts) {
         S->cap_w1.push_back(H.w1.size());
@@ -1877,9 +1890,9 @@ int Handle::apply_split(const double* x, double* y, int32_t nvec, cudaStream_t s
         return le;
     };
     if (D.n_xjobs > 0) {
-        XArgs xa{D.xjobs, D.jobs, x, plan.dim, S->ap_sl, S->ap_ex, S->xs, S->s2, D.s2_len, D.mid0, D.mid1};
+        XArgs xa{D.xjobs, D.jobs, x, plan.dim, S->ap_sl, S->ap_ex, S->xs, S->s2, D.s2_len, D.mid0, D.mid1, D.xchunks};
         prof.begin(S->kid_x, st, 0.0, D.x_bytes, &pe);
-        k_xprep<<<dim3(unsigned(D.n_xjobs), unsigned(nvec)), 256, 0, st>>>(xa);
+        k_xprep<<<dim3(unsigned(D.n_xjobs * D.xchunks), unsigned(nvec)), 256, 0, st>>>(xa);
         prof.end(pe, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "psi slices");
     }
@@ -1902,7 +1915,7 @@ int Handle::apply_split(const double* x, double* y, int32_t nvec, cudaStream_t s
     }
     if (D.n_blocks > 0) {
         prof.begin(S->kid_fin, st, 0.0, 0.0, &pe);
-        k_finalize<<<dim3(unsigned(D.n_blocks), unsigned(nvec)), 256, 0, st>>>(D.blocks, D.parts, S->s2, S->op_ex,
+        k_finalize<<<dim3(unsigned(D.n_blocks), unsigned(nvec), unsigned(D.fin_chunks)), 256, 0, st>>>(D.blocks, D.parts, S->s2, S->op_ex,
                                                                               S->ap_ex, y, plan.dim);
         prof.end(pe, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "finalize");
