@@ -270,12 +270,18 @@ int dmrg_heff_apply_noalloc(const int32_t* left, int32_t nl, const int32_t* righ
  *                     or a multiple of 8 up to 256.
  *   per_gemm          0 (default): each stage is one persistent launch over all its
  *                     GEMMs; 1: one launch per grouped GEMM (for comparison).
+ *   fp64_tile         output tile of the FP64 tile kernel: 0 (default) 32 x 32 (4
+ *                     warps), 1 64 x 32, 2 32 x 64 (8 warps); each element's sum runs
+ *                     in the same order whatever the tile.  The split path's slice GEMM
+ *                     tile is fixed at 128 x 96 (five accumulators of 96 columns fill
+ *                     480 of the 512 tensor-memory columns).
  */
 typedef struct {
     int32_t fp64_kchunk[3];
     int32_t fp64_ctas_per_sm;
     int32_t split_kchunk[3];
     int32_t per_gemm;
+    int32_t fp64_tile;
 } dmrg_schedule;
 
 /* Current schedule of the handle. */
@@ -288,18 +294,21 @@ int dmrg_heff_schedule_get(dmrg_heff_t h, dmrg_schedule* s);
 int dmrg_heff_schedule_set(dmrg_heff_t h, const dmrg_schedule* s);
 
 /* Outcome of dmrg_heff_autotune: applies timed, median ms per apply of the schedule
- * the handle had on entry and of the one chosen. */
+ * the handle had on entry and of the one chosen, and the output tile (rows x columns)
+ * of the GEMM kernel under the chosen schedule. */
 typedef struct {
     int32_t trials, nvec;
     double default_ms, best_ms;
     dmrg_schedule best;
+    int32_t tile_m, tile_n;
 } dmrg_tune_report;
 
 /*
  * Autotuner: times candidate schedules on this handle's plan with nvec vectors
  * (deterministic internal test vectors; `reps` timed applies per candidate, 1..100,
  * median) by coordinate descent over the stage-2 K extent of every shape class that
- * has GEMMs (and, FP64, the CTAs per SM), and leaves the fastest schedule in place.
+ * has GEMMs (and, FP64, the output tile and the CTAs per SM), and leaves the fastest
+ * schedule in place.
  * Allocates two nvec x dim device vectors for the duration and synchronises the
  * device.  Not for plan-only handles.
  */

@@ -62,11 +62,11 @@ class KernelStat(ctypes.Structure):
 
 class Schedule(ctypes.Structure):
     _fields_ = [("fp64_kchunk", ctypes.c_int32 * 3), ("fp64_ctas_per_sm", ctypes.c_int32),
-                ("split_kchunk", ctypes.c_int32 * 3), ("per_gemm", ctypes.c_int32)]
+                ("split_kchunk", ctypes.c_int32 * 3), ("per_gemm", ctypes.c_int32), ("fp64_tile", ctypes.c_int32)]
 
     def to_dict(self) -> dict:
         return dict(fp64_kchunk=list(self.fp64_kchunk), fp64_ctas_per_sm=self.fp64_ctas_per_sm,
-                    split_kchunk=list(self.split_kchunk), per_gemm=self.per_gemm)
+                    split_kchunk=list(self.split_kchunk), per_gemm=self.per_gemm, fp64_tile=self.fp64_tile)
 
     @classmethod
     def from_dict(cls, d: dict) -> "Schedule":
@@ -77,12 +77,14 @@ class Schedule(ctypes.Structure):
             s.split_kchunk[i] = int(v)
         s.fp64_ctas_per_sm = int(d["fp64_ctas_per_sm"])
         s.per_gemm = int(d["per_gemm"])
+        s.fp64_tile = int(d.get("fp64_tile", 0))
         return s
 
 
 class TuneReport(ctypes.Structure):
     _fields_ = [("trials", ctypes.c_int32), ("nvec", ctypes.c_int32), ("default_ms", ctypes.c_double),
-                ("best_ms", ctypes.c_double), ("best", Schedule)]
+                ("best_ms", ctypes.c_double), ("best", Schedule), ("tile_m", ctypes.c_int32),
+                ("tile_n", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -308,7 +310,7 @@ class HEff:
         r = TuneReport()
         _check(_lib.dmrg_heff_autotune(self._h, nvec, reps, ctypes.byref(r)))
         return dict(trials=r.trials, nvec=r.nvec, default_ms=r.default_ms, best_ms=r.best_ms,
-                    best=r.best.to_dict())
+                    best=r.best.to_dict(), tile=[r.tile_m, r.tile_n])
 
     def psi_blocks(self) -> np.ndarray:
         """Wave-function layout: rows (left sector, right sector, rows, cols, offset)."""

@@ -1,9 +1,9 @@
 // Schedule of the grouped GEMMs and its autotuner.
 //
 // A schedule fixes how the planned GEMMs are cut into work items (the K extent of a
-// stage-2 item, per shape class of contraction length), how many CTAs of the FP64
-// tile kernel share an SM, and whether each grouped GEMM runs as one persistent launch
-// of its stage or as a launch of its own.  The autotuner measures candidate schedules
+// stage-2 item, per shape class of contraction length, and the output tile of the FP64
+// kernel), how many CTAs of the FP64 tile kernel share an SM, and whether each grouped
+// GEMM runs as one persistent launch of its stage or as a launch of its own.  The autotuner measures candidate schedules
 // on the handle's own plan with CUDA events (coordinate descent: one parameter at a
 // time, every candidate of it, the fastest kept) and leaves the best one in place.
 #include <cuda_runtime.h>
@@ -36,6 +36,7 @@ Schedule from_abi(const dmrg_schedule& a) {
     }
     s.fp64_ctas_per_sm = a.fp64_ctas_per_sm;
     s.per_gemm = a.per_gemm;
+    s.fp64_tile = a.fp64_tile;
     return s;
 }
 
@@ -48,6 +49,7 @@ dmrg_schedule to_abi(const Schedule& s) {
     }
     a.fp64_ctas_per_sm = s.fp64_ctas_per_sm;
     a.per_gemm = s.per_gemm;
+    a.fp64_tile = s.fp64_tile;
     return a;
 }
 
@@ -76,6 +78,8 @@ int Handle::autotune(int32_t nvec, int32_t reps, dmrg_tune_report* rep) {
     rep->nvec = nvec;
     if (plan.dim == 0) {
         rep->best = to_abi(sched);
+        rep->tile_m = precision == DMRG_PREC_FP64 ? FP64_TILE_M[sched.fp64_tile] : SPL_TM;
+        rep->tile_n = precision == DMRG_PREC_FP64 ? FP64_TILE_N[sched.fp64_tile] : SPL_TN;
         return DMRG_OK;
     }
     double* x = nullptr;
@@ -138,10 +142,11 @@ int Handle::autotune(int32_t nvec, int32_t reps, dmrg_tune_report* rep) {
     };
     const std::vector<int> classes = present_classes(*this, nvec);
     if (precision == DMRG_PREC_FP64) {
+        tune(&best.fp64_tile, {0, 1, 2});
         for (int c : classes) tune(&best.fp64_kchunk[c], {256, 512, 1024, 2048, 4096, 0});
         std::vector<int32_t> ctas;
         for (int32_t v : {2, 4, 8, 16})
-            if (v < tiles_per_sm) ctas.push_back(v);
+            if (v < tiles_per_sm[best.fp64_tile]) ctas.push_back(v);
         ctas.push_back(0);
         tune(&best.fp64_ctas_per_sm, ctas);
     } else {
@@ -152,6 +157,8 @@ int Handle::autotune(int32_t nvec, int32_t reps, dmrg_tune_report* rep) {
     if (rc == DMRG_OK) rc = rc2;
     rep->best_ms = best_ms;
     rep->best = to_abi(sched);
+    rep->tile_m = precision == DMRG_PREC_FP64 ? FP64_TILE_M[sched.fp64_tile] : SPL_TM;
+    rep->tile_n = precision == DMRG_PREC_FP64 ? FP64_TILE_N[sched.fp64_tile] : SPL_TN;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (st) cudaStreamDestroy(st);

@@ -69,7 +69,8 @@ struct Profiler {
 struct Handle : dmrg_heff {
     Plan plan;
     int precision = 0, max_nvec = 1, n_slices = 0;
-    int device = 0, n_sm = 152, tiles_per_sm = 8;
+    int device = 0, n_sm = 152;
+    int tiles_per_sm[FP64_SHAPES] = {8, 8, 8};   // resident FP64 tile CTAs per SM, per tile shape
     bool plan_only = false;
     dmrg_memory mem{};              // device bytes (plan-only handles: what they would hold)
     int64_t split_mid_cap = 0;      // split path: intermediate bytes per output chunk (0: default)

@@ -70,7 +70,7 @@ int Handle::upload_fp64_work() {
     if ((rc = put(plan.tiles1, &d_tiles1, &cap_tiles1, "tiles")) != DMRG_OK) return rc;
     if ((rc = put(plan.tiles2, &d_tiles2, &cap_tiles2, "tiles")) != DMRG_OK) return rc;
     if ((rc = put(plan.reduces, &d_red, &cap_red, "reduce jobs")) != DMRG_OK) return rc;
-    const size_t part = size_t(plan.n_slots) * FP64_BM * FP64_BN * size_t(max_nvec);
+    const size_t part = size_t(plan.n_slots) * fp64_tile_elems(sched.fp64_tile) * size_t(max_nvec);
     if (precision == DMRG_PREC_FP64 && part > cap_part) {
         if (d_part) cudaFree(d_part);
         d_part = nullptr;
@@ -117,7 +117,7 @@ Spaces Handle::spaces(const double* x, double* y) const {
     Spaces s;
     s.ops = d_ops; s.x = x; s.scr = d_scr; s.y = y; s.part = d_part;
     s.x_vs = plan.dim; s.y_vs = plan.dim; s.scr_vs = plan.scratch_len;
-    s.part_vs = plan.n_slots * FP64_BM * FP64_BN;
+    s.part_vs = plan.n_slots * fp64_tile_elems(sched.fp64_tile);
     return s;
 }
 
@@ -128,7 +128,8 @@ int Handle::apply_fp64(const double* x, double* y, int32_t nvec, cudaStream_t st
     e = cudaMemsetAsync(d_counters, 0, sizeof(int32_t) * n_counters, st);
     if (e != cudaSuccess) return cuda_fail(e, "zero counters");
     const Spaces sp = spaces(x, y);
-    const int ctas = sched.fp64_ctas_per_sm > 0 ? std::min(sched.fp64_ctas_per_sm, tiles_per_sm) : tiles_per_sm;
+    const int shape = sched.fp64_tile, tps = tiles_per_sm[shape];
+    const int ctas = sched.fp64_ctas_per_sm > 0 ? std::min(sched.fp64_ctas_per_sm, tps) : tps;
     auto grid_for = [&](size_t n) {
         int64_t items = int64_t(n) * nvec;
         int64_t g = int64_t(n_sm) * ctas;
@@ -141,11 +142,11 @@ int Handle::apply_fp64(const double* x, double* y, int32_t nvec, cudaStream_t st
                      int32_t* counters) {
         if (!sched.per_gemm)
             return launch_fp64_tiles(d_t, int32_t(tl.size()), d_gemms, d_segs, sp, nvec, counters,
-                                     grid_for(tl.size()), st);
+                                     grid_for(tl.size()), st, shape);
         for (size_t r = 0; r < rg.size(); ++r) {
             const int32_t n = rg[r].second - rg[r].first;
             cudaError_t le = launch_fp64_tiles(d_t + rg[r].first, n, d_gemms, d_segs, sp, nvec,
-                                               counters + r, grid_for(size_t(n)), st);
+                                               counters + r, grid_for(size_t(n)), st, shape);
             if (le != cudaSuccess) return le;
         }
         return cudaSuccess;
@@ -165,8 +166,8 @@ int Handle::apply_fp64(const double* x, double* y, int32_t nvec, cudaStream_t st
         if (e != cudaSuccess) return cuda_fail(e, "stage-2 tiles");
     }
     if (!plan.reduces.empty()) {
-        prof.begin(kid_red, st, 0.0, double(plan.reduces.size()) * FP64_BM * FP64_BN * 8.0 * nvec, &pe);
-        e = launch_fp64_reduce(d_red, int32_t(plan.reduces.size()), d_gemms, sp, nvec, st);
+        prof.begin(kid_red, st, 0.0, double(plan.reduces.size()) * fp64_tile_elems(shape) * 8.0 * nvec, &pe);
+        e = launch_fp64_reduce(d_red, int32_t(plan.reduces.size()), d_gemms, sp, nvec, st, shape);
         prof.end(pe, st);
         if (e != cudaSuccess) return cuda_fail(e, "stage-2 reduce");
     }
@@ -309,7 +310,7 @@ int create_from_plan(Handle* h, const dmrg_heff_opts& o, const double* op_data, 
         return dmrg::cuda_fail(e, "cudaGetDevice");
     }
     cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
-    h->tiles_per_sm = dmrg::fp64_tiles_per_sm();
+    for (int sh = 0; sh < dmrg::FP64_SHAPES; ++sh) h->tiles_per_sm[sh] = dmrg::fp64_tiles_per_sm(sh);
     const dmrg::Plan& P = h->plan;
     // Algorithmic work per vector of each stage: flops of the planned order, bytes =
     // operator blocks read once + intermediates written (stage 1) or read (stage 2)

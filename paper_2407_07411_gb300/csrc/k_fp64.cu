@@ -1,6 +1,7 @@
 // FP64 path: grouped GEMM tiles on the FP64 tensor cores (DMMA, mma.sync
-// m16n8k16 .f64), one 32x32 output tile per CTA iteration, K staged through
-// shared memory 16 columns at a time.
+// m16n8k16 .f64), one output tile per CTA iteration (32x32 with 4 warps, or 64x32 /
+// 32x64 with 8, by the schedule), K staged through shared memory 16 columns at a time;
+// every warp owns a 16x16 quarter-tile.
 //
 // On GB300 the FP64 tensor pipe sustains about 1.1 TFLOP/s (m16n8k16, measured by
 // the library's probe; m8n8k4 and plain DFMA about 1.0-1.05), three orders of
@@ -16,8 +17,9 @@
 namespace dmrg {
 namespace {
 
-constexpr int BM = FP64_BM, BN = FP64_BN, BK = FP64_BK;
-constexpr int NT = 128;  // 4 warps, each a 16x16 quarter of the tile
+constexpr int BK = FP64_BK;
+template <int BM, int BN>
+constexpr int fp64_threads() { return (BM / 16) * (BN / 16) * 32; }
 
 __device__ __forceinline__ const double* space_ptr(const Spaces& sp, int32_t s, int v) {
     switch (s) {
@@ -38,10 +40,12 @@ __device__ __forceinline__ void dmma16816(double (&c)[4], const double (&a)[8], 
           "d"(b[0]), "d"(b[1]), "d"(b[2]), "d"(b[3]));
 }
 
-__global__ void __launch_bounds__(NT) k_fp64_tiles(const Tile* __restrict__ tiles, int32_t n_tiles,
+template <int BM, int BN>
+__global__ void __launch_bounds__(fp64_threads<BM, BN>()) k_fp64_tiles(const Tile* __restrict__ tiles, int32_t n_tiles,
                                                    const Gemm* __restrict__ gemms,
                                                    const Seg* __restrict__ segs, Spaces sp,
                                                    int32_t nvec, int32_t* counter) {
+    constexpr int NT = fp64_threads<BM, BN>();
     __shared__ double sL[BM][BK + 1];
     __shared__ double sR[BK][BN + 1];
     __shared__ const double* s_lp[BK];
@@ -51,7 +55,7 @@ __global__ void __launch_bounds__(NT) k_fp64_tiles(const Tile* __restrict__ tile
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, tg = lane & 3;
-    const int wm = (warp >> 1) * 16, wn = (warp & 1) * 16;
+    const int wm = (warp / (BN / 16)) * 16, wn = (warp % (BN / 16)) * 16;
     const int64_t n_items = int64_t(n_tiles) * nvec;
 
     for (;;) {
@@ -154,8 +158,10 @@ __global__ void __launch_bounds__(NT) k_fp64_tiles(const Tile* __restrict__ tile
     }
 }
 
-__global__ void __launch_bounds__(NT) k_fp64_reduce(const Reduce* __restrict__ red,
+template <int BM, int BN>
+__global__ void __launch_bounds__(128) k_fp64_reduce(const Reduce* __restrict__ red,
                                                     const Gemm* __restrict__ gemms, Spaces sp) {
+    constexpr int NT = 128;
     const Reduce rj = red[blockIdx.x];
     const int v = blockIdx.y;
     const Gemm gm = gemms[rj.gemm];
@@ -175,22 +181,39 @@ __global__ void __launch_bounds__(NT) k_fp64_reduce(const Reduce* __restrict__ r
 
 cudaError_t launch_fp64_tiles(const Tile* tiles, int32_t n_tiles, const Gemm* gemms,
                               const Seg* segs, const Spaces& sp, int32_t nvec, int32_t* counter,
-                              int32_t grid, cudaStream_t st) {
+                              int32_t grid, cudaStream_t st, int shape) {
     if (n_tiles <= 0) return cudaSuccess;
-    k_fp64_tiles<<<grid, NT, 0, st>>>(tiles, n_tiles, gemms, segs, sp, nvec, counter);
+    if (shape == 1)
+        k_fp64_tiles<64, 32><<<grid, fp64_threads<64, 32>(), 0, st>>>(tiles, n_tiles, gemms, segs, sp, nvec, counter);
+    else if (shape == 2)
+        k_fp64_tiles<32, 64><<<grid, fp64_threads<32, 64>(), 0, st>>>(tiles, n_tiles, gemms, segs, sp, nvec, counter);
+    else
+        k_fp64_tiles<32, 32><<<grid, fp64_threads<32, 32>(), 0, st>>>(tiles, n_tiles, gemms, segs, sp, nvec, counter);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fp64_reduce(const Reduce* red, int32_t n_red, const Gemm* gemms,
-                               const Spaces& sp, int32_t nvec, cudaStream_t st) {
+                               const Spaces& sp, int32_t nvec, cudaStream_t st, int shape) {
     if (n_red <= 0) return cudaSuccess;
-    k_fp64_reduce<<<dim3(n_red, nvec), NT, 0, st>>>(red, gemms, sp);
+    if (shape == 1)
+        k_fp64_reduce<64, 32><<<dim3(n_red, nvec), 128, 0, st>>>(red, gemms, sp);
+    else if (shape == 2)
+        k_fp64_reduce<32, 64><<<dim3(n_red, nvec), 128, 0, st>>>(red, gemms, sp);
+    else
+        k_fp64_reduce<32, 32><<<dim3(n_red, nvec), 128, 0, st>>>(red, gemms, sp);
     return cudaGetLastError();
 }
 
-int fp64_tiles_per_sm() {
+int fp64_tiles_per_sm(int shape) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fp64_tiles, NT, 0) != cudaSuccess) return 8;
+    cudaError_t e;
+    if (shape == 1)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fp64_tiles<64, 32>, fp64_threads<64, 32>(), 0);
+    else if (shape == 2)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fp64_tiles<32, 64>, fp64_threads<32, 64>(), 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fp64_tiles<32, 32>, fp64_threads<32, 32>(), 0);
+    if (e != cudaSuccess) return 8;
     return n > 0 ? n : 1;
 }
 

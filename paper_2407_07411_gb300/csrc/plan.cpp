@@ -272,8 +272,9 @@ int check_schedule(const Schedule& S, std::string* err) {
             return DMRG_ERR_INVALID_ARG;
         }
     }
-    if (S.fp64_ctas_per_sm < 0 || S.fp64_ctas_per_sm > 64 || (S.per_gemm != 0 && S.per_gemm != 1)) {
-        *err = "schedule: CTAs per SM in [0, 64], per_gemm 0 or 1";
+    if (S.fp64_ctas_per_sm < 0 || S.fp64_ctas_per_sm > 64 || (S.per_gemm != 0 && S.per_gemm != 1) ||
+        S.fp64_tile < 0 || S.fp64_tile >= FP64_SHAPES) {
+        *err = "schedule: CTAs per SM in [0, 64], per_gemm 0 or 1, fp64_tile 0..2";
         return DMRG_ERR_INVALID_ARG;
     }
     return DMRG_OK;
@@ -283,18 +284,19 @@ int build_fp64_work(Plan& P, const Schedule& S, std::string* err) {
     int rc = check_schedule(S, err);
     if (rc != DMRG_OK) return rc;
     P.tiles1.clear(); P.tiles2.clear(); P.reduces.clear(); P.ranges1.clear(); P.ranges2.clear();
+    const int32_t BM = FP64_TILE_M[S.fp64_tile], BN = FP64_TILE_N[S.fp64_tile];
     for (int32_t gi : P.s1gemms) {
         const Gemm& m = P.gemms[gi];
-        for (int32_t m0 = 0; m0 < m.M; m0 += FP64_BM)
-            for (int32_t n0 = 0; n0 < m.N; n0 += FP64_BN) P.tiles1.push_back({0, m.K, gi, m0, n0, -1});
+        for (int32_t m0 = 0; m0 < m.M; m0 += BM)
+            for (int32_t n0 = 0; n0 < m.N; n0 += BN) P.tiles1.push_back({0, m.K, gi, m0, n0, -1});
     }
     int64_t slot = 0;
     for (int32_t gi : P.s2gemms) {
         const Gemm& m = P.gemms[gi];
         const int64_t kc = S.fp64_kchunk[kclass(m.K)] > 0 ? S.fp64_kchunk[kclass(m.K)] : m.K;
         const int64_t ns = kc > 0 ? (m.K + kc - 1) / kc : 1;
-        for (int32_t m0 = 0; m0 < m.M; m0 += FP64_BM)
-            for (int32_t n0 = 0; n0 < m.N; n0 += FP64_BN) {
+        for (int32_t m0 = 0; m0 < m.M; m0 += BM)
+            for (int32_t n0 = 0; n0 < m.N; n0 += BN) {
                 if (ns <= 1) {
                     P.tiles2.push_back({0, m.K, gi, m0, n0, -1});
                     continue;

@@ -65,6 +65,7 @@ struct Schedule {
     int32_t fp64_ctas_per_sm = 0;                      // 0: the occupancy limit
     int32_t split_kchunk[N_KCLASS] = {0, 0, 0};        // K tiles per split stage-2 item (0: adaptive)
     int32_t per_gemm = 0;                              // 1: one launch per grouped GEMM
+    int32_t fp64_tile = 0;                             // FP64 output tile shape (FP64_TILE_M/N)
 };
 
 struct Group {
@@ -105,7 +106,10 @@ struct Plan {
 };
 
 // Tile shape of the FP64 kernels (the K extent of stage-2 items is scheduled).
-constexpr int FP64_BM = 32, FP64_BN = 32, FP64_BK = 16;
+constexpr int FP64_BM = 32, FP64_BN = 32, FP64_BK = 16;   // the default tile (shape 0)
+constexpr int FP64_SHAPES = 3;
+constexpr int FP64_TILE_M[FP64_SHAPES] = {32, 64, 32}, FP64_TILE_N[FP64_SHAPES] = {32, 32, 64};
+inline int fp64_tile_elems(int shape) { return FP64_TILE_M[shape] * FP64_TILE_N[shape]; }   // partial-slot stride
 
 // Validates the inputs and builds the plan; returns 0 or a DMRG_ERR_* code with
 // a message in *err.

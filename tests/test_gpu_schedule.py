@@ -12,7 +12,7 @@ from tests.gpu_util import gpu_apply, rel_fro
 
 pytestmark = pytest.mark.gpu
 lib = pytest.importorskip("paper_2407_07411_gb300")
-DEFAULT = dict(fp64_kchunk=[512, 512, 2048], fp64_ctas_per_sm=0, split_kchunk=[0, 0, 0], per_gemm=0)
+DEFAULT = dict(fp64_kchunk=[512, 512, 2048], fp64_ctas_per_sm=0, split_kchunk=[0, 0, 0], per_gemm=0, fp64_tile=0)
 
 
 @pytest.mark.parametrize("name,n_terms", [("mid", 200), ("heavy", 80)])
@@ -30,6 +30,13 @@ def test_fp64_schedules(name, n_terms):
         h.schedule = sched
         assert rel_fro(gpu_apply(h, X), ref) <= 1e-12
         assert rel_fro(gpu_apply(h, X[:1]), ref[:1]) <= 1e-12
+    # the output tile: each element's sum runs in the same order whatever the tile, so
+    # with the same K chunks the results are the same bits
+    for tile in (1, 2):
+        h.schedule = dict(DEFAULT, fp64_tile=tile)
+        assert np.array_equal(gpu_apply(h, X), y0)
+        h.schedule = dict(DEFAULT, fp64_tile=tile, per_gemm=1, fp64_ctas_per_sm=3)
+        assert np.array_equal(gpu_apply(h, X), y0)
 
 
 @pytest.mark.parametrize("name,n_terms,nvec", [("heavy", 120, 4), ("mid", 200, 2)])
@@ -56,6 +63,8 @@ def test_autotune(prec, tol):
     assert r["nvec"] == 2 and r["trials"] >= 2
     assert 0 < r["best_ms"] <= r["default_ms"]
     assert h.schedule == r["best"] and r["best"]["per_gemm"] == 0
+    want = [(32, 32), (64, 32), (32, 64)][r["best"]["fp64_tile"]] if prec == "fp64" else (128, 96)
+    assert tuple(r["tile"]) == want
     X = p.random_vectors(2)
     assert rel_fro(gpu_apply(h, X), heff.apply(p, X)) <= tol
     with pytest.raises(lib.DmrgError):

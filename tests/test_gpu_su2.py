@@ -128,7 +128,7 @@ def test_split_schedules_and_autotune():
     h = lib.HEff.from_problem(p, precision="split", max_nvec=2)
     y0 = gpu_apply(h, X)
     assert rel_fro(y0, ref) <= TOL["split"]
-    base = dict(fp64_kchunk=[512, 512, 2048], fp64_ctas_per_sm=0, split_kchunk=[0, 0, 0], per_gemm=0)
+    base = dict(fp64_kchunk=[512, 512, 2048], fp64_ctas_per_sm=0, split_kchunk=[0, 0, 0], per_gemm=0, fp64_tile=0)
     for sched in (dict(base, split_kchunk=[8, 64, 256]), dict(base, per_gemm=1)):
         h.schedule = sched
         assert np.array_equal(gpu_apply(h, X), y0)
