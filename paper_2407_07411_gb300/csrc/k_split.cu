@@ -1090,6 +1090,9 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_uest(EstArgs a) {
             const bool rv_ok = r < G.M;
             const int ea = rv_ok ? a.op_ex[G.er_off + r] : SPL_EXP_NONE;
             const int sa_i = rv_ok ? a.srow[G.er_off + r] : 0;
+            // the level-0 sums: an item of one chunk (every stage-1 item up to 1024 K)
+            // keeps the exact FP32 sum itself (bits in acc); longer ones add chunks in int
+            const bool one_chunk = W.k1 - W.k0 <= EST_DRAIN_KT;
             int acc[UM_EPI_COLS];
 #pragma unroll
             for (int j = 0; j < UM_EPI_COLS; ++j) acc[j] = 0;
@@ -1103,8 +1106,13 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_uest(EstArgs a) {
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 tc_fence_before();
                 mbar_arrive(&sm.tempty[slot]);
+                if (one_chunk) {
 #pragma unroll
-                for (int j = 0; j < UM_EPI_COLS; ++j) acc[j] += __float2int_rn(__uint_as_float(rv[j]));
+                    for (int j = 0; j < UM_EPI_COLS; ++j) acc[j] = int(rv[j]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < UM_EPI_COLS; ++j) acc[j] += __float2int_rn(__uint_as_float(rv[j]));
+                }
             }
             if (!ok) break;
             const int i = rv_ok ? r % G.per : 0;
@@ -1125,7 +1133,8 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_uest(EstArgs a) {
                     vend += G.cp;
                     Emax = SPL_EXP_NONE;
                 }
-                const float f = (float(abs(acc[j])) * (1.0f / 16384.0f) + xsj + sa) * (1.0f + 1.0f / 1048576.0f) +
+                const float aj = one_chunk ? fabsf(__int_as_float(acc[j])) : float(abs(acc[j]));   // exact either way
+                const float f = (aj * (1.0f / 16384.0f) + xsj + sa) * (1.0f + 1.0f / 1048576.0f) +
                                 (1.0f / 1073741824.0f);
                 // f is a positive normal float: f < 2^(biased exponent - 126)
                 const int e = int((__float_as_uint(f) >> 23) & 255u) - 126;
