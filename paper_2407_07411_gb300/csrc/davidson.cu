@@ -47,26 +47,34 @@ namespace {
 // out[i*nq + j] = P_i . Q_j: partial[(c*np + i)*nq + j] = sum over chunk c (fixed-order
 // tree), then the CTA that finishes last (a counter, reset by that CTA for the next
 // launch) adds the chunks' partials in chunk order, so the result does not depend on
-// which CTA runs when.
+// which CTA runs when.  With gridDim.z = 2 the same is done for out2 = P2 . Q2 (CTAs of
+// z = 1), and with S given the last CTA also writes the symmetric Rayleigh-Ritz entries
+// S[i][m0 + j] = S[m0 + j][i] = (out[i*nq + j] + out2[i*nq + j]) / 2.
 __global__ void __launch_bounds__(DOT_NT) k_multidot(const double* __restrict__ P, int64_t ldp, int np,
                                                      const double* __restrict__ Q, int64_t ldq, int nq,
                                                      int64_t dim, int64_t chunk, double* __restrict__ partial,
-                                                     double* __restrict__ out, unsigned* __restrict__ done) {
+                                                     double* __restrict__ out, unsigned* __restrict__ done,
+                                                     const double* __restrict__ P2, const double* __restrict__ Q2,
+                                                     double* __restrict__ out2, double* __restrict__ S, int lds,
+                                                     int m0) {
     __shared__ double red[DOT_NT];
     __shared__ bool last;
-    const int c = blockIdx.x, i = blockIdx.y;
+    const int c = blockIdx.x, i = blockIdx.y, z = blockIdx.z;
+    const int npq = np * nq;
     const int64_t n0 = int64_t(c) * chunk;
     const int64_t n1 = min(dim, n0 + chunk);
     double acc[MAXQ];
 #pragma unroll
     for (int j = 0; j < MAXQ; ++j) acc[j] = 0.0;
-    const double* p = P + i * ldp;
+    const double* p = (z ? P2 : P) + i * ldp;
+    const double* Qz = z ? Q2 : Q;
     for (int64_t n = n0 + threadIdx.x; n < n1; n += DOT_NT) {
         const double pv = p[n];
 #pragma unroll
         for (int j = 0; j < MAXQ; ++j)
-            if (j < nq) acc[j] += pv * Q[j * ldq + n];
+            if (j < nq) acc[j] += pv * Qz[j * ldq + n];
     }
+    double* part = partial + int64_t(z) * gridDim.x * npq;
 #pragma unroll
     for (int j = 0; j < MAXQ; ++j) {
         if (j >= nq) break;
@@ -76,22 +84,98 @@ __global__ void __launch_bounds__(DOT_NT) k_multidot(const double* __restrict__ 
             if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
             __syncthreads();
         }
-        if (threadIdx.x == 0) partial[(int64_t(c) * np + i) * nq + j] = red[0];
+        if (threadIdx.x == 0) part[(int64_t(c) * np + i) * nq + j] = red[0];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         __threadfence();   // this CTA's partials before its count
-        last = atomicAdd(done, 1u) == gridDim.x * gridDim.y - 1;
+        last = atomicAdd(done, 1u) == gridDim.x * gridDim.y * gridDim.z - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    const int npq = np * nq;
     for (int e = threadIdx.x; e < npq; e += DOT_NT) {
-        double s = 0.0;
-        for (int64_t cc = 0; cc < gridDim.x; ++cc) s += __ldcg(partial + cc * npq + e);
-        out[e] = s;
+        double s1 = 0.0, s2 = 0.0;
+        for (int64_t cc = 0; cc < gridDim.x; ++cc) s1 += __ldcg(partial + cc * npq + e);
+        out[e] = s1;
+        if (gridDim.z > 1) {
+            const double* part2 = partial + int64_t(gridDim.x) * npq;
+            for (int64_t cc = 0; cc < gridDim.x; ++cc) s2 += __ldcg(part2 + cc * npq + e);
+            out2[e] = s2;
+            if (S) {
+                const int ii = e / nq, jj = e - ii * nq;
+                const double v = 0.5 * (s1 + s2);
+                S[ii * lds + m0 + jj] = v;
+                S[(m0 + jj) * lds + ii] = v;
+            }
+        }
     }
+    if (threadIdx.x == 0) *done = 0u;
+}
+
+// Ritz vectors and residuals of the lowest kb pairs in one pass over the vectors:
+// X_j = sum_{i<m} U[i][j] V_i, R_j = sum_{i<m} U[i][j] W_i - theta_j X_j (the sums in
+// the order of i), and |R_j|^2: per-CTA tree sums in partial, added in CTA order by the
+// CTA that finishes last, which also copies theta[0:m] next to them.
+__global__ void __launch_bounds__(DOT_NT) k_ritz(const double* __restrict__ U, int ldu, int kb, int m,
+                                                 const double* __restrict__ V, const double* __restrict__ W,
+                                                 int64_t dim, double* __restrict__ X, double* __restrict__ R,
+                                                 const double* __restrict__ theta, double* __restrict__ norms,
+                                                 double* __restrict__ theta_out, double* __restrict__ partial,
+                                                 unsigned* __restrict__ done) {
+    __shared__ double red[DOT_NT];
+    __shared__ bool last;
+    double sq[MAXQ];
+#pragma unroll
+    for (int j = 0; j < MAXQ; ++j) sq[j] = 0.0;
+    for (int64_t n = int64_t(blockIdx.x) * DOT_NT + threadIdx.x; n < dim; n += int64_t(gridDim.x) * DOT_NT) {
+        double ax[MAXQ], aw[MAXQ];
+#pragma unroll
+        for (int j = 0; j < MAXQ; ++j) ax[j] = aw[j] = 0.0;
+        for (int i = 0; i < m; ++i) {
+            const double v = V[i * dim + n], w = W[i * dim + n];
+#pragma unroll
+            for (int j = 0; j < MAXQ; ++j)
+                if (j < kb) {
+                    const double u = U[i * ldu + j];
+                    ax[j] += u * v;
+                    aw[j] += u * w;
+                }
+        }
+#pragma unroll
+        for (int j = 0; j < MAXQ; ++j)
+            if (j < kb) {
+                const double r = aw[j] - theta[j] * ax[j];
+                X[j * dim + n] = ax[j];
+                R[j * dim + n] = r;
+                sq[j] += r * r;
+            }
+    }
+#pragma unroll
+    for (int j = 0; j < MAXQ; ++j) {
+        if (j >= kb) break;
+        red[threadIdx.x] = sq[j];
+        __syncthreads();
+        for (int s = DOT_NT / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[int64_t(blockIdx.x) * kb + j] = red[0];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int j = threadIdx.x; j < kb; j += DOT_NT) {
+        double s = 0.0;
+        for (int64_t cc = 0; cc < gridDim.x; ++cc) s += __ldcg(partial + cc * kb + j);
+        norms[j] = s;
+    }
+    for (int j = threadIdx.x; j < m; j += DOT_NT) theta_out[j] = theta[j];
     if (threadIdx.x == 0) *done = 0u;
 }
 
@@ -116,14 +200,6 @@ __global__ void k_lincomb(const double* __restrict__ coef, int ldc, int col0, in
             if (sub) out[j * ldo + n] -= acc[j];
             else out[j * ldo + n] = acc[j];
         }
-}
-
-// R_j -= theta[j] X_j for j < kb
-__global__ void k_residual(double* __restrict__ R, const double* __restrict__ X, const double* __restrict__ theta,
-                           int kb, int64_t dim) {
-    const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (n >= dim) return;
-    for (int j = 0; j < kb; ++j) R[j * dim + n] -= theta[j] * X[j * dim + n];
 }
 
 // out = r / (diag - theta[j]) with the denominator floor
@@ -172,17 +248,7 @@ __global__ void k_lanczos_probe(double* __restrict__ out, const double* __restri
     out[2] = *beta2_j;
 }
 
-// S[i][m0+j] = S[m0+j][i] = (G1[i][j] + G2[i][j]) / 2 for i < m, j < nb (G ld = nb)
-__global__ void k_sym_update(double* __restrict__ S, int lds, const double* __restrict__ G1,
-                             const double* __restrict__ G2, int m, int m0, int nb) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= m * nb) return;
-    const int i = e / nb, j = e % nb;
-    const double v = 0.5 * (G1[e] + G2[e]);
-    S[i * lds + m0 + j] = v;
-    S[(m0 + j) * lds + i] = v;
-}
-
+// S after a thick restart: diag(theta[0:r]) in the leading r x r block, zero elsewhere
 __global__ void k_diag_set(double* __restrict__ S, int lds, int mmax, const double* __restrict__ theta, int r) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= mmax * mmax) return;
@@ -386,8 +452,8 @@ struct Run {
     // out[i*nq + j] = P_i . Q_j  (np <= MAX_BASIS, nq <= MAXQ); result in s->small
     int dots(const double* P, int np, const double* Q, int nq, double* out) {
         if (np == 0 || nq == 0) return DMRG_OK;
-        k_multidot<<<dim3(unsigned(s->n_chunks), unsigned(np)), DOT_NT, 0, st>>>(P, dim, np, Q, dim, nq, dim, s->chunk,
-                                                                             s->partial, out, s->done);
+        k_multidot<<<dim3(unsigned(s->n_chunks), unsigned(np)), DOT_NT, 0, st>>>(
+            P, dim, np, Q, dim, nq, dim, s->chunk, s->partial, out, s->done, nullptr, nullptr, nullptr, nullptr, 0, 0);
         return check(cudaGetLastError(), "dot kernel");
     }
     int lincomb(const double* coef, int ldc, int col0, int nj, int m, const double* V, double* out, int sub) {
@@ -427,20 +493,29 @@ struct Run {
         *kept = true;
         return DMRG_OK;
     }
-    // S entries of the new columns [m0, m): S_ij = (V_i.W_j + V_j.W_i)/2
+    // S entries of the new columns [m0, m): S_ij = (V_i.W_j + V_j.W_i)/2, both dot sets and
+    // the update in one launch
     int s_update(int m0, int m) {
         const int nb = m - m0;
         double* g1 = s->small + 256;
         double* g2 = g1 + MAX_BASIS * MAXQ;
         for (int j0 = 0; j0 < nb; j0 += MAXQ) {
             const int nq = nb - j0 < MAXQ ? nb - j0 : MAXQ;
+            k_multidot<<<dim3(unsigned(s->n_chunks), unsigned(m), 2u), DOT_NT, 0, st>>>(
+                s->V, dim, m, s->W + int64_t(m0 + j0) * dim, dim, nq, dim, s->chunk, s->partial, g1, s->done, s->W,
+                s->V + int64_t(m0 + j0) * dim, g2, s->S, mmax, m0 + j0);
             int rc;
-            if ((rc = dots(s->V, m, s->W + int64_t(m0 + j0) * dim, nq, g1))) return rc;
-            if ((rc = dots(s->W, m, s->V + int64_t(m0 + j0) * dim, nq, g2))) return rc;
-            k_sym_update<<<blocks_for(m * nq), 256, 0, st>>>(s->S, mmax, g1, g2, m, m0 + j0, nq);
             if ((rc = check(cudaGetLastError(), "S update"))) return rc;
         }
         return DMRG_OK;
+    }
+    // Ritz vectors X, residuals R and |R_j|^2 (into small[2048 + j]) with theta[0:m] next to
+    // them (small[2048 + MAX_BASIS + j]), one launch
+    int ritz(int kb, int m) {
+        const int64_t grid = std::min<int64_t>((dim + DOT_NT - 1) / DOT_NT, s->n_chunks * MAX_BASIS);
+        k_ritz<<<unsigned(grid), DOT_NT, 0, st>>>(s->U, mmax, kb, m, s->V, s->W, dim, s->X, s->R, s->theta,
+                                                   s->small + 2048, s->small + 2048 + MAX_BASIS, s->partial, s->done);
+        return check(cudaGetLastError(), "ritz vectors");
     }
 };
 
@@ -474,7 +549,7 @@ int ensure_state(Handle* h, int mmax, int kbmax, int block, int k_eig) {
         (rc = al(&s->C, int64_t(block) * dim, "C")) || (rc = al(&s->T, int64_t(k_eig + block) * dim, "T")) ||
         (rc = al(&s->diag, dim, "diag")) || (rc = al(&s->S, mmax * mmax, "S")) ||
         (rc = al(&s->U, mmax * mmax, "U")) || (rc = al(&s->theta, mmax, "theta")) ||
-        (rc = al(&s->small, 4096, "small")) || (rc = al(&s->partial, s->n_chunks * MAX_BASIS * MAXQ, "partials"))) {
+        (rc = al(&s->small, 4096, "small")) || (rc = al(&s->partial, 2 * s->n_chunks * MAX_BASIS * MAXQ, "partials"))) {
         h->release_davidson();
         return rc;
     }
@@ -544,16 +619,8 @@ extern "C" int dmrg_davidson(dmrg_heff_t hh, int32_t k_eig, double tol, int32_t 
         if ((rc = run.check(cudaGetLastError(), "jacobi"))) return rc;
         m_prev = m;
         kb = m < kbmax ? m : kbmax;
-        if ((rc = run.lincomb(s->U, mmax, 0, kb, m, s->V, s->X, 0))) return rc;
-        if ((rc = run.lincomb(s->U, mmax, 0, kb, m, s->W, s->R, 0))) return rc;
-        k_residual<<<blocks_for(dim), 256, 0, st>>>(s->R, s->X, s->theta, kb, dim);
-        for (int j = 0; j < kb; ++j)
-            if ((rc = run.dots(s->R + j * dim, 1, s->R + j * dim, 1, s->small + 2048 + j))) return rc;
+        if ((rc = run.ritz(kb, m))) return rc;
         // Ritz values next to the residual norms: one read-back per step
-        if ((rc = run.check(cudaMemcpyAsync(s->small + 2048 + MAX_BASIS, s->theta, sizeof(double) * m,
-                                            cudaMemcpyDeviceToDevice, st),
-                            "stage theta")))
-            return rc;
         if ((rc = run.check(cudaMemcpy(rb.data(), s->small + 2048, sizeof(double) * (MAX_BASIS + m),
                                        cudaMemcpyDeviceToHost),
                             "read residuals and theta")))
