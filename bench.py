@@ -53,10 +53,10 @@ NCU_TRAFFIC = {
     # 1216.0) / 4 MB, k_fp64_tiles (708.0 + 998.8) / 2 MB per launch
     ("1d4e0711bb97b9a9e36d9a142b4bae3ef00a40cd9656b8dffcb7a602e566ed1e", "su2_mid"): dict(traffic=1206.8e6),
     ("7ea6b95187a63352e09b039a09918be5e89d2a14561ebf2f4d93d0eae118ec22", "su2_mid"): dict(traffic=853.4e6),
-    # k_umma, precision workload, captured on its first 200 terms: (2648.3 + 2655.6) / 2 MB
+    # k_umma, precision workload, captured on its first 200 terms: (2651.0 + 2655.3) / 2 MB
     # per launch against 2580.4 MB of algorithmic bytes per launch (profiles/split_umma_precision.md)
-    ("b2b2275a36709c21e5097b73d1e3b429a59c72f001d35055866d64ccc2ab36a1", "precision"):
-        dict(traffic=2651.9e6, alg=2580436912),
+    ("f62b783283bb5466dde7e40be8d46d080ad38ae0a71c9bcc1cab68db999bd095", "precision"):
+        dict(traffic=2653.2e6, alg=2580436912),
 }
 
 
