@@ -16,6 +16,7 @@
 
 #include "../../include/dmrg_heff.h"
 #include "handle.h"
+#include "jacobi_rot.cuh"
 
 namespace dmrg {
 
@@ -256,38 +257,6 @@ __global__ void k_diag_set(double* __restrict__ S, int lds, int mmax, const doub
     S[i * lds + j] = (i == j && i < r) ? theta[i] : 0.0;
 }
 
-// Jacobi rotation (c, s) that annihilates apq of the 2 x 2 block [[app, apq], [apq, aqq]],
-// d = aqq - app: t = tan of the angle is the root of smaller magnitude of
-// t^2 + 2 tau t - 1 = 0, tau = d / (2 apq).  Double-precision division and square roots
-// are long dependent chains on this GPU's few FP64 units, so the angle is formed in
-// single precision from d and apq scaled by a power of two (exact), and the pair is then
-// made orthonormal to double precision: with c, s the single-precision cosine and sine,
-// c^2 + s^2 = 1 + delta (|delta| < 2^-20), and c, s are divided by sqrt(1 + delta) =
-// 1 + delta / 2 - delta^2 / 8 + O(delta^3) through the series 1 - delta / 2 +
-// 3 delta^2 / 8 of its reciprocal.  The rotation is exactly orthogonal; the angle's
-// single-precision error leaves |apq| reduced by ~2^-22 of its scale instead of to zero,
-// which the next sweep removes (convergence is judged on the rounding-level threshold).
-__device__ __forceinline__ void rotation(double d, double apq, double* c, double* s) {
-    // scale by 2^-E, E the exponent of the larger magnitude (bit patterns; exact)
-    const long long em = max(__double_as_longlong(d) & 0x7FF0000000000000ll,
-                             __double_as_longlong(apq) & 0x7FF0000000000000ll);
-    const double sc = __longlong_as_double((2046ll << 52) - em);
-    const float df = float(d * sc), af = float(apq * sc);
-    if (!(fabsf(af) > 1e-18f * fabsf(df))) {   // angle below 1e-18: t = apq / d, cos 1 to double
-        *c = 1.0;
-        *s = apq / d;
-        return;
-    }
-    const float tau = df / (2.0f * af);
-    const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
-    const float cf = rsqrtf(fmaf(t, t, 1.0f));
-    const double c0 = cf, s0 = double(t * cf);
-    const double delta = fma(c0, c0, fma(s0, s0, -1.0));
-    const double r = fma(delta, fma(delta, 0.375, -0.5), 1.0);
-    *c = c0 * r;
-    *s = s0 * r;
-}
-
 // Integer key whose order is the order of the finite double x.
 __device__ __forceinline__ long long order_key(double x) {
     const long long b = __double_as_longlong(x);
@@ -370,7 +339,7 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ S, in
                 // only regenerate rounding noise and run sweeps up to the limit
                 if (apq * apq > 1e-30 * fabs(app * aqq) + 1e-300) {
                     double c, s;
-                    rotation(aqq - app, apq, &c, &s);
+                    jacobi_rotation(aqq - app, apq, &c, &s);
                     const int slot = atomicAdd(&s_nr, 1);
                     pp[slot] = p; qq[slot] = q; cs[slot] = c; sn[slot] = s;
                     s_rot = 1;

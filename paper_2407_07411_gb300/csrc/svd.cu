@@ -1,11 +1,12 @@
 // Two-site decomposition and truncation: per left sector of the wave function the matrix
 // M_q = [psi_b ...] of its blocks side by side (rows = dim of the left sector; one block
 // per left sector in U(1), one per coupled right spin in SU(2)), its singular values and
-// left vectors by one-sided (Hestenes) Jacobi in FP64, one CTA per matrix: column pairs
-// in the round-robin order, 8 lanes per pair (fixed-order sums), a sweep without
-// rotation above 1e-15 of the pair's norms ends it.  The columns then hold
+// left vectors by one-sided (Hestenes) Jacobi in FP64, one CTA per matrix (one cluster of
+// 8 CTAs for a matrix above 200 KB): column pairs in the round-robin order, fixed-order
+// sums, a sweep without rotation above 1e-15 of the pair's norms ends it.  The columns then hold
 // sigma_j u_j.  The host keeps the D largest singular values over all matrices and the
 // kernel k_svd_emit writes the kept left vectors.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,12 +17,14 @@
 
 #include "../../include/dmrg_heff.h"
 #include "handle.h"
+#include "jacobi_rot.cuh"
 
 namespace dmrg {
 namespace {
 
 constexpr int SVD_NT = 512;
-constexpr int64_t SVD_SMEM_MAX = 200 * 1024;   // matrices up to this size are rotated in shared memory
+constexpr int64_t SVD_SMEM_MAX = 200 * 1024;   // shared-memory limit of the one-CTA kernel
+constexpr int64_t SVD_CLUSTER_MIN = 64 * 1024;  // matrices above this size go to the cluster kernel
 constexpr int SVD_WARPS = SVD_NT / 32;
 constexpr int SVD_LPP = 8;                               // lanes per column pair
 constexpr int SVD_BATCH = SVD_WARPS * (32 / SVD_LPP);    // pairs in flight (64)
@@ -46,6 +49,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // SMEM: the matrix is rotated in dynamic shared memory (rows * cols doubles) and copied to
 // the scratch A at the end; otherwise it is rotated in A.  The arithmetic is the same.
+// (Larger matrices go to k_svd_cluster below.)
 template <bool SMEM>
 __global__ void __launch_bounds__(SVD_NT) k_svd_jacobi(const double* __restrict__ psi, double* __restrict__ A,
                                                        const SvdJob* __restrict__ jobs,
@@ -120,10 +124,7 @@ __global__ void __launch_bounds__(SVD_NT) k_svd_jacobi(const double* __restrict_
                                 ga += s_part[tid][2][l];
                             }
                             if (ga != 0.0 && ga * ga > 1e-30 * al * be) {
-                                const double zeta = (be - al) / (2.0 * ga);
-                                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                                c = 1.0 / sqrt(1.0 + t * t);
-                                sn = c * t;
+                                jacobi_rotation(be - al, ga, &c, &sn);
                                 s_rot = 1;
                             }
                         }
@@ -169,6 +170,114 @@ __global__ void __launch_bounds__(SVD_NT) k_svd_jacobi(const double* __restrict_
     }
     if (SMEM)   // the emit kernel reads the rotated columns from A
         for (int64_t e = tid; e < int64_t(rows) * cols; e += SVD_NT) A[J.off + e] = s_mat[e];
+}
+
+// Matrices above the shared-memory size: one cluster of SVD_CL CTAs per matrix, the
+// columns in the scratch A (L2-resident; read and written past L1, whose lines are not
+// coherent between SMs), the round's disjoint pairs dealt to the CTAs (pair k to rank
+// k % SVD_CL), one warp per pair: 32-lane dot products summed in a fixed butterfly and
+// broadcast, so every lane forms the same rotation (angle in single precision made
+// exactly orthonormal in double, jacobi_rotation), then applied by the warp.  A cluster
+// barrier ends each round.  Whether a sweep rotated is gathered in flag[2 job + sweep
+// parity] (rank 0 clears the other parity once every CTA has read it, after this
+// sweep's first barrier), and every CTA reads it after the sweep's last barrier, so all
+// CTAs of a cluster leave the sweep loop together.  FP64 issue is this kernel's limit: the cluster divides each
+// round's work by SVD_CL.
+constexpr int SVD_CL = 8;
+__global__ void __launch_bounds__(SVD_NT) k_svd_cluster(const double* __restrict__ psi, double* __restrict__ A,
+                                                        const SvdJob* __restrict__ jobs,
+                                                        const int32_t* __restrict__ bcols, double* __restrict__ raw,
+                                                        double* __restrict__ sv, int32_t* __restrict__ order,
+                                                        int* __restrict__ flag) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int job = blockIdx.x / SVD_CL, rank = int(cluster.block_rank());
+    const SvdJob J = jobs[job];
+    const int rows = J.rows, cols = J.cols, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    double* a = A + J.off;   // column j at a + j * rows
+    {   // the blocks into column-major A, dealt over the cluster's threads
+        int cbase = 0;
+        int64_t boff = J.off;
+        for (int bi = 0; bi < J.nb; ++bi) {
+            const int cb = bcols[J.b0 + bi];
+            for (int64_t e = int64_t(rank) * SVD_NT + tid; e < int64_t(rows) * cb; e += int64_t(SVD_CL) * SVD_NT) {
+                const int r = int(e / cb), c = int(e % cb);
+                __stcg(a + int64_t(cbase + c) * rows + r, psi[boff + e]);
+            }
+            cbase += cb;
+            boff += int64_t(rows) * cb;
+        }
+    }
+    if (rank == 0 && tid == 0) {
+        flag[2 * job] = 0;
+        flag[2 * job + 1] = 0;
+    }
+    __shared__ int s_rot;
+    cluster.sync();
+    const int M = (cols + 1) & ~1, half = M / 2;
+    for (int sweep = 0; sweep < SVD_MAX_SWEEPS && cols >= 2; ++sweep) {
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        for (int r = 0; r < M - 1; ++r) {
+            for (int k = rank + SVD_CL * warp; k < half; k += SVD_CL * SVD_WARPS) {
+                const int x = k == 0 ? 0 : ((k - 1 + r) % (M - 1)) + 1;
+                const int y = ((M - 2 - k + r) % (M - 1)) + 1;
+                const int p = min(x, y), q = max(x, y);
+                if (q >= cols) continue;   // the padding column (warp-uniform)
+                double* ap = a + int64_t(p) * rows;
+                double* aq = a + int64_t(q) * rows;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = lane; i < rows; i += 32) {
+                    const double u = __ldcg(ap + i), w = __ldcg(aq + i);
+                    al += u * u; be += w * w; ga += u * w;
+                }
+                al = warp_sum(al);
+                be = warp_sum(be);
+                ga = warp_sum(ga);
+                if (ga != 0.0 && ga * ga > 1e-30 * al * be) {
+                    double c, sn;
+                    jacobi_rotation(be - al, ga, &c, &sn);
+                    if (lane == 0) s_rot = 1;
+                    for (int i = lane; i < rows; i += 32) {
+                        const double u = __ldcg(ap + i), w = __ldcg(aq + i);
+                        __stcg(ap + i, c * u - sn * w);
+                        __stcg(aq + i, sn * u + c * w);
+                    }
+                }
+            }
+            cluster.sync();   // the next round's pairs read these columns
+        }
+        // the other parity was read at the end of the previous sweep, before this sweep's
+        // first barrier; it is written again only after the barrier below
+        if (rank == 0 && tid == 0) flag[2 * job + ((sweep + 1) & 1)] = 0;
+        __syncthreads();
+        if (tid == 0 && s_rot) atomicOr(flag + 2 * job + (sweep & 1), 1);
+        cluster.sync();
+        if (__ldcg(flag + 2 * job + (sweep & 1)) == 0) break;   // the same value in every CTA
+    }
+    if (rank != 0) return;
+    // column norms (sigma_j, any order), then ranks: descending, ties to the lower index
+    for (int j = warp; j < cols; j += SVD_WARPS) {
+        const double* aj = a + int64_t(j) * rows;
+        double s = 0.0;
+        for (int i = lane; i < rows; i += 32) {
+            const double v = __ldcg(aj + i);
+            s += v * v;
+        }
+        s = warp_sum(s);
+        if (lane == 0) raw[J.sv_off + j] = sqrt(s);
+    }
+    __syncthreads();
+    for (int j = tid; j < cols; j += SVD_NT) {
+        const double sj = raw[J.sv_off + j];
+        int rank_j = 0;
+        for (int k = 0; k < cols; ++k) {
+            const double sk = raw[J.sv_off + k];
+            rank_j += (sk > sj || (sk == sj && k < j)) ? 1 : 0;
+        }
+        sv[J.sv_off + rank_j] = sj;
+        order[J.sv_off + rank_j] = j;
+    }
 }
 
 // U_q (rows x kept_q, row-major at u_off[q]) = kept columns / their singular values
@@ -267,18 +376,22 @@ extern "C" int dmrg_svd_truncate(dmrg_heff_t hh, const double* psi, int32_t D, d
     if (e == cudaSuccess) e = cudaMemcpy(d_jobs, jobs.data(), sizeof(SvdJob) * size_t(nb), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(d_bcols, bcols.data(), sizeof(int32_t) * bcols.size(), cudaMemcpyHostToDevice);
-    // matrices that fit in shared memory first, then the others (rotated in A)
+    // matrices up to SVD_CLUSTER_MIN on one CTA each (rotated in shared memory), the
+    // larger ones on a cluster each, the two launches side by side on two streams
     std::vector<SvdJob> small, large;
     int64_t smem = 0;
     for (const SvdJob& J : jobs) {
         const int64_t bytes = int64_t(J.rows) * J.cols * int64_t(sizeof(double));
-        if (bytes <= SVD_SMEM_MAX) {
+        if (bytes <= SVD_CLUSTER_MIN) {
             small.push_back(J);
             smem = std::max(smem, bytes);
         } else {
             large.push_back(J);
         }
     }
+    static_assert(SVD_CLUSTER_MIN <= SVD_SMEM_MAX, "one-CTA matrices must fit in shared memory");
+    cudaStream_t side = nullptr;
+    if (e == cudaSuccess && !large.empty()) e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
     SvdJob *d_small = nullptr, *d_large = nullptr;
     if (e == cudaSuccess && !small.empty()) e = al(reinterpret_cast<void**>(&d_small), sizeof(SvdJob) * small.size());
     if (e == cudaSuccess && !large.empty()) e = al(reinterpret_cast<void**>(&d_large), sizeof(SvdJob) * large.size());
@@ -286,15 +399,39 @@ extern "C" int dmrg_svd_truncate(dmrg_heff_t hh, const double* psi, int32_t D, d
         e = cudaMemcpy(d_small, small.data(), sizeof(SvdJob) * small.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !large.empty())
         e = cudaMemcpy(d_large, large.data(), sizeof(SvdJob) * large.size(), cudaMemcpyHostToDevice);
+    int* d_flag = nullptr;
+    if (e == cudaSuccess && !large.empty()) e = al(reinterpret_cast<void**>(&d_flag), sizeof(int) * 2 * large.size());
+    // the side stream does not order itself after the default stream: the copies above
+    // (and the caller's work on psi) finish before either kernel starts
+    if (e == cudaSuccess && side) e = cudaDeviceSynchronize();
     if (e == cudaSuccess && !small.empty())
         e = cudaFuncSetAttribute(k_svd_jacobi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e == cudaSuccess && !small.empty()) {
         k_svd_jacobi<true><<<unsigned(small.size()), SVD_NT, size_t(smem)>>>(psi, A, d_small, d_bcols, raw, sv, order);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess && !large.empty()) {
-        k_svd_jacobi<false><<<unsigned(large.size()), SVD_NT>>>(psi, A, d_large, d_bcols, raw, sv, order);
-        e = cudaGetLastError();
+    if (e == cudaSuccess && !large.empty()) {   // one cluster of SVD_CL CTAs per large matrix
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(unsigned(large.size() * SVD_CL));
+        cfg.blockDim = dim3(SVD_NT);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = side;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = SVD_CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, k_svd_cluster, static_cast<const double*>(psi), A,
+                               static_cast<const SvdJob*>(d_large), static_cast<const int32_t*>(d_bcols), raw, sv,
+                               order, d_flag);
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    if (side) {
+        const cudaError_t es = cudaStreamSynchronize(side);
+        if (e == cudaSuccess) e = es;
+        cudaStreamDestroy(side);
     }
     std::vector<double> hsv(static_cast<size_t>(nsv));
     if (e == cudaSuccess) e = cudaMemcpy(hsv.data(), sv, sizeof(double) * size_t(nsv), cudaMemcpyDeviceToHost);
