@@ -322,6 +322,14 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ S, in
     const int half = M / 2;
     __shared__ int s_rot;
     for (int sweep = 0; sweep < 40 && M >= 2; ++sweep) {
+        // converged when no pair passes the rotation test (the sweep would rotate nothing):
+        // one pass over the matrix instead of a sweep of rounds
+        int any = 0;
+        for (int e = tid; e < M * M; e += nt) {
+            const int i = e / M, j = e % M;
+            if (i < j && jacobi_rotate_needed(A[i * ld + j], A[i * ld + i], A[j * ld + j])) any = 1;
+        }
+        if (!__syncthreads_or(any)) break;
         if (tid == 0) s_rot = 0;
         __syncthreads();
         for (int r = 0; r < M - 1; ++r) {
@@ -333,11 +341,8 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ S, in
                 const int b = ((M - 2 - k + r) % (M - 1)) + 1;
                 const int p = min(a, b), q = max(a, b);
                 const double apq = A[p * ld + q], app = A[p * ld + p], aqq = A[q * ld + q];
-                // rotate only while the off-diagonal entry is above rounding level,
-                // |apq| > 1e-15 sqrt|app aqq| (compared in squares): a smaller one moves
-                // the eigenvalues by < 1e-30 relative, and rotations below rounding level
-                // only regenerate rounding noise and run sweeps up to the limit
-                if (apq * apq > 1e-30 * fabs(app * aqq) + 1e-300) {
+                // rotate only while the off-diagonal entry is above rounding level
+                if (jacobi_rotate_needed(apq, app, aqq)) {
                     double c, s;
                     jacobi_rotation(aqq - app, apq, &c, &s);
                     const int slot = atomicAdd(&s_nr, 1);

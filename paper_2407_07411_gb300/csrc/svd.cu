@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(SVD_NT) k_svd_jacobi(const double* __restrict_
                                 be += s_part[tid][1][l];
                                 ga += s_part[tid][2][l];
                             }
-                            if (ga != 0.0 && ga * ga > 1e-30 * al * be) {
+                            if (jacobi_rotate_needed(ga, al, be)) {
                                 jacobi_rotation(be - al, ga, &c, &sn);
                                 s_rot = 1;
                             }
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(SVD_NT) k_svd_cluster(const double* __restrict
                 al = warp_sum(al);
                 be = warp_sum(be);
                 ga = warp_sum(ga);
-                if (ga != 0.0 && ga * ga > 1e-30 * al * be) {
+                if (jacobi_rotate_needed(ga, al, be)) {
                     double c, sn;
                     jacobi_rotation(be - al, ga, &c, &sn);
                     if (lane == 0) s_rot = 1;
