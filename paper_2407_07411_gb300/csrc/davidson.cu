@@ -22,7 +22,7 @@ namespace dmrg {
 
 // Dot products are cut into chunks of at least DOT_MIN_CHUNK elements, about two per SM
 // (FP64 arithmetic is scarce on this GPU, so every SM takes a share); partials are
-// summed in chunk order.
+// summed in a fixed order.
 constexpr int DOT_MIN_CHUNK = 1024;
 constexpr int DOT_NT = 256;
 constexpr int MAXQ = 8;          // Q vectors per multi-dot launch
@@ -45,48 +45,65 @@ struct DavidsonState {
 
 namespace {
 
+// Sum over the warp in a fixed shuffle tree (the result in lane 0).  FP64 additions are
+// long-latency operations on this GPU: reductions use shuffle trees over many lanes
+// instead of long chains in one thread.
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Sum over the CTA of DOT_NT threads (fixed order: warp trees, then the warps' sums in
+// warp order); the result in thread 0.  red holds DOT_NT / 32 doubles.
+__device__ __forceinline__ double cta_sum(double x, double* red) {
+    x = warp_sum(x);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < DOT_NT / 32; ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
 // out[i*nq + j] = P_i . Q_j: partial[(c*np + i)*nq + j] = sum over chunk c (fixed-order
 // tree), then the CTA that finishes last (a counter, reset by that CTA for the next
-// launch) adds the chunks' partials in chunk order, so the result does not depend on
-// which CTA runs when.  With gridDim.z = 2 the same is done for out2 = P2 . Q2 (CTAs of
+// launch) adds the chunks' partials in a fixed order (a warp per output), so the result
+// does not depend on which CTA runs when.  With gridDim.z = 2 the same is done for out2 = P2 . Q2 (CTAs of
 // z = 1), and with S given the last CTA also writes the symmetric Rayleigh-Ritz entries
 // S[i][m0 + j] = S[m0 + j][i] = (out[i*nq + j] + out2[i*nq + j]) / 2.
+// nq is a template parameter: an FP64 instruction whose predicate is off still holds the
+// FP64 pipe on this GPU, so the loops over the Q vectors have exactly nq iterations.
+template <int nq>
 __global__ void __launch_bounds__(DOT_NT) k_multidot(const double* __restrict__ P, int64_t ldp, int np,
-                                                     const double* __restrict__ Q, int64_t ldq, int nq,
+                                                     const double* __restrict__ Q, int64_t ldq,
                                                      int64_t dim, int64_t chunk, double* __restrict__ partial,
                                                      double* __restrict__ out, unsigned* __restrict__ done,
                                                      const double* __restrict__ P2, const double* __restrict__ Q2,
                                                      double* __restrict__ out2, double* __restrict__ S, int lds,
                                                      int m0) {
-    __shared__ double red[DOT_NT];
+    __shared__ double red[DOT_NT / 32];
     __shared__ bool last;
     const int c = blockIdx.x, i = blockIdx.y, z = blockIdx.z;
     const int npq = np * nq;
     const int64_t n0 = int64_t(c) * chunk;
     const int64_t n1 = min(dim, n0 + chunk);
-    double acc[MAXQ];
+    double acc[nq];
 #pragma unroll
-    for (int j = 0; j < MAXQ; ++j) acc[j] = 0.0;
+    for (int j = 0; j < nq; ++j) acc[j] = 0.0;
     const double* p = (z ? P2 : P) + i * ldp;
     const double* Qz = z ? Q2 : Q;
     for (int64_t n = n0 + threadIdx.x; n < n1; n += DOT_NT) {
         const double pv = p[n];
 #pragma unroll
-        for (int j = 0; j < MAXQ; ++j)
-            if (j < nq) acc[j] += pv * Qz[j * ldq + n];
+        for (int j = 0; j < nq; ++j) acc[j] += pv * Qz[j * ldq + n];
     }
     double* part = partial + int64_t(z) * gridDim.x * npq;
 #pragma unroll
-    for (int j = 0; j < MAXQ; ++j) {
-        if (j >= nq) break;
-        red[threadIdx.x] = acc[j];
-        __syncthreads();
-        for (int s = DOT_NT / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) part[(int64_t(c) * np + i) * nq + j] = red[0];
-        __syncthreads();
+    for (int j = 0; j < nq; ++j) {
+        const double t = cta_sum(acc[j], red);
+        if (threadIdx.x == 0) part[(int64_t(c) * np + i) * nq + j] = t;
     }
     if (threadIdx.x == 0) {
         __threadfence();   // this CTA's partials before its count
@@ -95,19 +112,27 @@ __global__ void __launch_bounds__(DOT_NT) k_multidot(const double* __restrict__ 
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int e = threadIdx.x; e < npq; e += DOT_NT) {
+    // warp per output: lane l adds chunks l, l + 32, ... in order, then the warp tree
+    const int lane = threadIdx.x & 31;
+    for (int e = threadIdx.x >> 5; e < npq; e += DOT_NT / 32) {
         double s1 = 0.0, s2 = 0.0;
-        for (int64_t cc = 0; cc < gridDim.x; ++cc) s1 += __ldcg(partial + cc * npq + e);
-        out[e] = s1;
+        for (int64_t cc = lane; cc < gridDim.x; cc += 32) s1 += __ldcg(partial + cc * npq + e);
+        s1 = warp_sum(s1);
         if (gridDim.z > 1) {
             const double* part2 = partial + int64_t(gridDim.x) * npq;
-            for (int64_t cc = 0; cc < gridDim.x; ++cc) s2 += __ldcg(part2 + cc * npq + e);
-            out2[e] = s2;
-            if (S) {
-                const int ii = e / nq, jj = e - ii * nq;
-                const double v = 0.5 * (s1 + s2);
-                S[ii * lds + m0 + jj] = v;
-                S[(m0 + jj) * lds + ii] = v;
+            for (int64_t cc = lane; cc < gridDim.x; cc += 32) s2 += __ldcg(part2 + cc * npq + e);
+            s2 = warp_sum(s2);
+        }
+        if (lane == 0) {
+            out[e] = s1;
+            if (gridDim.z > 1) {
+                out2[e] = s2;
+                if (S) {
+                    const int ii = e / nq, jj = e - ii * nq;
+                    const double v = 0.5 * (s1 + s2);
+                    S[ii * lds + m0 + jj] = v;
+                    S[(m0 + jj) * lds + ii] = v;
+                }
             }
         }
     }
@@ -116,53 +141,47 @@ __global__ void __launch_bounds__(DOT_NT) k_multidot(const double* __restrict__ 
 
 // Ritz vectors and residuals of the lowest kb pairs in one pass over the vectors:
 // X_j = sum_{i<m} U[i][j] V_i, R_j = sum_{i<m} U[i][j] W_i - theta_j X_j (the sums in
-// the order of i), and |R_j|^2: per-CTA tree sums in partial, added in CTA order by the
-// CTA that finishes last, which also copies theta[0:m] next to them.
-__global__ void __launch_bounds__(DOT_NT) k_ritz(const double* __restrict__ U, int ldu, int kb, int m,
+// the order of i), and |R_j|^2: per-CTA tree sums in partial, added in a fixed order by the
+// CTA that finishes last, which also copies theta_all[0:m] next to them.  kb (at most
+// MAXQ pairs per launch; U, theta, X, R and norms point at the launch's first pair) is a
+// template parameter (exact loop counts, as for k_multidot).
+template <int kb>
+__global__ void __launch_bounds__(DOT_NT) k_ritz(const double* __restrict__ U, int ldu, int m,
                                                  const double* __restrict__ V, const double* __restrict__ W,
                                                  int64_t dim, double* __restrict__ X, double* __restrict__ R,
                                                  const double* __restrict__ theta, double* __restrict__ norms,
-                                                 double* __restrict__ theta_out, double* __restrict__ partial,
-                                                 unsigned* __restrict__ done) {
-    __shared__ double red[DOT_NT];
+                                                 const double* __restrict__ theta_all, double* __restrict__ theta_out,
+                                                 double* __restrict__ partial, unsigned* __restrict__ done) {
+    __shared__ double red[DOT_NT / 32];
     __shared__ bool last;
-    double sq[MAXQ];
+    double sq[kb];
 #pragma unroll
-    for (int j = 0; j < MAXQ; ++j) sq[j] = 0.0;
+    for (int j = 0; j < kb; ++j) sq[j] = 0.0;
     for (int64_t n = int64_t(blockIdx.x) * DOT_NT + threadIdx.x; n < dim; n += int64_t(gridDim.x) * DOT_NT) {
-        double ax[MAXQ], aw[MAXQ];
+        double ax[kb], aw[kb];
 #pragma unroll
-        for (int j = 0; j < MAXQ; ++j) ax[j] = aw[j] = 0.0;
+        for (int j = 0; j < kb; ++j) ax[j] = aw[j] = 0.0;
         for (int i = 0; i < m; ++i) {
             const double v = V[i * dim + n], w = W[i * dim + n];
 #pragma unroll
-            for (int j = 0; j < MAXQ; ++j)
-                if (j < kb) {
-                    const double u = U[i * ldu + j];
-                    ax[j] += u * v;
-                    aw[j] += u * w;
-                }
+            for (int j = 0; j < kb; ++j) {
+                const double u = U[i * ldu + j];
+                ax[j] += u * v;
+                aw[j] += u * w;
+            }
         }
 #pragma unroll
-        for (int j = 0; j < MAXQ; ++j)
-            if (j < kb) {
-                const double r = aw[j] - theta[j] * ax[j];
-                X[j * dim + n] = ax[j];
-                R[j * dim + n] = r;
-                sq[j] += r * r;
-            }
+        for (int j = 0; j < kb; ++j) {
+            const double r = aw[j] - theta[j] * ax[j];
+            X[j * dim + n] = ax[j];
+            R[j * dim + n] = r;
+            sq[j] += r * r;
+        }
     }
 #pragma unroll
-    for (int j = 0; j < MAXQ; ++j) {
-        if (j >= kb) break;
-        red[threadIdx.x] = sq[j];
-        __syncthreads();
-        for (int s = DOT_NT / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) partial[int64_t(blockIdx.x) * kb + j] = red[0];
-        __syncthreads();
+    for (int j = 0; j < kb; ++j) {
+        const double t = cta_sum(sq[j], red);
+        if (threadIdx.x == 0) partial[int64_t(blockIdx.x) * kb + j] = t;
     }
     if (threadIdx.x == 0) {
         __threadfence();
@@ -171,37 +190,54 @@ __global__ void __launch_bounds__(DOT_NT) k_ritz(const double* __restrict__ U, i
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int j = threadIdx.x; j < kb; j += DOT_NT) {
+    const int lane = threadIdx.x & 31;
+    for (int j = threadIdx.x >> 5; j < kb; j += DOT_NT / 32) {   // warp per pair, as in k_multidot
         double s = 0.0;
-        for (int64_t cc = 0; cc < gridDim.x; ++cc) s += __ldcg(partial + cc * kb + j);
-        norms[j] = s;
+        for (int64_t cc = lane; cc < gridDim.x; cc += 32) s += __ldcg(partial + cc * kb + j);
+        s = warp_sum(s);
+        if (lane == 0) norms[j] = s;
     }
-    for (int j = threadIdx.x; j < m; j += DOT_NT) theta_out[j] = theta[j];
+    for (int j = threadIdx.x; j < m; j += DOT_NT) theta_out[j] = theta_all[j];
     if (threadIdx.x == 0) *done = 0u;
 }
 
 // out_j = sum_{i<m} coef[i*ldc + col0 + j] * V_i  (j < nj <= MAXQ); sub: out_j -= ...
-__global__ void k_lincomb(const double* __restrict__ coef, int ldc, int col0, int nj, int m,
+// (nj a template parameter, as for k_multidot)
+template <int nj>
+__global__ void k_lincomb(const double* __restrict__ coef, int ldc, int col0, int m,
                           const double* __restrict__ V, int64_t ldv, int64_t dim, double* __restrict__ out,
                           int64_t ldo, int sub) {
     const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (n >= dim) return;
-    double acc[MAXQ];
+    double acc[nj];
 #pragma unroll
-    for (int j = 0; j < MAXQ; ++j) acc[j] = 0.0;
+    for (int j = 0; j < nj; ++j) acc[j] = 0.0;
     for (int i = 0; i < m; ++i) {
         const double v = V[i * ldv + n];
 #pragma unroll
-        for (int j = 0; j < MAXQ; ++j)
-            if (j < nj) acc[j] += coef[i * ldc + col0 + j] * v;
+        for (int j = 0; j < nj; ++j) acc[j] += coef[i * ldc + col0 + j] * v;
     }
 #pragma unroll
-    for (int j = 0; j < MAXQ; ++j)
-        if (j < nj) {
-            if (sub) out[j * ldo + n] -= acc[j];
-            else out[j * ldo + n] = acc[j];
-        }
+    for (int j = 0; j < nj; ++j) {
+        if (sub) out[j * ldo + n] -= acc[j];
+        else out[j * ldo + n] = acc[j];
+    }
 }
+
+// Launch of a kernel templated on a vector count 1..MAXQ: LAUNCH(N) is expanded with the
+// count as a compile-time constant.
+#define DMRG_DISPATCH_COUNT(n, LAUNCH) \
+    switch (n) {                      \
+        case 1: LAUNCH(1); break;     \
+        case 2: LAUNCH(2); break;     \
+        case 3: LAUNCH(3); break;     \
+        case 4: LAUNCH(4); break;     \
+        case 5: LAUNCH(5); break;     \
+        case 6: LAUNCH(6); break;     \
+        case 7: LAUNCH(7); break;     \
+        case 8: LAUNCH(8); break;     \
+        default: break;               \
+    }
 
 // out = r / (diag - theta[j]) with the denominator floor
 __global__ void k_precond(double* __restrict__ out, const double* __restrict__ r, const double* __restrict__ diag,
@@ -426,15 +462,20 @@ struct Run {
     // out[i*nq + j] = P_i . Q_j  (np <= MAX_BASIS, nq <= MAXQ); result in s->small
     int dots(const double* P, int np, const double* Q, int nq, double* out) {
         if (np == 0 || nq == 0) return DMRG_OK;
-        k_multidot<<<dim3(unsigned(s->n_chunks), unsigned(np)), DOT_NT, 0, st>>>(
-            P, dim, np, Q, dim, nq, dim, s->chunk, s->partial, out, s->done, nullptr, nullptr, nullptr, nullptr, 0, 0);
+#define DMRG_DOTS(N)                                                                                      \
+    k_multidot<N><<<dim3(unsigned(s->n_chunks), unsigned(np)), DOT_NT, 0, st>>>(                          \
+        P, dim, np, Q, dim, dim, s->chunk, s->partial, out, s->done, nullptr, nullptr, nullptr, nullptr, 0, 0)
+        DMRG_DISPATCH_COUNT(nq, DMRG_DOTS)
+#undef DMRG_DOTS
         return check(cudaGetLastError(), "dot kernel");
     }
     int lincomb(const double* coef, int ldc, int col0, int nj, int m, const double* V, double* out, int sub) {
         for (int j0 = 0; j0 < nj; j0 += MAXQ) {
             const int n = nj - j0 < MAXQ ? nj - j0 : MAXQ;
-            k_lincomb<<<blocks_for(dim), 256, 0, st>>>(coef, ldc, col0 + j0, n, m, V, dim, dim, out + j0 * dim, dim,
-                                                       sub);
+#define DMRG_LINCOMB(N)                                                                                   \
+    k_lincomb<N><<<blocks_for(dim), 256, 0, st>>>(coef, ldc, col0 + j0, m, V, dim, dim, out + j0 * dim, dim, sub)
+            DMRG_DISPATCH_COUNT(n, DMRG_LINCOMB)
+#undef DMRG_LINCOMB
         }
         return check(cudaGetLastError(), "lincomb");
     }
@@ -453,7 +494,7 @@ struct Run {
                 const int ni = *m - i0 < MAX_BASIS ? *m - i0 : MAX_BASIS;
                 if ((rc = dots(s->V + i0 * dim, ni, v, 1, d + i0))) return rc;
             }
-            k_lincomb<<<blocks_for(dim), 256, 0, st>>>(d, 1, 0, 1, *m, s->V, dim, dim, v, dim, 1);
+            k_lincomb<1><<<blocks_for(dim), 256, 0, st>>>(d, 1, 0, *m, s->V, dim, dim, v, dim, 1);
             if ((rc = check(cudaGetLastError(), "cgs update"))) return rc;
         }
         if ((rc = dots(v, 1, v, 1, nrm + 1))) return rc;
@@ -475,9 +516,12 @@ struct Run {
         double* g2 = g1 + MAX_BASIS * MAXQ;
         for (int j0 = 0; j0 < nb; j0 += MAXQ) {
             const int nq = nb - j0 < MAXQ ? nb - j0 : MAXQ;
-            k_multidot<<<dim3(unsigned(s->n_chunks), unsigned(m), 2u), DOT_NT, 0, st>>>(
-                s->V, dim, m, s->W + int64_t(m0 + j0) * dim, dim, nq, dim, s->chunk, s->partial, g1, s->done, s->W,
-                s->V + int64_t(m0 + j0) * dim, g2, s->S, mmax, m0 + j0);
+#define DMRG_SUPD(N)                                                                                          \
+    k_multidot<N><<<dim3(unsigned(s->n_chunks), unsigned(m), 2u), DOT_NT, 0, st>>>(                           \
+        s->V, dim, m, s->W + int64_t(m0 + j0) * dim, dim, dim, s->chunk, s->partial, g1, s->done, s->W,        \
+        s->V + int64_t(m0 + j0) * dim, g2, s->S, mmax, m0 + j0)
+            DMRG_DISPATCH_COUNT(nq, DMRG_SUPD)
+#undef DMRG_SUPD
             int rc;
             if ((rc = check(cudaGetLastError(), "S update"))) return rc;
         }
@@ -487,8 +531,15 @@ struct Run {
     // them (small[2048 + MAX_BASIS + j]), one launch
     int ritz(int kb, int m) {
         const int64_t grid = std::min<int64_t>((dim + DOT_NT - 1) / DOT_NT, s->n_chunks * MAX_BASIS);
-        k_ritz<<<unsigned(grid), DOT_NT, 0, st>>>(s->U, mmax, kb, m, s->V, s->W, dim, s->X, s->R, s->theta,
-                                                   s->small + 2048, s->small + 2048 + MAX_BASIS, s->partial, s->done);
+        for (int j0 = 0; j0 < kb; j0 += MAXQ) {   // MAXQ pairs per launch
+            const int n = kb - j0 < MAXQ ? kb - j0 : MAXQ;
+#define DMRG_RITZ(N)                                                                                       \
+    k_ritz<N><<<unsigned(grid), DOT_NT, 0, st>>>(s->U + j0, mmax, m, s->V, s->W, dim, s->X + j0 * dim,       \
+                                                 s->R + j0 * dim, s->theta + j0, s->small + 2048 + j0, s->theta, \
+                                                 s->small + 2048 + MAX_BASIS, s->partial, s->done)
+            DMRG_DISPATCH_COUNT(n, DMRG_RITZ)
+#undef DMRG_RITZ
+        }
         return check(cudaGetLastError(), "ritz vectors");
     }
 };

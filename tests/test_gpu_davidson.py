@@ -31,7 +31,7 @@ def test_tiny_lowest(tiny_problem, tiny_dense):
     assert np.linalg.norm(r) <= 1e-8 and abs(np.linalg.norm(X[0]) - 1) < 1e-12
 
 
-@pytest.mark.parametrize("k_eig,block", [(3, 1), (3, 4), (1, 8)])
+@pytest.mark.parametrize("k_eig,block", [(3, 1), (3, 4), (1, 8), (10, 1)])
 def test_tiny_block(tiny_problem, tiny_dense, k_eig, block):
     w = np.linalg.eigvalsh(tiny_dense)
     ev, info, X = gpu_davidson(tiny_problem, k_eig=k_eig, block=block)
