@@ -314,9 +314,11 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ S, in
     const int ld = MAX_BASIS + 1;
     double* A = sm;                      // M x ld
     double* Z = sm + MAX_BASIS * ld;     // eigenvectors, M x ld
-    __shared__ double cs[MAX_BASIS / 2], sn[MAX_BASIS / 2];
-    __shared__ int pp[MAX_BASIS / 2], qq[MAX_BASIS / 2];
-    __shared__ int s_nr;   // rotations of the current round (compacted into pp, qq, cs, sn)
+    // rotations of a round (compacted), in two sets: the eigenvector update Z <- Z J of a
+    // round runs during the next round's angle computation, which occupies one warp
+    __shared__ double cs[2][MAX_BASIS / 2], sn[2][MAX_BASIS / 2];
+    __shared__ int pp[2][MAX_BASIS / 2], qq[2][MAX_BASIS / 2];
+    __shared__ int s_nr[2];
     __shared__ int order[MAX_BASIS];
     const int tid = threadIdx.x, nt = blockDim.x;
     // Z = B;  A = S B (into A), then A = B^T A
@@ -355,8 +357,23 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ S, in
         A[i * ld + j] = bt[nb++];
     }
     __syncthreads();
-    const int half = M / 2;
+    const int half = M / 2;   // <= 32: the angles of a round are computed by warp 0
     __shared__ int s_rot;
+    // Z <- Z J for the n rotations of set b, by threads t0, t0 + step, ...
+    auto z_update = [&](int b, int n, int t0, int step) {
+        for (int e = t0; e < n * M; e += step) {
+            const int k = e / M, row = e % M;
+            const int p = pp[b][k], q = qq[b][k];
+            const double c = cs[b][k], s = sn[b][k];
+            const double u = Z[row * ld + p], w = Z[row * ld + q];
+            Z[row * ld + p] = c * u - s * w;
+            Z[row * ld + q] = s * u + c * w;
+        }
+    };
+    if (tid == 0) s_nr[0] = s_nr[1] = 0;
+    int cur = 0;              // set of this round's rotations
+    int pend = 0, pend_n = 0; // set and count of the rotations not yet applied to Z
+    __syncthreads();
     for (int sweep = 0; sweep < 40 && M >= 2; ++sweep) {
         // converged when no pair passes the rotation test (the sweep would rotate nothing):
         // one pass over the matrix instead of a sweep of rounds
@@ -369,8 +386,7 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ S, in
         if (tid == 0) s_rot = 0;
         __syncthreads();
         for (int r = 0; r < M - 1; ++r) {
-            if (tid == 0) s_nr = 0;
-            __syncthreads();
+            // s_nr[cur] is zero here
             if (tid < half) {
                 const int k = tid;
                 const int a = k == 0 ? 0 : ((k - 1 + r) % (M - 1)) + 1;
@@ -381,45 +397,50 @@ __global__ void __launch_bounds__(256) k_jacobi(const double* __restrict__ S, in
                 if (jacobi_rotate_needed(apq, app, aqq)) {
                     double c, s;
                     jacobi_rotation(aqq - app, apq, &c, &s);
-                    const int slot = atomicAdd(&s_nr, 1);
-                    pp[slot] = p; qq[slot] = q; cs[slot] = c; sn[slot] = s;
+                    const int slot = atomicAdd(&s_nr[cur], 1);
+                    pp[cur][slot] = p; qq[cur][slot] = q; cs[cur][slot] = c; sn[cur][slot] = s;
                     s_rot = 1;
                 }
+            } else if (tid >= 32) {
+                z_update(pend, pend_n, tid - 32, nt - 32);   // the previous round's rotations
             }
             __syncthreads();
             // the disjoint rotations of this round, in any order; every thread reads the
-            // same count (no write to s_nr before the next barrier), and that barrier -- the
-            // first of the update loops, or the one below -- comes before the next reset
-            const int nr = s_nr;
+            // same count.  The other set's Z update has finished: its count is cleared for
+            // the next round (no thread reads it before the next barrier)
+            const int nr = s_nr[cur];
+            pend = cur;
+            pend_n = nr;
+            if (tid == 0) s_nr[cur ^ 1] = 0;
+            cur ^= 1;
             if (nr == 0) {
                 __syncthreads();
                 continue;
             }
             for (int e = tid; e < nr * M; e += nt) {       // A <- A J
                 const int k = e / M, row = e % M;
-                const int p = pp[k], q = qq[k];
-                const double c = cs[k], s = sn[k];
+                const int p = pp[pend][k], q = qq[pend][k];
+                const double c = cs[pend][k], s = sn[pend][k];
                 const double x = A[row * ld + p], y = A[row * ld + q];
                 A[row * ld + p] = c * x - s * y;
                 A[row * ld + q] = s * x + c * y;
             }
             __syncthreads();
-            for (int e = tid; e < nr * M; e += nt) {       // A <- J^T A, Z <- Z J
+            for (int e = tid; e < nr * M; e += nt) {       // A <- J^T A
                 const int k = e / M, col = e % M;
-                const int p = pp[k], q = qq[k];
-                const double c = cs[k], s = sn[k];
+                const int p = pp[pend][k], q = qq[pend][k];
+                const double c = cs[pend][k], s = sn[pend][k];
                 const double x = A[p * ld + col], y = A[q * ld + col];
                 A[p * ld + col] = c * x - s * y;
                 A[q * ld + col] = s * x + c * y;
-                const double u = Z[col * ld + p], w = Z[col * ld + q];
-                Z[col * ld + p] = c * u - s * w;
-                Z[col * ld + q] = s * u + c * w;
             }
             __syncthreads();
         }
         if (s_rot == 0) break;   // a sweep without rotations: converged to rounding level
         __syncthreads();
     }
+    z_update(pend, pend_n, tid, nt);   // the last round's rotations
+    __syncthreads();
     // ascending order of the m real eigenvalues (ties by index): the rank of eigenvalue
     // i is the count of those before it, compared as integers (order-preserving keys)
     for (int i = tid; i < m; i += nt) {
