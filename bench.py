@@ -44,15 +44,15 @@ SPLIT_ARITH = ("FP64-equivalent: every FP64 operand cut into 6 BF16 digit slices
 # same workload (fewer terms) is scaled to a full launch by the ratio of algorithmic
 # bytes.  A changed kernel, or a workload without a capture, reports null.
 NCU_TRAFFIC = {
-    # k_fp64_tiles, mid workload: (280.8 + 358.1) / 2 MB per launch (profiles/fp64_tiles_mid.md)
-    ("7ea6b95187a63352e09b039a09918be5e89d2a14561ebf2f4d93d0eae118ec22", "mid"): dict(traffic=319.5e6),
-    # k_umma, mid workload: (470.5 + 538.5 + 467.5 + 538.4) / 4 MB per launch
+    # k_umma, mid workload: (507.8 + 594.0 + 507.5 + 594.4) / 4 MB per launch
     # (profiles/split_umma_mid.md)
-    ("1d4e0711bb97b9a9e36d9a142b4bae3ef00a40cd9656b8dffcb7a602e566ed1e", "mid"): dict(traffic=503.7e6),
-    # spin-adapted su2_mid (profiles/su2_mid.md): k_umma (1199.5 + 1215.7 + 1195.8 +
-    # 1216.0) / 4 MB, k_fp64_tiles (708.0 + 998.8) / 2 MB per launch
-    ("1d4e0711bb97b9a9e36d9a142b4bae3ef00a40cd9656b8dffcb7a602e566ed1e", "su2_mid"): dict(traffic=1206.8e6),
-    ("7ea6b95187a63352e09b039a09918be5e89d2a14561ebf2f4d93d0eae118ec22", "su2_mid"): dict(traffic=853.4e6),
+    ("f62b783283bb5466dde7e40be8d46d080ad38ae0a71c9bcc1cab68db999bd095", "mid"): dict(traffic=550.9e6),
+    # k_fp64_tiles, mid workload: (280.7 + 363.6) / 2 MB per launch (profiles/fp64_tiles_mid.md)
+    ("650a109e74edab18a3dc989256a122e4e1942d7c6ca9fc79c7845bd665ff2377", "mid"): dict(traffic=322.2e6),
+    # spin-adapted su2_mid (profiles/su2_mid.md): k_umma (1339.9 + 1309.7 + 1336.5 +
+    # 1309.7) / 4 MB, k_fp64_tiles (708.3 + 992.7) / 2 MB per launch
+    ("f62b783283bb5466dde7e40be8d46d080ad38ae0a71c9bcc1cab68db999bd095", "su2_mid"): dict(traffic=1323.9e6),
+    ("650a109e74edab18a3dc989256a122e4e1942d7c6ca9fc79c7845bd665ff2377", "su2_mid"): dict(traffic=850.5e6),
     # k_umma, precision workload, captured on its first 200 terms: (2651.0 + 2655.3) / 2 MB
     # per launch against 2580.4 MB of algorithmic bytes per launch (profiles/split_umma_precision.md)
     ("f62b783283bb5466dde7e40be8d46d080ad38ae0a71c9bcc1cab68db999bd095", "precision"):
