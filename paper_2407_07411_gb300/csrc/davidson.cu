@@ -21,9 +21,10 @@
 namespace dmrg {
 
 // Dot products are cut into chunks of at least DOT_MIN_CHUNK elements, about two per SM
-// (FP64 arithmetic is scarce on this GPU, so every SM takes a share); partials are
-// summed in a fixed order.
-constexpr int DOT_MIN_CHUNK = 1024;
+// on large vectors (FP64 arithmetic is scarce on this GPU, so every SM takes a share);
+// a chunk gives each thread at least 16 elements, so that a CTA's reduction (FP64 work
+// too) stays small against its products.  Partials are summed in a fixed order.
+constexpr int DOT_MIN_CHUNK = 4096;
 constexpr int DOT_NT = 256;
 constexpr int MAXQ = 8;          // Q vectors per multi-dot launch
 constexpr int MAX_BASIS = 64;    // m_max limit of the Jacobi kernel
@@ -54,15 +55,18 @@ __device__ __forceinline__ double warp_sum(double x) {
     return x;
 }
 
-// Sum over the CTA of DOT_NT threads (fixed order: warp trees, then the warps' sums in
-// warp order); the result in thread 0.  red holds DOT_NT / 32 doubles.
+// Sum over the CTA of DOT_NT threads (fixed order: warp trees, then a shuffle tree over
+// the warps' sums in warp 0); the result in thread 0.  red holds DOT_NT / 32 doubles.
 __device__ __forceinline__ double cta_sum(double x, double* red) {
     x = warp_sum(x);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
     __syncthreads();
     double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < DOT_NT / 32; ++w) t += red[w];
+    if (threadIdx.x < 32) {
+        t = threadIdx.x < DOT_NT / 32 ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = DOT_NT / 64; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    }
     __syncthreads();
     return t;
 }
