@@ -272,22 +272,147 @@ __global__ void k_lanczos_step(double* __restrict__ w, const double* __restrict_
     w[n] = v;
 }
 
-// T (n x n, row stride lds): diagonal alpha, off-diagonal sqrt(beta2)
-__global__ void k_tridiag(double* __restrict__ T, int lds, const double* __restrict__ alpha,
-                          const double* __restrict__ beta2, int n) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n * n) return;
-    const int i = e / n, k = e % n;
-    T[i * lds + k] = i == k ? alpha[i] : (i == k + 1 || k == i + 1 ? sqrt(beta2[i < k ? i : k]) : 0.0);
+// Number of eigenvalues below x of the symmetric tridiagonal matrix with diagonal a[0:n]
+// and squared off-diagonal b2[0:n-1]: the sign changes of the characteristic-polynomial
+// sequence p_{-1} = 1, p_i(x) = (a_i - x) p_{i-1} - b2_{i-1} p_{i-2} (a zero takes the
+// sign opposite to its predecessor; b2 = 0 restarts the sequence).  Division-free: three
+// FP64 operations per step (FP64 division is a long chain on this GPU); (p_i, p_{i-1})
+// are rescaled by 2^-+256 when their larger exponent leaves [2^-256, 2^256].
+__device__ int tri_sturm_count(const double* a, const double* b2, int n, double x) {
+    double pp = 1.0, p = a[0] - x;
+    int sp = 1, cnt = 0;
+    for (int i = 0;; ++i) {
+        const long long bits = __double_as_longlong(p);
+        const int s = (bits & 0x7FFFFFFFFFFFFFFFll) == 0 ? -sp : (bits < 0 ? -1 : 1);
+        cnt += s != sp;
+        sp = s;
+        if (i + 1 == n) break;
+        const int e = max(int((bits >> 52) & 0x7FF), int((__double_as_longlong(pp) >> 52) & 0x7FF));
+        if (e > 1023 + 256) {
+            p *= 0x1p-256;
+            pp *= 0x1p-256;
+        } else if (e < 1023 - 256) {
+            p *= 0x1p256;
+            pp *= 0x1p256;
+        }
+        const double q = b2[i];
+        const double np = q == 0.0 ? (a[i + 1] - x) : fma(-q, pp, (a[i + 1] - x) * p);
+        pp = q == 0.0 ? 1.0 : p;
+        if (q == 0.0) sp = 1;   // a new block: its sequence starts from p_{-1} = 1
+        p = np;
+    }
+    return cnt;
 }
 
-// out = (theta[0], U[last][0], beta2[j]) for the one read-back of a Lanczos step
-__global__ void k_lanczos_probe(double* __restrict__ out, const double* __restrict__ theta, const double* __restrict__ U,
-                                int ldu, int last, const double* __restrict__ beta2_j) {
-    out[0] = theta[0];
-    out[1] = U[last * ldu];
-    out[2] = *beta2_j;
+constexpr int TRI_NT = 128;   // multisection points per round (one warp per SM sub-partition)
+
+// Lowest eigenpair of the symmetric tridiagonal T_n (diagonal alpha[0:n], squared
+// off-diagonal beta2[0:n-1]) for the Rayleigh-Ritz step of Lanczos, which needs only
+// that pair: theta[0] = lambda_min, U[i*ldu] = component i of its unit eigenvector (the
+// other columns of U are not touched), and probe = (lambda_min, its last component,
+// *beta2_j) for the step's read-back.
+// lambda_min by multisection on Sturm counts: the bracket (Gershgorin, widened by a few
+// ulps) is cut at TRI_NT points per round, each thread counting the eigenvalues below
+// its point, and shrinks to the interval between the last point with none and the first
+// with one, until its width is 4 ulps of the matrix scale.  The eigenvector by two steps
+// of inverse iteration with the LDL^T factorisation of T - lambda I (pivots kept at least
+// one ulp of the scale away from zero), from the all-ones vector.
+__global__ void __launch_bounds__(TRI_NT) k_tridiag_lowest(const double* __restrict__ alpha,
+                                                          const double* __restrict__ beta2, int n,
+                                                          double* __restrict__ theta, double* __restrict__ U, int ldu,
+                                                          double* __restrict__ probe,
+                                                          const double* __restrict__ beta2_j) {
+    __shared__ double a[MAX_BASIS], b2[MAX_BASIS], bb[MAX_BASIS], rd[MAX_BASIS], ll[MAX_BASIS], y[MAX_BASIS];
+    __shared__ double red_lo[TRI_NT / 32], red_hi[TRI_NT / 32];
+    __shared__ int s_first;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < n; i += TRI_NT) {
+        a[i] = alpha[i];
+        const double q = i + 1 < n ? beta2[i] : 0.0;
+        b2[i] = q;
+        bb[i] = sqrt(q);
+    }
+    __syncthreads();
+    // Gershgorin bracket
+    double glo = HUGE_VAL, ghi = -HUGE_VAL;
+    for (int i = tid; i < n; i += TRI_NT) {
+        const double r = (i > 0 ? bb[i - 1] : 0.0) + bb[i];
+        glo = fmin(glo, a[i] - r);
+        ghi = fmax(ghi, a[i] + r);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        glo = fmin(glo, __shfl_xor_sync(0xffffffffu, glo, o));
+        ghi = fmax(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
+    }
+    if (lane == 0) {
+        red_lo[warp] = glo;
+        red_hi[warp] = ghi;
+    }
+    __syncthreads();
+    double lo = red_lo[0], hi = red_hi[0];
+    for (int w = 1; w < TRI_NT / 32; ++w) {
+        lo = fmin(lo, red_lo[w]);
+        hi = fmax(hi, red_hi[w]);
+    }
+    const double scale = fmax(fabs(lo), fabs(hi));
+    const double eps = 0x1p-52;
+    lo -= 4.0 * eps * scale + 0x1p-1000;
+    hi += 4.0 * eps * scale + 0x1p-1000;
+    // multisection: every thread holds the same bracket (the same arithmetic)
+    for (int round = 0; round < 24; ++round) {
+        const double w = hi - lo;
+        if (!(w > 4.0 * eps * scale)) break;
+        const double x = lo + w * (double(tid + 1) / double(TRI_NT + 1));
+        const int cnt = tri_sturm_count(a, b2, n, x);
+        if (tid == 0) s_first = TRI_NT;
+        __syncthreads();
+        if (cnt >= 1) atomicMin(&s_first, tid);
+        __syncthreads();
+        const int k = s_first;
+        const double nlo = k == 0 ? lo : lo + w * (double(k) / double(TRI_NT + 1));
+        const double nhi = k == TRI_NT ? hi : lo + w * (double(k + 1) / double(TRI_NT + 1));
+        __syncthreads();   // s_first is read by every thread before the next round resets it
+        if (nlo == lo && nhi == hi) break;
+        lo = nlo;
+        hi = nhi;
+    }
+    const double lambda = 0.5 * (lo + hi);
+    if (tid == 0) {
+        // T - lambda I = L D L^T: d_i = (a_i - lambda) - l_{i-1} b_{i-1}, l_i = b_i / d_i
+        const double piv = eps * scale + 0x1p-1000;
+        double d = a[0] - lambda;
+        for (int i = 0; i < n; ++i) {
+            if (i > 0) d = (a[i] - lambda) - ll[i - 1] * bb[i - 1];
+            if (fabs(d) < piv) d = d < 0.0 ? -piv : piv;
+            rd[i] = 1.0 / d;
+            ll[i] = bb[i] * rd[i];
+        }
+        for (int i = 0; i < n; ++i) y[i] = 1.0;
+        for (int iter = 0; iter < 2; ++iter) {
+            for (int i = 1; i < n; ++i) y[i] -= ll[i - 1] * y[i - 1];   // L z = y
+            for (int i = 0; i < n; ++i) y[i] *= rd[i];                  // D w = z
+            for (int i = n - 2; i >= 0; --i) y[i] -= ll[i] * y[i + 1];  // L^T x = w
+            double mx = 0.0;
+            for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(y[i]));
+            const double inv = mx > 0.0 ? 1.0 / mx : 1.0;
+            double ss = 0.0;
+            for (int i = 0; i < n; ++i) {
+                y[i] *= inv;
+                ss += y[i] * y[i];
+            }
+            const double r = 1.0 / sqrt(ss);
+            for (int i = 0; i < n; ++i) y[i] *= r;
+        }
+        theta[0] = lambda;
+        probe[0] = lambda;
+        probe[1] = y[n - 1];
+        probe[2] = *beta2_j;
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += TRI_NT) U[i * ldu] = y[i];
 }
+
 
 // S after a thick restart: diag(theta[0:r]) in the leading r x r block, zero elsewhere
 __global__ void k_diag_set(double* __restrict__ S, int lds, int mmax, const double* __restrict__ theta, int r) {
@@ -739,7 +864,7 @@ extern "C" int dmrg_davidson(dmrg_heff_t hh, int32_t k_eig, double tol, int32_t 
 // Lowest eigenpair by restarted Lanczos with full reorthogonalisation (the steps are
 // listed with the oracle's variant): per step one apply, alpha_j, the three-term step,
 // two Gram-Schmidt passes against the basis, beta_j, and Rayleigh-Ritz on the growing
-// tridiagonal T with the warm-started Jacobi kernel; one read-back per step.
+// tridiagonal T (its lowest pair only, k_tridiag_lowest); one read-back per step.
 extern "C" int dmrg_lanczos(dmrg_heff_t hh, double tol, int32_t max_iter, int32_t m_max, double* x_inout,
                             double* eval, dmrg_davidson_info* info) {
     using namespace dmrg;
@@ -761,14 +886,13 @@ extern "C" int dmrg_lanczos(dmrg_heff_t hh, double tol, int32_t max_iter, int32_
     double* alpha = s->small + 3000;   // alpha_j (device)
     double* beta2 = s->small + 3100;   // beta_j^2 (device)
     double* probe = s->small + 3200;
-    const size_t jac_smem = sizeof(double) * 2 * MAX_BASIS * (MAX_BASIS + 1);
     // q_0 = x0 / ||x0||
     if ((rc = run.check(cudaMemcpy(s->R, x_inout, sizeof(double) * dim, cudaMemcpyDeviceToDevice), "x0"))) return rc;
     int m = 0;
     bool kept = false;
     if ((rc = run.cgs2_append(s->R, &m, &kept))) return rc;
     if (!kept) return fail(DMRG_ERR_INVALID_ARG, "start vector is numerically zero");
-    int it = 0, matvecs = 0, restarts = 0, m_prev = 0, n = 0;
+    int it = 0, matvecs = 0, restarts = 0, n = 0;
     double theta = 0.0;
     bool converged = false, restart = false;
     while (it < max_iter) {
@@ -777,7 +901,6 @@ extern "C" int dmrg_lanczos(dmrg_heff_t hh, double tol, int32_t max_iter, int32_
             m = 0;
             if ((rc = run.cgs2_append(s->C, &m, &kept))) return rc;
             if (!kept) return fail(DMRG_ERR_INVALID_ARG, "Ritz vector is numerically zero");
-            m_prev = 0;
             ++restarts;
             restart = false;
         }
@@ -796,10 +919,7 @@ extern "C" int dmrg_lanczos(dmrg_heff_t hh, double tol, int32_t max_iter, int32_
                             "beta")))
             return rc;
         n = j + 1;   // T_j is n x n
-        k_tridiag<<<blocks_for(n * n), 256, 0, st>>>(s->S, mmax, alpha, beta2, n);
-        k_jacobi<<<1, 256, jac_smem, st>>>(s->S, n, mmax, s->theta, s->U, mmax, m_prev < n ? m_prev : 0);
-        m_prev = n;
-        k_lanczos_probe<<<1, 1, 0, st>>>(probe, s->theta, s->U, mmax, n - 1, beta2 + j);
+        k_tridiag_lowest<<<1, TRI_NT, 0, st>>>(alpha, beta2, n, s->theta, s->U, mmax, probe, beta2 + j);
         if ((rc = run.check(cudaGetLastError(), "lanczos ritz"))) return rc;
         double pr[3];
         if ((rc = run.check(cudaMemcpy(pr, probe, sizeof(pr), cudaMemcpyDeviceToHost), "read ritz"))) return rc;
