@@ -209,9 +209,9 @@ int dmrg_davidson(dmrg_heff_t h, int32_t k_eig, double tol, int32_t max_iter, in
 /* Lowest eigenpair by restarted Lanczos (paper: Numerical procedure, the Lanczos
  * alternative to Davidson named after Eq. 2): per step one H_eff product, the
  * three-term recurrence, full FP64 reorthogonalisation against the basis (two
- * Gram-Schmidt passes) and Rayleigh-Ritz on the tridiagonal matrix by cyclic Jacobi
- * on the device; explicit restart from the Ritz vector when the basis holds m_max
- * vectors.  Converged when the residual estimate beta_j |s_j| <= tol, or when the
+ * Gram-Schmidt passes) and Rayleigh-Ritz on the tridiagonal matrix for its lowest
+ * pair on the device (multisection on Sturm counts, then inverse iteration); explicit
+ * restart from the Ritz vector when the basis holds m_max vectors.  Converged when the residual estimate beta_j |s_j| <= tol, or when the
  * Krylov space becomes invariant.
  *   max_iter : steps allowed (each one product);  m_max : 2 .. 63
  *   x_inout  : device, dim doubles: the start vector (any norm); on return the unit
@@ -367,8 +367,8 @@ int dmrg_heff_psi_blocks(dmrg_heff_t h, int64_t* buf, int64_t* n_blocks);
  * left sector; a spin-adapted one has one per right spin coupling to the target, and the
  * squared singular values are then the multiplet weights of the left block's density
  * matrix summed over the magnetic sublevels.  Per matrix the singular values and left
- * singular vectors (one-sided Jacobi in FP64 on the device, one CTA per matrix, up to 8192
- * columns), then the D largest singular values over all matrices are kept (values below
+ * singular vectors (one-sided Jacobi in FP64 on the device: one CTA per matrix up to
+ * 64 KB, an 8-CTA cluster per larger matrix; up to 8192 columns), then the D largest singular values over all matrices are kept (values below
  * 1e-13 of the largest are zero and never kept; ties go to the earlier matrix, then
  * position).  Matrices are indexed in the order of their left sectors.
  *   psi       : device, dim doubles
